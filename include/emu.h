@@ -1,0 +1,225 @@
+/*
+ * emu.h: C ABI of the GB300 quasi-static muscle solver (EMU, arXiv 2006.08821).
+ *
+ * The library solves the quasi-static problem of Sec. 3 (Eq. 1) in EMU's
+ * variable-separated form (Eq. 5). Each tet carries its own deformation
+ * gradient F_i. On the device it is stored as a rotation R_i and a
+ * symmetric stretch S_i (six coordinates s_i), F_i = R_i S_i. Positions q
+ * are the "nearest continuous mesh" of Eq. 4. Each Newton iteration:
+ *
+ *   - evaluates the exact gradient of Eqs. 6-7 per tet;
+ *   - builds the elastic Hessian in rotation/stretch coordinates (rotation
+ *     block zero because Psi is rotation invariant; 6x6 stretch block with a
+ *     definiteness fix, Sec. 3.2.1);
+ *   - forms the low-rank Woodbury direction of Eqs. 9-12 (k = 48);
+ *   - solves the constant ACAP system of Eq. 4 on the device in FP64;
+ *   - runs the backtracking Armijo line search of Algorithm 1;
+ *   - re-extracts R_i, S_i from F_i + sigma d_i by a polar decomposition.
+ *
+ * Conventions, shared by every entry point:
+ *   - Return value 0 (EMU_OK) on success, a negative emu_status otherwise.
+ *     No C++ exception crosses this boundary. emu_last_error() returns a
+ *     thread-local message for the last failure.
+ *   - Host input buffers are read during the call and copied; the caller
+ *     keeps ownership. Output buffers are caller-owned.
+ *   - Device state is owned by the handle. It is allocated through the
+ *     optional allocator callback at create time, or with cudaMalloc when
+ *     the allocator is NULL, and released by emu_destroy.
+ *   - All device work is enqueued on the stream given at create time
+ *     (NULL = the legacy default stream). Calls that return host-visible
+ *     results synchronise that stream only.
+ *   - A handle is not thread-safe. Distinct handles may be used from
+ *     distinct threads.
+ *   - Units: SI (metres, pascals). Positions are row-major (n, 3) float64.
+ */
+#ifndef EMU_H_
+#define EMU_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+typedef enum {
+  EMU_OK = 0,
+  EMU_ERR_INVALID_ARG = -1,     /* bad pointer, size, index or parameter      */
+  EMU_ERR_DEGENERATE_TET = -2,  /* |det D_m| below 1e-14 h^3 (Eq. 2)          */
+  EMU_ERR_OOM = -3,             /* allocator or device memory failure          */
+  EMU_ERR_NOT_CONVERGED = -4,   /* max_newton reached; state kept and usable   */
+  EMU_ERR_LINESEARCH = -5,      /* no Armijo step within ls_max_trials         */
+  EMU_ERR_PCG = -6,             /* ACAP solve did not reach pcg_tol            */
+  EMU_ERR_INVERTED = -7,        /* non-finite gradient / inverted element      */
+  EMU_ERR_TIMEOUT = -8,         /* a bounded device wait ran out               */
+  EMU_ERR_CUDA = -9,            /* CUDA runtime error                          */
+  EMU_ERR_NOT_IMPLEMENTED = -10
+} emu_status;
+
+typedef enum { EMU_PRECISION_FP64 = 0, EMU_PRECISION_MIXED = 1 } emu_precision;
+
+/* Opaque solver handle (library-owned). */
+typedef struct emu_handle emu_handle;
+
+/* Device allocator callback. alloc returns a device pointer aligned to at
+ * least 256 bytes, or NULL on failure; free releases it. ``stream`` is the
+ * handle's cudaStream_t. The PyTorch binding routes these to torch's caching
+ * allocator. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*free)(void* ctx, void* ptr, size_t bytes, void* stream);
+} emu_allocator;
+
+/* Mesh, materials, fibers and pins (Eq. 1; Sec. 3.1, 3.6).
+ *   rest_pos     n_verts x 3 rest positions Q (m). Copied.
+ *   tets         n_tets x 4 vertex indices; corner 3 is the reference corner
+ *                of Eq. 2. Negatively oriented tets are re-oriented by
+ *                swapping corners 1 and 2. Copied.
+ *   youngs, poisson   n_materials entries (Pa, dimensionless).
+ *   material_id  n_tets entries in [0, n_materials).
+ *   fiber_dir    n_tets x 3 fiber directions u_i; normalised on copy. NULL =
+ *                no fiber term.
+ *   fixed_verts  n_fixed vertex indices pinned (Sec. 3.1 removes the rigid
+ *                null space by pinning). Must be non-empty.
+ *   fixed_pos    n_fixed x 3 prescribed positions of the pinned vertices;
+ *                NULL pins them at their rest positions. */
+typedef struct {
+  int64_t n_verts;
+  int64_t n_tets;
+  const double* rest_pos;
+  const int32_t* tets;
+  int32_t n_materials;
+  const double* youngs;
+  const double* poisson;
+  const uint8_t* material_id;
+  const double* fiber_dir;
+  int64_t n_fixed;
+  const int32_t* fixed_verts;
+  const double* fixed_pos;
+} emu_mesh_desc;
+
+/* Solver parameters. emu_default_params fills the defaults shown.
+ *   alpha_rel       ACAP weight alpha of Eq. 5 as a multiple of mu_ref, the
+ *                   smallest shear modulus in the mesh (default 1).
+ *   weight_mode     0: w_i = V_i (Eq. 3 up to the volume measure, default);
+ *                   1: w_i = V_i max(1, mu_i/mu_ref) (the stiffness-weighted
+ *                   variant of Sec. 3.3).
+ *   k_modes         low-rank size of Eq. 9; a multiple of 3 in [3, 48]
+ *                   (default 48 = 16 scalar modes x 3 coordinates).
+ *   fiber_scale     kappa = fiber_scale * mu_ref multiplies a_i u^T C u.
+ *   tol_rel_residual stop when ||dE/dF||_2 / ||dE/dF at F=I||_2 <= tol.
+ *   max_newton      Newton iteration cap per solve.
+ *   ls_sigma0, ls_c, ls_rho, ls_max_trials   Armijo backtracking
+ *                   (Algorithm 1 uses 10, 1e-4, 0.5).
+ *   pcg_tol         relative residual of each ACAP solve.
+ *   pcg_max         CG iteration cap per ACAP solve.
+ *   precision       EMU_PRECISION_FP64 or EMU_PRECISION_MIXED (per-tet
+ *                   Hessian/Woodbury work in FP32; state, gradient,
+ *                   residual, line-search sums and ACAP solve in FP64).
+ *   mode_iters      subspace iterations used to build the low-rank basis.
+ *   seed            seeds the random start of the subspace iteration. */
+typedef struct {
+  double alpha_rel;
+  int32_t weight_mode;
+  int32_t k_modes;
+  double fiber_scale;
+  double tol_rel_residual;
+  int32_t max_newton;
+  double ls_sigma0;
+  double ls_c;
+  double ls_rho;
+  int32_t ls_max_trials;
+  double pcg_tol;
+  int32_t pcg_max;
+  int32_t precision;
+  int32_t mode_iters;
+  uint64_t seed;
+} emu_params;
+
+/* Per-solve statistics. */
+typedef struct {
+  int32_t newton_iters;     /* Newton iterations taken                         */
+  int32_t ls_trials;        /* line-search energy evaluations                  */
+  int32_t pcg_iters;        /* CG iterations summed over all ACAP solves       */
+  int32_t status;           /* emu_status of the solve                         */
+  double rel_residual;      /* final ||g|| / ||g(I)||                          */
+  double energy_change;     /* E(final) - E(start), summed line-search deltas  */
+  double ms;                /* wall time of the solve (host clock)             */
+} emu_solve_stats;
+
+void emu_default_params(emu_params* p);
+const char* emu_status_string(int status);
+const char* emu_last_error(void);
+
+/* Builds the solver for one mesh (Sec. 3.1 setup): D_m^-1 and V_i (Eq. 2),
+ * ACAP weights, the scalar ACAP Laplacian (G^T W G = L x I_3 with full-vertex
+ * pins, Eq. 4), its Jacobi preconditioner and the low-rank basis of Eq. 9.
+ * The state starts at rest (R = I, S = I, q = q*(I)). ``stream`` is a
+ * cudaStream_t (NULL = default stream). Returns EMU_ERR_DEGENERATE_TET,
+ * EMU_ERR_INVALID_ARG or EMU_ERR_OOM on the corresponding failure. */
+int emu_create(const emu_mesh_desc* mesh, const emu_params* params, const emu_allocator* alloc,
+               void* stream, emu_handle** out);
+
+/* Releases all device memory of the handle. NULL is accepted. */
+int emu_destroy(emu_handle* h);
+
+/* Sets a_i(t) of Sec. 3.1 (Psi_fiber = kappa a_i u_i^T F_i^T F_i u_i).
+ * ``a`` is a host array of n_tets entries, each finite and >= 0. */
+int emu_set_activation(emu_handle* h, const double* a, int64_t count);
+
+/* Same as emu_set_activation with ``a`` a device pointer (n_tets float64). */
+int emu_set_activation_device(emu_handle* h, const double* a_device, int64_t count);
+
+/* Runs Newton iterations from the resident state (warm start) until the
+ * relative residual reaches tol_rel_residual (Algorithm 1, Newton part).
+ * ``stats`` may be NULL. Returns EMU_ERR_NOT_CONVERGED when max_newton is
+ * reached; the state is then kept. */
+int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats);
+
+/* Copies q (n_verts x 3 float64, row-major) to ``out``: a host pointer when
+ * out_is_device == 0, a device pointer otherwise. */
+int emu_get_positions(emu_handle* h, double* out, int32_t out_is_device);
+
+/* Copies the per-tet state to host arrays (any may be NULL):
+ * R n_tets x 9 row-major, s n_tets x 6 in the order (xx, yy, zz, yz, xz, xy)
+ * with off-diagonals scaled by sqrt(2) so that |s| = ||S||_F, and
+ * F = R S, n_tets x 9 row-major. */
+int emu_get_element_state(emu_handle* h, double* R, double* s, double* F);
+
+/* Overwrites the per-tet stretch/rotation state and positions from host
+ * arrays (R n_tets x 9, s n_tets x 6, q n_verts x 3). R must be a rotation
+ * and S(s) positive definite. Used for warm starts and resume. */
+int emu_set_element_state(emu_handle* h, const double* R, const double* s, const double* q);
+
+/* Resets the state to rest (R = I, S = I, q = q*(I)). */
+int emu_reset(emu_handle* h);
+
+/* Sizes of the mesh held by the handle. */
+int emu_get_sizes(emu_handle* h, int64_t* n_verts, int64_t* n_tets, int32_t* k_modes);
+
+/* Evaluates, on the device, the per-element stretch terms that the solver
+ * uses (Sec. 3.1 energy with F = S, Sec. 3.2.1 Hessian):
+ *   psi[i]  = V_i Psi(S_i),
+ *   grad[i] = V_i dPsi/ds (6),
+ *   hess[i] = V_i d2Psi/ds2 (6x6 row-major) with the definiteness fix
+ *             (the coefficient mu - lambda ln J of the S^-1 dS S^-1 term
+ *             clamped at zero).
+ * All pointers are device pointers: s (n x 6), params (n x 8: V, mu,
+ * lambda, kappa*a, u_x, u_y, u_z, unused), outputs psi (n), grad (n x 6),
+ * hess (n x 36). FP64 when mixed == 0, else the FP32 code path with FP64
+ * inputs and outputs. */
+int emu_eval_stretch_terms(const double* s, const double* params, int64_t n, int32_t mixed,
+                           double* psi, double* grad, double* hess, void* stream);
+
+/* Polar decomposition F = R S (R proper rotation, S symmetric positive
+ * definite) of n row-major 3x3 matrices with det F > 0, on the device.
+ * Outputs R (n x 9) and s (n x 6, ordering as emu_get_element_state). */
+int emu_eval_polar(const double* F, int64_t n, double* R, double* s, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMU_H_ */

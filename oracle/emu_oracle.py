@@ -1,0 +1,438 @@
+"""FP64 CPU oracle of EMU's quasi-static solve (arXiv 2006.08821).
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module. The CUDA library
+never calls it, and it shares no code with the CUDA path.
+
+It follows the paper's own formulation: one free deformation gradient F_i
+per tet (9 DOF), 9x9 Hessian blocks and the low-rank Woodbury quasi-Newton
+step. The GPU path uses a rotation/stretch parametrisation of the same
+objective instead. The two reach the same stationary point, so parity is
+checked on converged positions.
+
+Section / equation map (numbers follow the paper's order):
+
+* Eq. 2 (defograd): F_i = D_s(q) D_m^-1, with corner 4 (index 3) as origin.
+* Eq. 3 (ACAPEnergy): E_C(q, F) = 1/2 sum_i w_i ||G_i q - F_i||^2. The
+  stiffness weights w_i are the paper's Sec. 3.3 remark, read as
+  w_i = V_i max(1, mu_i/mu_ref). weight_mode 0 gives w_i = V_i.
+* Eq. 4 (acap): q*(F) = (G^T W G)^-1 G^T W F on the free DOFs, with pinned
+  vertices moved to the right-hand side. Sec. 3.1 removes the rigid null
+  space by pinning.
+* Eq. 5 (separated): E(F) = sum_i V_i Psi(F_i) + alpha E_C(q*(F), F), with W = 0.
+* Sec. 3.1: Psi = compressible neo-Hookean (inverted tets get 1e40) plus the
+  fiber term a_i u_i^T F_i^T F_i u_i, scaled by a stiffness kappa.
+* Eqs. 6-7 (gradient): dE/dF = V Psi'(F) + alpha W (F - G q*(F)). The sign of
+  the second form of Eq. 7 is used; the first form has a sign typo.
+* Eqs. 9-12: the low-rank approximation of (G^T W G)^-1 by its lowest k
+  eigenpairs; H = PSD(V Psi'') + alpha W; B = Phi^T G^T W. Woodbury then
+  gives d = -[H^-1 g + alpha H^-1 B^T (Lambda - alpha B H^-1 B^T)^-1 B H^-1 g].
+* Algorithm 1 (Newton part): backtracking Armijo line search, with the
+  paper's constants as defaults apart from sigma0. q(F + s d) = q + s dq,
+  because q*(.) is affine.
+
+The converged result is a stationary point of Eq. 5. Gravity, contact,
+bones and joints are not handled here.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+INVERTED_ENERGY = 1e40  # Sec. 3.1: inverted elements get a huge energy
+
+
+# ----------------------------------------------------------------------------
+# Materials and rest geometry
+# ----------------------------------------------------------------------------
+
+def lame(youngs, poisson):
+    """Lame parameters (mu, lambda) from Young's modulus and Poisson ratio."""
+    E = np.asarray(youngs, dtype=np.float64)
+    nu = np.asarray(poisson, dtype=np.float64)
+    mu = E / (2.0 * (1.0 + nu))
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    return mu, lam
+
+
+def rest_geometry(rest_pos, tets):
+    """D_m (columns Q_j - Q_4, Eq. 2), its inverse and rest volumes V_i."""
+    Q = np.asarray(rest_pos, dtype=np.float64)
+    T = np.asarray(tets, dtype=np.int64)
+    Dm = np.stack([Q[T[:, j]] - Q[T[:, 3]] for j in range(3)], axis=2)  # (m,3,3), column j
+    det = np.linalg.det(Dm)
+    if np.any(det <= 0.0):
+        raise ValueError("tets must be positively oriented ([Q0-Q3, Q1-Q3, Q2-Q3] det > 0)")
+    return Dm, np.linalg.inv(Dm), det / 6.0
+
+
+def build_G(n_verts, tets, Dinv):
+    """Sparse G (9m x 3n) with (G q)_{9i+3r+c} = F_i[r][c] of Eq. 2.
+
+    F_i[r][c] = sum_{j<3} (q_j[r] - q_3[r]) Dinv_i[j][c].
+    """
+    T = np.asarray(tets, dtype=np.int64)
+    m = T.shape[0]
+    rows, cols, vals = [], [], []
+    ii = np.arange(m)
+    for r in range(3):
+        for c in range(3):
+            row = 9 * ii + 3 * r + c
+            for j in range(3):
+                rows.append(row)
+                cols.append(3 * T[:, j] + r)
+                vals.append(Dinv[:, j, c])
+            rows.append(row)
+            cols.append(3 * T[:, 3] + r)
+            vals.append(-(Dinv[:, 0, c] + Dinv[:, 1, c] + Dinv[:, 2, c]))
+    G = sp.csr_matrix(
+        (np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+        shape=(9 * m, 3 * n_verts),
+    )
+    G.sum_duplicates()
+    return G
+
+
+# ----------------------------------------------------------------------------
+# Per-tet energy (Sec. 3.1): neo-Hookean + fiber, F-form
+# ----------------------------------------------------------------------------
+
+def psi(F, mu, lam, ka, u):
+    """Psi(F) = mu/2 (tr F^T F - 3) - mu ln J + lam/2 ln^2 J + ka |F u|^2.
+
+    J = det F; J <= 0 returns INVERTED_ENERGY. ``ka`` is kappa * a_i.
+    """
+    J = np.linalg.det(F)
+    I1 = np.einsum("...ij,...ij->...", F, F)
+    Fu = np.einsum("...ij,...j->...i", F, u)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        lnJ = np.log(np.where(J > 0, J, 1.0))
+    val = 0.5 * mu * (I1 - 3.0) - mu * lnJ + 0.5 * lam * lnJ**2 + ka * np.einsum("...i,...i->...", Fu, Fu)
+    return np.where(J > 0, val, INVERTED_ENERGY)
+
+
+def dpsi(F, mu, lam, ka, u):
+    """First Piola stress P = mu F - mu F^-T + lam ln J F^-T + 2 ka F u u^T."""
+    J = np.linalg.det(F)
+    FinvT = np.swapaxes(np.linalg.inv(F), -1, -2)
+    lnJ = np.log(J)
+    uu = np.einsum("...i,...j->...ij", u, u)
+    return (mu[..., None, None] * (F - FinvT) + (lam * lnJ)[..., None, None] * FinvT
+            + 2.0 * ka[..., None, None] * np.einsum("...ij,...jk->...ik", F, uu))
+
+
+def d2psi(F, mu, lam, ka, u):
+    """9x9 Hessian of Psi in row-major vec(F) (index 3r+c).
+
+    dP = mu dF + (mu - lam ln J) F^-T dF^T F^-T + lam tr(F^-1 dF) F^-T
+         + 2 ka dF u u^T.
+    """
+    m = F.shape[0]
+    Finv = np.linalg.inv(F)
+    lnJ = np.log(np.linalg.det(F))
+    H = np.zeros((m, 3, 3, 3, 3))  # H[i, r, c, b, a] = dP_rc / dF_ba
+    eye = np.eye(3)
+    H += mu[:, None, None, None, None] * np.einsum("rb,ca->rcba", eye, eye)[None]
+    # (F^-T dF^T F^-T)_rc = sum_ab Finv[a,r] dF[b,a] Finv[c,b]
+    H += (mu - lam * lnJ)[:, None, None, None, None] * np.einsum("iar,icb->ircba", Finv, Finv)
+    # tr(F^-1 dF) F^-T: coefficient of dF[b,a] is Finv[a,b]; (F^-T)_rc = Finv[c,r]
+    H += lam[:, None, None, None, None] * np.einsum("icr,iab->ircba", Finv, Finv)
+    # 2 ka (dF u u^T)_rc = 2 ka sum_a dF[r,a] u_a u_c
+    H += (2.0 * ka)[:, None, None, None, None] * np.einsum("rb,ia,ic->ircba", eye, u, u)
+    return H.reshape(m, 9, 9)
+
+
+def psd_project(Hb):
+    """Clamp negative eigenvalues of symmetric blocks to zero (Sec. 3.2.1's
+    definiteness fix)."""
+    Hs = 0.5 * (Hb + np.swapaxes(Hb, -1, -2))
+    lam, vec = np.linalg.eigh(Hs)
+    lam = np.maximum(lam, 0.0)
+    return np.einsum("...ij,...j,...kj->...ik", vec, lam, vec)
+
+
+def delta_psi(F, d, sigma, mu, lam, ka, u):
+    """Psi(F + sigma d) - Psi(F), computed term by term so that it stays
+    accurate when the step is tiny (Armijo test near convergence).
+
+    ln J' - ln J = ln det(I + sigma M), M = F^-1 d, expanded as
+    det(I + sM) = 1 + s tr M + s^2 e2(M) + s^3 det M.
+    """
+    M = np.linalg.solve(F, d)
+    trM = np.trace(M, axis1=-2, axis2=-1)
+    e2 = 0.5 * (trM**2 - np.einsum("...ij,...ji->...", M, M))
+    x = sigma * trM + sigma**2 * e2 + sigma**3 * np.linalg.det(M)
+    ok = x > -1.0
+    dlnJ = np.log1p(np.where(ok, x, 0.0))
+    lnJ = np.log(np.linalg.det(F))
+    Fd = np.einsum("...ij,...ij->...", F, d)
+    dd = np.einsum("...ij,...ij->...", d, d)
+    Fu = np.einsum("...ij,...j->...i", F, u)
+    du = np.einsum("...ij,...j->...i", d, u)
+    val = (0.5 * mu * (2.0 * sigma * Fd + sigma**2 * dd)
+           - mu * dlnJ
+           + 0.5 * lam * dlnJ * (2.0 * lnJ + dlnJ)
+           + ka * (2.0 * sigma * np.einsum("...i,...i->...", Fu, du)
+                   + sigma**2 * np.einsum("...i,...i->...", du, du)))
+    return np.where(ok, val, np.inf)
+
+
+# ----------------------------------------------------------------------------
+# Symmetric-stretch embedding, used only to express Psi as a function of the
+# six stretch coordinates s for per-element checks of the GPU's stretch form.
+# ----------------------------------------------------------------------------
+
+_R2 = np.sqrt(0.5)
+
+
+def sym_basis():
+    """Six orthonormal symmetric 3x3 matrices E_k (Frobenius metric), order
+    xx, yy, zz, yz, xz, xy; S(s) = sum_k s_k E_k."""
+    E = np.zeros((6, 3, 3))
+    E[0, 0, 0] = E[1, 1, 1] = E[2, 2, 2] = 1.0
+    E[3, 1, 2] = E[3, 2, 1] = _R2
+    E[4, 0, 2] = E[4, 2, 0] = _R2
+    E[5, 0, 1] = E[5, 1, 0] = _R2
+    return E
+
+
+def stretch_from_s(s):
+    return np.einsum("...k,kij->...ij", s, sym_basis())
+
+
+def s_from_stretch(S):
+    return np.einsum("...ij,kij->...k", S, sym_basis())
+
+
+def element_terms_s(s, mu, lam, ka, u, V):
+    """V Psi(S(s)), its s-gradient and its exact (unprojected) s-Hessian.
+
+    With S(s) linear in s, d/ds = A^T vec(P(S)) and d2/ds2 = A^T Psi''(S) A,
+    where A (9x6) holds vec(E_k) as columns.
+    """
+    S = stretch_from_s(s)
+    Amat = sym_basis().reshape(6, 9).T  # (9, 6)
+    val = V * psi(S, mu, lam, ka, u)
+    g = V[:, None] * np.einsum("ka,ia->ik", Amat.T, dpsi(S, mu, lam, ka, u).reshape(-1, 9))
+    H = V[:, None, None] * np.einsum("ak,iab,bl->ikl", Amat, d2psi(S, mu, lam, ka, u), Amat)
+    return val, g, H
+
+
+# ----------------------------------------------------------------------------
+# The problem and Algorithm 1
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class OracleParams:
+    alpha_rel: float = 1.0          # alpha = alpha_rel * mu_ref (Pa)
+    weight_mode: int = 1            # 1: w = V max(1, mu/mu_ref); 0: w = V
+    k_modes: int = 48               # Sec. 3.2.1: k = 48
+    fiber_scale: float = 1.0        # kappa = fiber_scale * mu_ref
+    tol: float = 1e-8               # relative F-space gradient norm
+    max_newton: int = 1000
+    ls_sigma0: float = 1.0          # Algorithm 1 uses 10; 1 is the Newton step
+    ls_c: float = 1e-4              # Algorithm 1
+    ls_rho: float = 0.5             # Algorithm 1
+    ls_max_trials: int = 60
+
+
+@dataclasses.dataclass
+class OracleResult:
+    q: np.ndarray          # (n, 3) converged positions
+    F: np.ndarray          # (m, 3, 3)
+    iterations: int
+    rel_residual: float
+    energy: float
+    ls_trials: int
+    history: list
+    seconds: float
+
+
+class EmuOracle:
+    """Setup (Sec. 3.1-3.2.1) for one mesh; ``solve`` runs Algorithm 1."""
+
+    def __init__(self, mesh, params: OracleParams | None = None, modes: str = "eigsh"):
+        self.p = params or OracleParams()
+        self.mesh = mesh
+        Q = np.asarray(mesh.rest_pos, dtype=np.float64)
+        T = np.asarray(mesh.tets, dtype=np.int64)
+        self.n, self.m = Q.shape[0], T.shape[0]
+        self.Q = Q
+        self.T = T
+        _, self.Dinv, self.V = rest_geometry(Q, T)
+        mu_mat, lam_mat = lame(mesh.youngs, mesh.poisson)
+        mid = np.asarray(mesh.material_id, dtype=np.int64)
+        self.mu = mu_mat[mid]
+        self.lam = lam_mat[mid]
+        bone = np.zeros(self.m, dtype=bool) if mesh.bone_id is None else np.asarray(mesh.bone_id) >= 0
+        self.mu_ref = float(self.mu[~bone].min()) if np.any(~bone) else float(self.mu.min())
+        if self.p.weight_mode == 1:
+            self.w = self.V * np.where(bone, 1.0, np.maximum(1.0, self.mu / self.mu_ref))
+        else:
+            self.w = self.V.copy()
+        self.alpha = self.p.alpha_rel * self.mu_ref
+        self.kappa = self.p.fiber_scale * self.mu_ref
+        u = np.asarray(mesh.fiber_dir, dtype=np.float64)
+        self.u = u / np.linalg.norm(u, axis=1, keepdims=True)
+
+        # Free / pinned DOFs (full-vertex pins; Sec. 3.1 null-space removal)
+        fixed_v = np.asarray(mesh.fixed_verts, dtype=np.int64)
+        if fixed_v.size == 0:
+            raise ValueError("at least one pinned vertex is needed (rigid null space)")
+        is_fixed = np.zeros(self.n, dtype=bool)
+        is_fixed[fixed_v] = True
+        self.fixed_dofs = (3 * np.nonzero(is_fixed)[0][:, None] + np.arange(3)).ravel()
+        self.free_dofs = (3 * np.nonzero(~is_fixed)[0][:, None] + np.arange(3)).ravel()
+        qfix = Q.copy()
+        if mesh.fixed_pos is not None:
+            qfix[fixed_v] = np.asarray(mesh.fixed_pos, dtype=np.float64)
+        self.q_c = qfix.ravel()[self.fixed_dofs]
+
+        # Eq. 3 operator and the constant ACAP matrix of Eq. 4
+        self.G = build_G(self.n, T, self.Dinv)
+        self.G_f = self.G[:, self.free_dofs].tocsr()
+        self.G_c = self.G[:, self.fixed_dofs].tocsr()
+        self.w9 = np.repeat(self.w, 9)
+        self.K = (self.G_f.T @ sp.diags(self.w9) @ self.G_f).tocsc()
+        self._lu = spla.splu(self.K)
+        self.Gc_qc = self.G_c @ self.q_c
+
+        # Eq. 9: lowest k eigenpairs of the ACAP matrix
+        nf = self.free_dofs.size
+        k = min(self.p.k_modes, nf)
+        if modes == "eigsh" and k < nf - 1 and nf > 600:
+            lam_k, Phi = spla.eigsh(self.K, k=k, sigma=0.0, which="LM")
+        else:
+            lam_all, vec_all = np.linalg.eigh(self.K.toarray())
+            lam_k, Phi = lam_all[:k], vec_all[:, :k]
+        order = np.argsort(lam_k)
+        self.Lam = lam_k[order]
+        self.Phi = Phi[:, order]                      # (3 n_f, k)
+        # Eq. 11: B = Phi^T G^T W (k x 9m), dense
+        self.B = (sp.diags(self.w9) @ (self.G_f @ self.Phi)).T.copy()
+        self.k = k
+
+    # --- Eq. 4 -------------------------------------------------------------
+    def acap_solve(self, F):
+        """q*(F): positions minimising E_C for the given per-tet F (m,3,3)."""
+        rhs = self.G_f.T @ (self.w9 * (F.reshape(-1) - self.Gc_qc))
+        q = np.empty(3 * self.n)
+        q[self.free_dofs] = self._lu.solve(rhs)
+        q[self.fixed_dofs] = self.q_c
+        return q
+
+    def acap_solve_d(self, d):
+        """Linear part of q*(.): the free-DOF change from F -> F + d."""
+        rhs = self.G_f.T @ (self.w9 * d.reshape(-1))
+        dq = np.zeros(3 * self.n)
+        dq[self.free_dofs] = self._lu.solve(rhs)
+        return dq
+
+    def deformation_gradients(self, q):
+        """G q as (m,3,3) (Eq. 2)."""
+        return (self.G @ q).reshape(self.m, 3, 3)
+
+    # --- Eq. 5 and Eqs. 6-7 --------------------------------------------------
+    def energy(self, F, q, a):
+        ka = self.kappa * a
+        Psi = np.sum(self.V * psi(F, self.mu, self.lam, ka, self.u))
+        D = self.deformation_gradients(q) - F
+        return Psi + 0.5 * self.alpha * np.sum(self.w * np.einsum("ijk,ijk->i", D, D))
+
+    def gradient(self, F, q, a):
+        """dE/dF = V Psi'(F) + alpha w (F - G q*(F)), (m,3,3)."""
+        ka = self.kappa * a
+        P = dpsi(F, self.mu, self.lam, ka, self.u)
+        return self.V[:, None, None] * P + (self.alpha * self.w)[:, None, None] * (F - self.deformation_gradients(q))
+
+    def residual_normaliser(self, a, F_start=None):
+        """||dE/dF|| at F = I, q = q*(I) (the unloaded state), the scale of
+        the relative residual. When the load vanishes (a = 0 with rest pins)
+        that norm is rounding noise, so a value below 1e-12 sqrt(sum (V mu)^2)
+        falls back to the gradient at the starting state; 0 means the start
+        is already the solution."""
+        floor = 1e-12 * np.sqrt(np.sum((self.V * self.mu) ** 2))
+        I = np.broadcast_to(np.eye(3), (self.m, 3, 3)).copy()
+        g0 = np.linalg.norm(self.gradient(I, self.acap_solve(I), a))
+        if g0 <= floor:
+            g0 = 0.0
+            if F_start is not None:
+                g0 = np.linalg.norm(self.gradient(F_start, self.acap_solve(F_start), a))
+                if g0 <= floor:
+                    g0 = 0.0
+        return g0
+
+    # --- Eqs. 11-12 ----------------------------------------------------------
+    def hessian_blocks(self, F, a):
+        ka = self.kappa * a
+        Hel = self.V[:, None, None] * d2psi(F, self.mu, self.lam, ka, self.u)
+        return psd_project(Hel) + (self.alpha * self.w)[:, None, None] * np.eye(9)[None]
+
+    def woodbury_direction(self, H, g):
+        """d = -[H^-1 g + alpha H^-1 B^T (Lambda - alpha B H^-1 B^T)^-1 B H^-1 g]."""
+        gm = g.reshape(self.m, 9)
+        Hinv_g = np.linalg.solve(H, gm[..., None])[..., 0].reshape(-1)
+        Bt = self.B.T.reshape(self.m, 9, self.k)
+        Hinv_Bt = np.linalg.solve(H, Bt).reshape(9 * self.m, self.k)
+        Cap = np.diag(self.Lam) - self.alpha * (self.B @ Hinv_Bt)
+        z = sla.solve(0.5 * (Cap + Cap.T), self.B @ Hinv_g, assume_a="pos")
+        return -(Hinv_g + self.alpha * (Hinv_Bt @ z))
+
+    def delta_energy(self, F, d, q, dq, a, sigma):
+        """E(F + sigma d) - E(F) with q(F + sigma d) = q + sigma dq."""
+        ka = self.kappa * a
+        dP = np.sum(self.V * delta_psi(F, d, sigma, self.mu, self.lam, ka, self.u))
+        D = (self.deformation_gradients(q) - F).reshape(self.m, 9)
+        dD = (self.deformation_gradients(dq) - d).reshape(self.m, 9)
+        dC = 0.5 * self.alpha * np.sum(self.w * (2.0 * sigma * np.einsum("ij,ij->i", D, dD)
+                                                 + sigma**2 * np.einsum("ij,ij->i", dD, dD)))
+        return dP + dC
+
+    # --- Algorithm 1 (Newton part) ------------------------------------------
+    def solve(self, a, F0=None, tol=None, max_newton=None, record=False):
+        p = self.p
+        tol = p.tol if tol is None else tol
+        max_newton = p.max_newton if max_newton is None else max_newton
+        a = np.broadcast_to(np.asarray(a, dtype=np.float64), (self.m,)).copy()
+        F = np.broadcast_to(np.eye(3), (self.m, 3, 3)).copy() if F0 is None else np.array(F0, dtype=np.float64)
+        t0 = time.perf_counter()
+        gnorm0 = self.residual_normaliser(a, F)
+        hist = []
+        trials_total = 0
+        it = 0
+        res = 0.0
+        while True:
+            q = self.acap_solve(F)
+            g = self.gradient(F, q, a)
+            res = float(np.linalg.norm(g) / gnorm0) if gnorm0 > 0 else 0.0
+            if record:
+                hist.append(res)
+            if res <= tol or it >= max_newton:
+                break
+            H = self.hessian_blocks(F, a)
+            d = self.woodbury_direction(H, g.reshape(-1)).reshape(self.m, 3, 3)
+            gtd = float(np.sum(g * d))
+            if gtd >= 0.0:
+                raise RuntimeError("quasi-Newton direction is not a descent direction")
+            dq = self.acap_solve_d(d)
+            sigma = p.ls_sigma0
+            for trial in range(p.ls_max_trials):
+                trials_total += 1
+                if self.delta_energy(F, d, q, dq, a, sigma) <= p.ls_c * sigma * gtd:
+                    break
+                sigma *= p.ls_rho
+            else:
+                raise RuntimeError("line search failed")
+            F = F + sigma * d
+            it += 1
+        q = self.acap_solve(F)
+        return OracleResult(
+            q=q.reshape(self.n, 3), F=F, iterations=it, rel_residual=res,
+            energy=float(self.energy(F, q, a)), ls_trials=trials_total, history=hist,
+            seconds=time.perf_counter() - t0,
+        )
