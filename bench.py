@@ -1,0 +1,341 @@
+"""Benchmark of the GB300 quasi-static solve (tet-iterations per second).
+
+Workload (default): the muscle-tendon unit, a 32x32x128 Kuhn-split cube grid
+masked to a cylinder (401,920 tets, 74,929 vertices). The outer 10% of its
+length is tendon (E = 1e8 Pa), the rest muscle (E = 6e5 Pa). Fibers follow
+the axis with a seeded 5-degree Gaussian tilt, and a 60-frame activation ramp
+goes from 0 to 1. Each frame is solved from the previous frame's state to a
+relative residual of 1e-6. A step is one frame. Warm-up frames come first,
+then K timed frames; the L2 cache is flushed between frames, outside the
+timed intervals.
+
+Reported:
+  value      tet-iterations/s = sum(n_tets * newton_iters) / sum(frame device time)
+  e2e        the same metric through the public API with host buffers: each
+             frame's activation upload, solve and position download inside
+             the host-clocked interval.
+  roofline   the kernel with the most device time: algorithmic bytes per
+             launch over its average CUDA-event duration, against the
+             measured HBM copy peak.
+  cpu_baseline / --impl reference: the FP64 CPU oracle on a bounded sample of
+             the same workload.
+
+Multi-GPU: one process per GPU (torchrun), each solving an independent
+replica of the workload ("replicas only": the method has no exchange step);
+max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from emu_inputs import box_beam, muscle_tendon_unit  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            pk = json.load(f)
+        for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if key in pk:
+                v = pk[key]
+                if isinstance(v, dict):
+                    v = v.get("value", v.get("gbs"))
+                return float(v), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def make_workload(name):
+    if name == "mtu":
+        mesh = muscle_tendon_unit()  # 32x32x128, r = 12.9h, 60 frames
+        desc = (f"muscle-tendon unit: 32x32x128 Kuhn grid masked to a cylinder, {mesh.n_tets} tets, "
+                f"{mesh.n_verts} verts, 10% tendon E=1e8, muscle E=6e5, nu=0.45, fibers +-5deg, "
+                f"60-frame activation ramp 0->1, warm starts, rel residual 1e-6")
+        return mesh, desc
+    if name == "box":
+        mesh = box_beam(4, 4, 16, activation=np.linspace(0.0, 0.5, 6))
+        return mesh, "box beam 4x4x16 (1,536 tets), activation ramp to 0.5, rel residual 1e-6"
+    if name == "mtu_small":
+        mesh = muscle_tendon_unit(8, 8, 32, h=0.01, radius_cells=12.9 / 4, frames=60)
+        return mesh, f"muscle-tendon unit 8x8x32 ({mesh.n_tets} tets), 60-frame ramp, rel residual 1e-6"
+    raise ValueError(name)
+
+
+def algorithmic_bytes_per_tet(phase, mixed, n_over_m, nnz_per_row):
+    """Minimum HBM bytes per tet of one launch of a per-tet phase (one pass over
+    the per-tet records; vertex arrays counted once per vertex)."""
+    tw = 4 if mixed else 8
+    rec = 16 + 72 + 8 * 8  # tet indices, D_m^-1, V, c, w, mu, lam, ka, 2 of u ... (u counted below)
+    u = 24
+    state = 72 + 48        # R, s
+    vert = 24 * n_over_m   # q gathered, each vertex once
+    if phase == "grad":
+        return rec + u + state + vert + 72 + 9 * tw + 54 * tw   # + write g, y, Uw
+    if phase == "dir":
+        return 48 * tw + 54 * tw + 9 * tw + 72 + 72 + 8 + 9 * tw + 96  # gam, Uw, y, g, Dinv, w -> d, corner terms
+    if phase == "ls":
+        return rec + u + state + 9 * tw + 2 * vert
+    if phase == "update":
+        return state + 9 * tw + state + 48 * n_over_m
+    if phase == "syrk":
+        return 54 * tw + 48 * tw + 9 * tw + 8
+    if phase == "rhs":
+        return 16 + 72 + state + 8 + 96
+    if phase == "pcg":
+        # per CG iteration and vertex: matrix (12 B/nnz + rowptr) and the
+        # x, p, r, s, u, w vectors (3 RHS) read and written once, D^-1
+        return n_over_m * (12 * nnz_per_row + 4 + 8 + 6 * 48)
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        out.update(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def cpu_baseline(workload_name, budget_s=15.0):
+    """FP64 oracle on a bounded sample of the workload (tet-iters/s)."""
+    from oracle import EmuOracle, OracleParams
+
+    if workload_name in ("mtu", "mtu_small"):
+        mesh = muscle_tendon_unit(8, 8, 32, h=0.01, radius_cells=12.9 / 4, frames=60)
+        sample = f"muscle-tendon unit 8x8x32 grid ({mesh.n_tets} tets, same construction), warm-started ramp frames"
+    else:
+        mesh = box_beam(4, 4, 16, activation=np.linspace(0.0, 0.5, 6))
+        sample = "box beam 4x4x16, ramp frames"
+    o = EmuOracle(mesh, OracleParams(alpha_rel=1.0, weight_mode=0))
+    F = None
+    t0 = time.perf_counter()
+    tets_iters = 0
+    frames = 0
+    for f in range(1, mesh.activations.shape[0]):
+        r = o.solve(mesh.activations[f], F0=F, tol=1e-6, max_newton=5000)
+        F = r.F
+        tets_iters += mesh.n_tets * r.iterations
+        frames += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    return {"value": tets_iters / dt, "unit": "tet-iters/s", "cores": cores, "kind": "oracle",
+            "sample": f"{sample}; frames 1..{frames} ({tets_iters} tet-iters, {dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.workload, budget_s=max(5.0, 60.0 * args.steps / max(args.steps, 1) / 4))
+    _, desc = make_workload(args.workload)
+    line = {"impl": "reference", "metric": "tet-iters/s", "value": cb["value"], "unit": "tet-iters/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc}, "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "tet-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mtu", choices=["mtu", "box", "mtu_small"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flush-mb", type=int, default=512)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(args.workload)  # before any GPU work (no fork after CUDA init)
+
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2006_08821_gb300 import build as b
+
+    b.build()
+    import paper_2006_08821_gb300 as emu
+
+    mesh, desc = make_workload(args.workload)
+    frames = mesh.activations.shape[0]
+    if args.warmup + args.steps > frames - 1:
+        raise SystemExit(f"workload has {frames} frames; warmup + steps must be <= {frames - 1}")
+    mixed = args.precision == "mixed"
+    stream = torch.cuda.Stream()
+    params = emu.Params(tol_rel_residual=args.tol, precision=emu.PRECISION_MIXED if mixed else emu.PRECISION_FP64)
+    t_setup = time.perf_counter()
+    solver = emu.Solver(mesh, params, stream=stream.cuda_stream, allocator=emu.TorchAllocator(local))
+    setup_s = time.perf_counter() - t_setup
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+    m, n = mesh.n_tets, mesh.n_verts
+
+    # warm-up frames 1..W (frame 0 is the unloaded state)
+    for f in range(1, 1 + args.warmup):
+        solver.set_activation(mesh.activations[f])
+        solver.solve()
+    solver.set_profiling(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    frame_ms, e2e_s, iters, resid = [], [], [], []
+    act_pinned = torch.empty(m, dtype=torch.float64).pin_memory()
+    for f in range(1 + args.warmup, 1 + args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        act_pinned.numpy()[:] = mesh.activations[f]
+        t0 = time.perf_counter()
+        solver.set_activation(act_pinned.numpy())
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = solver.solve()
+        e1.record(stream)
+        q = solver.positions()
+        t1 = time.perf_counter()
+        e1.synchronize()
+        frame_ms.append(e0.elapsed_time(e1))
+        e2e_s.append(t1 - t0)
+        iters.append(st.newton_iters)
+        resid.append(st.rel_residual)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof, launches = solver.profile()
+    total_ms = float(np.sum(frame_ms))
+    total_e2e = float(np.sum(e2e_s))
+    if dist:
+        t = torch.tensor([total_ms, total_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, total_e2e = float(t[0]), float(t[1])
+    tet_iters = float(m * np.sum(iters)) * world
+    value = tet_iters / (total_ms / 1e3)
+    e2e_value = tet_iters / total_e2e
+
+    # roofline of the dominant kernel phase
+    peak, peak_kind = hbm_peak()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (ms_tot, nl) = dom
+    nnz_per_row = 15.0
+    per = algorithmic_bytes_per_tet(name, mixed, n / m, nnz_per_row)
+    roof = None
+    if per is not None and nl > 0:
+        if name == "pcg":
+            units = m * prof["pcg"][1]  # placeholder: per-launch iterations unknown here
+            roof = None
+        else:
+            bytes_per_launch = per * m
+            achieved = bytes_per_launch / (ms_tot / nl / 1e3) / 1e9
+            roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                    "bytes_per_launch": bytes_per_launch, "avg_launch_ms": ms_tot / nl}
+    line = {
+        "metric": "tet-iters/s", "value": value, "unit": "tet-iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": desc, "precision": args.precision, "l2": f"flushed ({args.flush_mb} MB write) between steps",
+                   "tets": m, "verts": n},
+        "ms_per_converged_frame_p50": float(np.median(frame_ms)),
+        "frame_ms_p99": float(np.percentile(frame_ms, 99)),
+        "newton_iters_per_frame": [int(x) for x in iters],
+        "max_rel_residual": float(np.max(resid)),
+        "setup_s": setup_s,
+        "phase_ms": {k: round(v[0], 3) for k, v in prof.items()},
+        "phase_launches": {k: v[1] for k, v in prof.items()},
+        "roofline": roof,
+        "cpu_baseline": cb,
+        "e2e": {"value": e2e_value, "unit": "tet-iters/s", "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 24 * n},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

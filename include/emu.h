@@ -218,6 +218,35 @@ int emu_eval_stretch_terms(const double* s, const double* params, int64_t n, int
  * Outputs R (n x 9) and s (n x 6, ordering as emu_get_element_state). */
 int emu_eval_polar(const double* F, int64_t n, double* R, double* s, void* stream);
 
+/* ---- profiling ----------------------------------------------------------
+ * Kernel phases of one Newton iteration, in launch order. When profiling is
+ * on, every launch of a phase is bracketed by CUDA events on the handle's
+ * stream and its device time is accumulated; this adds event records but no
+ * synchronisation inside an iteration. */
+typedef enum {
+  EMU_PHASE_RHS = 0,      /* per tet: corner terms of G^T W (R S) (Eq. 4 RHS)   */
+  EMU_PHASE_ASSEMBLE = 1, /* per vertex: gather of corner terms (both solves)  */
+  EMU_PHASE_PCG = 2,      /* ACAP conjugate-gradient solves (Eq. 4)            */
+  EMU_PHASE_GRAD = 3,     /* per tet: gradient (Eqs. 6-7), chart factor, y      */
+  EMU_PHASE_SYRK = 4,     /* capacitance and B y partial sums (Eqs. 11-12)      */
+  EMU_PHASE_SMALL = 5,    /* single-block reductions, 48x48 Cholesky, Armijo   */
+  EMU_PHASE_DIR = 6,      /* per tet: Woodbury direction and its RHS terms      */
+  EMU_PHASE_LS = 7,       /* per tet: line-search energy differences           */
+  EMU_PHASE_UPDATE = 8,   /* per tet polar update and per vertex q update       */
+  EMU_N_PHASES = 9
+} emu_phase;
+
+/* Turns per-phase event timing on (enable != 0) or off and clears the
+ * accumulated times and launch counts. */
+int emu_set_profiling(emu_handle* h, int32_t enable);
+
+/* Reads the accumulated device milliseconds and launch counts per phase
+ * (arrays of n_phases <= EMU_N_PHASES entries, either may be NULL) and the
+ * total number of kernel launches the handle issued since profiling was
+ * last enabled (counted whether or not timing is on). */
+int emu_get_profile(emu_handle* h, double* phase_ms, int32_t* phase_launches, int32_t n_phases,
+                    int64_t* total_launches);
+
 #ifdef __cplusplus
 }
 #endif

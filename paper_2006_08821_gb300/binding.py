@@ -1,0 +1,339 @@
+"""ctypes binding of the C ABI in ``include/emu.h`` (argument marshalling only).
+
+Every computation runs in the CUDA library ``libemu_gb300.so``. This module
+loads it, mirrors the structs of the header and wraps the entry points with
+the same names. Loading fails loudly if the library is missing; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libemu_gb300.so")
+
+EMU_OK = 0
+EMU_ERR_INVALID_ARG = -1
+EMU_ERR_DEGENERATE_TET = -2
+EMU_ERR_OOM = -3
+EMU_ERR_NOT_CONVERGED = -4
+EMU_ERR_LINESEARCH = -5
+EMU_ERR_PCG = -6
+EMU_ERR_INVERTED = -7
+EMU_ERR_TIMEOUT = -8
+EMU_ERR_CUDA = -9
+EMU_ERR_NOT_IMPLEMENTED = -10
+
+PRECISION_FP64 = 0
+PRECISION_MIXED = 1
+
+# Entry points declared in include/emu.h (checked by the export test).
+EXPORTED = [
+    "emu_default_params", "emu_status_string", "emu_last_error", "emu_create", "emu_destroy",
+    "emu_set_activation", "emu_set_activation_device", "emu_solve_quasistatic", "emu_get_positions",
+    "emu_get_element_state", "emu_set_element_state", "emu_reset", "emu_get_sizes",
+    "emu_eval_stretch_terms", "emu_eval_polar", "emu_set_profiling", "emu_get_profile",
+]
+
+PHASES = ["rhs", "assemble", "pcg", "grad", "syrk", "small", "dir", "ls", "update"]
+
+
+class EmuError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class emu_allocator(C.Structure):
+    _fields_ = [
+        ("ctx", C.c_void_p),
+        ("alloc", C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)),
+        ("free", C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)),
+    ]
+
+
+class emu_mesh_desc(C.Structure):
+    _fields_ = [
+        ("n_verts", C.c_int64),
+        ("n_tets", C.c_int64),
+        ("rest_pos", C.POINTER(C.c_double)),
+        ("tets", C.POINTER(C.c_int32)),
+        ("n_materials", C.c_int32),
+        ("youngs", C.POINTER(C.c_double)),
+        ("poisson", C.POINTER(C.c_double)),
+        ("material_id", C.POINTER(C.c_uint8)),
+        ("fiber_dir", C.POINTER(C.c_double)),
+        ("n_fixed", C.c_int64),
+        ("fixed_verts", C.POINTER(C.c_int32)),
+        ("fixed_pos", C.POINTER(C.c_double)),
+    ]
+
+
+class emu_params(C.Structure):
+    _fields_ = [
+        ("alpha_rel", C.c_double),
+        ("weight_mode", C.c_int32),
+        ("k_modes", C.c_int32),
+        ("fiber_scale", C.c_double),
+        ("tol_rel_residual", C.c_double),
+        ("max_newton", C.c_int32),
+        ("ls_sigma0", C.c_double),
+        ("ls_c", C.c_double),
+        ("ls_rho", C.c_double),
+        ("ls_max_trials", C.c_int32),
+        ("pcg_tol", C.c_double),
+        ("pcg_max", C.c_int32),
+        ("precision", C.c_int32),
+        ("mode_iters", C.c_int32),
+        ("seed", C.c_uint64),
+    ]
+
+
+class emu_solve_stats(C.Structure):
+    _fields_ = [
+        ("newton_iters", C.c_int32),
+        ("ls_trials", C.c_int32),
+        ("pcg_iters", C.c_int32),
+        ("status", C.c_int32),
+        ("rel_residual", C.c_double),
+        ("energy_change", C.c_double),
+        ("ms", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2006_08821_gb300.build.build() "
+                           "(needs nvcc); there is no CPU fallback")
+    lib = C.CDLL(path)
+    P = C.POINTER
+    lib.emu_default_params.argtypes = [P(emu_params)]
+    lib.emu_default_params.restype = None
+    lib.emu_status_string.argtypes = [C.c_int]
+    lib.emu_status_string.restype = C.c_char_p
+    lib.emu_last_error.argtypes = []
+    lib.emu_last_error.restype = C.c_char_p
+    lib.emu_create.argtypes = [P(emu_mesh_desc), P(emu_params), P(emu_allocator), C.c_void_p, P(C.c_void_p)]
+    lib.emu_destroy.argtypes = [C.c_void_p]
+    lib.emu_set_activation.argtypes = [C.c_void_p, P(C.c_double), C.c_int64]
+    lib.emu_set_activation_device.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    lib.emu_solve_quasistatic.argtypes = [C.c_void_p, P(emu_solve_stats)]
+    lib.emu_get_positions.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
+    lib.emu_get_element_state.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double), P(C.c_double)]
+    lib.emu_set_element_state.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double), P(C.c_double)]
+    lib.emu_reset.argtypes = [C.c_void_p]
+    lib.emu_get_sizes.argtypes = [C.c_void_p, P(C.c_int64), P(C.c_int64), P(C.c_int32)]
+    lib.emu_eval_stretch_terms.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.emu_eval_polar.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.emu_set_profiling.argtypes = [C.c_void_p, C.c_int32]
+    lib.emu_get_profile.argtypes = [C.c_void_p, P(C.c_double), P(C.c_int32), C.c_int32, P(C.c_int64)]
+    for name in EXPORTED:
+        if name not in ("emu_default_params", "emu_status_string", "emu_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc, lib=None):
+    if rc != EMU_OK:
+        lib = lib or load_library()
+        raise EmuError(rc, f"{lib.emu_status_string(rc).decode()}: {lib.emu_last_error().decode()}")
+
+
+def _dptr(a, dtype):
+    """Host pointer of a C-contiguous numpy array of the given dtype (kept alive by the caller)."""
+    return a.ctypes.data_as(C.POINTER(dtype))
+
+
+@dataclasses.dataclass
+class Params:
+    """Mirror of emu_params with the library defaults."""
+    alpha_rel: float = 1.0
+    weight_mode: int = 0
+    k_modes: int = 48
+    fiber_scale: float = 1.0
+    tol_rel_residual: float = 1e-6
+    max_newton: int = 2000
+    ls_sigma0: float = 1.0
+    ls_c: float = 1e-4
+    ls_rho: float = 0.5
+    ls_max_trials: int = 40
+    pcg_tol: float = 1e-12
+    pcg_max: int = 5000
+    precision: int = PRECISION_FP64
+    mode_iters: int = 4
+    seed: int = 12345
+
+    def to_c(self) -> emu_params:
+        p = emu_params()
+        for f in dataclasses.fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+def default_params() -> Params:
+    lib = load_library()
+    p = emu_params()
+    lib.emu_default_params(C.byref(p))
+    return Params(**{f.name: getattr(p, f.name) for f in dataclasses.fields(Params)})
+
+
+class TorchAllocator:
+    """Routes the library's device allocations to PyTorch's caching allocator."""
+
+    def __init__(self, device=0):
+        import torch
+
+        self._torch = torch
+        self.device = device
+        AF = emu_allocator._fields_[1][1]
+        FF = emu_allocator._fields_[2][1]
+
+        def _alloc(ctx, size, stream):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(size), self.device, stream))
+            except Exception:  # pragma: no cover - OOM path
+                return None
+
+        def _free(ctx, ptr, size, stream):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._af = AF(_alloc)
+        self._ff = FF(_free)
+        self.struct = emu_allocator(None, self._af, self._ff)
+
+
+class Solver:
+    """One mesh resident on the GPU (wraps emu_create ... emu_destroy)."""
+
+    def __init__(self, mesh, params: Params | None = None, stream=None, allocator=None):
+        self.lib = load_library()
+        self.params = params or Params()
+        self._keep = []
+        Q = np.ascontiguousarray(mesh.rest_pos, dtype=np.float64)
+        T = np.ascontiguousarray(mesh.tets, dtype=np.int32)
+        E = np.ascontiguousarray(mesh.youngs, dtype=np.float64)
+        nu = np.ascontiguousarray(mesh.poisson, dtype=np.float64)
+        mid = np.ascontiguousarray(mesh.material_id, dtype=np.uint8)
+        fib = None if mesh.fiber_dir is None else np.ascontiguousarray(mesh.fiber_dir, dtype=np.float64)
+        fx = np.ascontiguousarray(mesh.fixed_verts, dtype=np.int32)
+        fp = None if getattr(mesh, "fixed_pos", None) is None else np.ascontiguousarray(mesh.fixed_pos, dtype=np.float64)
+        self._keep += [Q, T, E, nu, mid, fib, fx, fp]
+        d = emu_mesh_desc()
+        d.n_verts = Q.shape[0]
+        d.n_tets = T.shape[0]
+        d.rest_pos = _dptr(Q, C.c_double)
+        d.tets = _dptr(T, C.c_int32)
+        d.n_materials = E.shape[0]
+        d.youngs = _dptr(E, C.c_double)
+        d.poisson = _dptr(nu, C.c_double)
+        d.material_id = _dptr(mid, C.c_uint8)
+        d.fiber_dir = _dptr(fib, C.c_double) if fib is not None else None
+        d.n_fixed = fx.shape[0]
+        d.fixed_verts = _dptr(fx, C.c_int32)
+        d.fixed_pos = _dptr(fp, C.c_double) if fp is not None else None
+        self.n_verts = int(d.n_verts)
+        self.n_tets = int(d.n_tets)
+        self.stream = stream
+        st = None if stream is None else C.c_void_p(int(stream))
+        self._allocator = allocator
+        ap = C.byref(allocator.struct) if allocator is not None else None
+        h = C.c_void_p()
+        cp = self.params.to_c()
+        _check(self.lib.emu_create(C.byref(d), C.byref(cp), ap, st, C.byref(h)), self.lib)
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.emu_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_activation(self, a):
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (self.n_tets,)))
+        _check(self.lib.emu_set_activation(self.handle, _dptr(a, C.c_double), a.shape[0]), self.lib)
+
+    def set_activation_device(self, a_dev_ptr: int):
+        _check(self.lib.emu_set_activation_device(self.handle, C.c_void_p(a_dev_ptr), self.n_tets), self.lib)
+
+    def solve(self, raise_on_error=True) -> emu_solve_stats:
+        st = emu_solve_stats()
+        rc = self.lib.emu_solve_quasistatic(self.handle, C.byref(st))
+        if raise_on_error and rc not in (EMU_OK,):
+            _check(rc, self.lib)
+        st.status = rc
+        return st
+
+    def positions(self) -> np.ndarray:
+        out = np.empty((self.n_verts, 3), dtype=np.float64)
+        _check(self.lib.emu_get_positions(self.handle, out.ctypes.data_as(C.c_void_p), 0), self.lib)
+        return out
+
+    def positions_to_device(self, dev_ptr: int):
+        _check(self.lib.emu_get_positions(self.handle, C.c_void_p(dev_ptr), 1), self.lib)
+
+    def element_state(self):
+        R = np.empty((self.n_tets, 3, 3))
+        s = np.empty((self.n_tets, 6))
+        F = np.empty((self.n_tets, 3, 3))
+        _check(self.lib.emu_get_element_state(self.handle, _dptr(R, C.c_double), _dptr(s, C.c_double),
+                                              _dptr(F, C.c_double)), self.lib)
+        return R, s, F
+
+    def set_element_state(self, R=None, s=None, q=None):
+        arrs = [None if x is None else np.ascontiguousarray(x, dtype=np.float64) for x in (R, s, q)]
+        ptrs = [None if x is None else _dptr(x, C.c_double) for x in arrs]
+        _check(self.lib.emu_set_element_state(self.handle, *ptrs), self.lib)
+
+    def reset(self):
+        _check(self.lib.emu_reset(self.handle), self.lib)
+
+    def set_profiling(self, enable: bool):
+        _check(self.lib.emu_set_profiling(self.handle, 1 if enable else 0), self.lib)
+
+    def profile(self):
+        """(dict phase -> (ms, launches), total launches) since profiling was enabled."""
+        n = len(PHASES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int32 * n)()
+        tot = C.c_int64()
+        _check(self.lib.emu_get_profile(self.handle, ms, cnt, n, C.byref(tot)), self.lib)
+        return {PHASES[k]: (ms[k], cnt[k]) for k in range(n)}, tot.value
+
+    def sizes(self):
+        n = C.c_int64()
+        m = C.c_int64()
+        k = C.c_int32()
+        _check(self.lib.emu_get_sizes(self.handle, C.byref(n), C.byref(m), C.byref(k)), self.lib)
+        return n.value, m.value, k.value
+
+
+def eval_stretch_terms(s_dev, params_dev, n, mixed, psi_dev, grad_dev, hess_dev, stream=0):
+    """emu_eval_stretch_terms on device pointers (ints)."""
+    lib = load_library()
+    cv = lambda x: None if x is None else C.c_void_p(int(x))  # noqa: E731
+    _check(lib.emu_eval_stretch_terms(cv(s_dev), cv(params_dev), n, mixed, cv(psi_dev), cv(grad_dev),
+                                      cv(hess_dev), cv(stream)), lib)
+
+
+def eval_polar(F_dev, n, R_dev, s_dev, stream=0):
+    lib = load_library()
+    _check(lib.emu_eval_polar(C.c_void_p(int(F_dev)), n, C.c_void_p(int(R_dev)), C.c_void_p(int(s_dev)),
+                              C.c_void_p(int(stream))), lib)

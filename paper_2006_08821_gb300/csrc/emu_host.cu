@@ -1,0 +1,1031 @@
+// Host side of the C ABI declared in include/emu.h: mesh setup, the Newton
+// loop of Algorithm 1 (arXiv 2006.08821) and the entry points.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "emu_internal.h"
+#include "emu_kernels.cuh"
+#include "emu_pcg.h"
+
+using namespace emu;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define EMU_CK(call)                                                                           \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(EMU_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DevBuf {
+  void* p;
+  size_t bytes;
+};
+
+}  // namespace
+
+struct emu_handle {
+  emu_params prm;
+  emu_allocator alloc;
+  bool has_alloc = false;
+  cudaStream_t st = nullptr;
+  int64_t n = 0, m = 0;
+  int sms = 0;
+  int kmodes = 16;
+  bool mixed = false;
+  std::vector<DevBuf> bufs;
+
+  double mu_ref = 0, alpha = 0, kappa = 0;
+  double gref = 0;  // ||g(I)||
+  bool gref_valid = false;
+  double floor = 0;  // 1e-12 sqrt(sum (V mu)^2)
+  std::vector<double> V_h;
+
+  // device arrays
+  int4* tet = nullptr;
+  double *Dinv = nullptr, *V = nullptr, *c = nullptr, *w = nullptr, *mu = nullptr, *lam = nullptr, *u = nullptr,
+         *ka = nullptr;
+  double* gam64 = nullptr;
+  float* gam32 = nullptr;
+  double *R = nullptr, *s = nullptr, *q = nullptr, *dq = nullptr, *q0 = nullptr, *g = nullptr;
+  double *y64 = nullptr, *d64 = nullptr, *Uw64 = nullptr;
+  float *y32 = nullptr, *d32 = nullptr, *Uw32 = nullptr;
+  double* contrib = nullptr;
+  double* b = nullptr;
+  double *pr = nullptr, *pu = nullptr, *pw = nullptr, *pp = nullptr, *ps = nullptr;
+  double *part_grad = nullptr, *part_dir = nullptr, *part_ls = nullptr, *part_pcg = nullptr, *cpart = nullptr;
+  double* z = nullptr;
+  double* scratch16 = nullptr;  // n x 16 mode vectors
+  double* small = nullptr;      // 256 doubles of small-matrix exchange
+  DevScalars* sc = nullptr;
+  DevScalars* sc_host = nullptr;  // pinned
+  GridBarrier* bar = nullptr;
+  // Laplacian and pins
+  int32_t *rowptr = nullptr, *col = nullptr;
+  double *val = nullptr, *ldinv = nullptr, *bfix = nullptr, *qfix = nullptr;
+  uint8_t* is_fixed = nullptr;
+  int32_t *slot_ptr = nullptr, *slot_idx = nullptr;
+  // launch shapes
+  int grid_tet = 1, grid_syrk = 1, grid_pcg3 = 1, grid_pcg16 = 1;
+
+  // profiling: event pairs per phase, resolved at the next host sync
+  struct Pending {
+    int phase;
+    int launches;
+    cudaEvent_t e0, e1;
+  };
+  bool prof_on = false;
+  double prof_ms[EMU_N_PHASES] = {0};
+  int32_t prof_cnt[EMU_N_PHASES] = {0};
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<Pending> pending;
+  cudaEvent_t cur_e0 = nullptr;
+
+  cudaEvent_t ev_get() {
+    if (!ev_pool.empty()) {
+      cudaEvent_t e = ev_pool.back();
+      ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void ph_begin() {
+    if (!prof_on) return;
+    cur_e0 = ev_get();
+    cudaEventRecord(cur_e0, st);
+  }
+  void ph_end(int phase, int nlaunch) {
+    launches += nlaunch;
+    if (!prof_on) return;
+    cudaEvent_t e1 = ev_get();
+    cudaEventRecord(e1, st);
+    pending.push_back({phase, nlaunch, cur_e0, e1});
+  }
+  // call after the stream was synchronised
+  void prof_flush() {
+    for (auto& p_ : pending) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, p_.e0, p_.e1);
+      prof_ms[p_.phase] += ms;
+      prof_cnt[p_.phase] += p_.launches;
+      ev_pool.push_back(p_.e0);
+      ev_pool.push_back(p_.e1);
+    }
+    pending.clear();
+  }
+  void prof_destroy() {
+    prof_flush();
+    for (auto e : ev_pool) cudaEventDestroy(e);
+    ev_pool.clear();
+  }
+
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (has_alloc) {
+      p = alloc.alloc(alloc.ctx, bytes, (void*)st);
+    } else {
+      if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    }
+    if (p) bufs.push_back({p, bytes});
+    return p;
+  }
+  template <typename T> bool get(T*& out, size_t count) {
+    out = static_cast<T*>(dalloc(count * sizeof(T)));
+    return out != nullptr;
+  }
+  void release() {
+    if (st) cudaStreamSynchronize(st);
+    prof_destroy();
+    for (auto& b_ : bufs) {
+      if (has_alloc)
+        alloc.free(alloc.ctx, b_.p, b_.bytes, (void*)st);
+      else
+        cudaFree(b_.p);
+    }
+    bufs.clear();
+    if (sc_host) cudaFreeHost(sc_host);
+    sc_host = nullptr;
+  }
+
+  template <typename TW> TetArgs<TW> args();
+
+  PcgArgs pcg_args(const double* rhs, double* x, int nrhs) {
+    PcgArgs a;
+    a.L.n = n;
+    a.L.rowptr = rowptr;
+    a.L.col = col;
+    a.L.val = val;
+    a.L.dinv = ldinv;
+    a.b = rhs;
+    a.x = x;
+    a.r = pr;
+    a.u = pu;
+    a.w = pw;
+    a.p = pp;
+    a.s = ps;
+    a.partials = part_pcg;
+    a.bar = bar;
+    a.tol = prm.pcg_tol;
+    a.max_iter = prm.pcg_max;
+    a.iters_out = &sc->pcg_iters;
+    a.fail_out = &sc->pcg_fail;
+    a.timeout_out = &sc->barrier_timeout;
+    a.last_iters = nullptr;
+    (void)nrhs;
+    return a;
+  }
+};
+
+template <> TetArgs<double> emu_handle::args<double>() {
+  TetArgs<double> a;
+  a.m = m;
+  a.n = n;
+  a.tet = tet;
+  a.Dinv = Dinv;
+  a.V = V;
+  a.c = c;
+  a.w = w;
+  a.mu = mu;
+  a.lam = lam;
+  a.u = u;
+  a.ka = ka;
+  a.gam = gam64;
+  a.R = R;
+  a.s = s;
+  a.q = q;
+  a.dq = dq;
+  a.g = g;
+  a.y = y64;
+  a.d = d64;
+  a.Uw = Uw64;
+  a.contrib = contrib;
+  a.z = z;
+  a.sc = sc;
+  a.partials = part_grad;
+  return a;
+}
+template <> TetArgs<float> emu_handle::args<float>() {
+  TetArgs<float> a;
+  a.m = m;
+  a.n = n;
+  a.tet = tet;
+  a.Dinv = Dinv;
+  a.V = V;
+  a.c = c;
+  a.w = w;
+  a.mu = mu;
+  a.lam = lam;
+  a.u = u;
+  a.ka = ka;
+  a.gam = gam32;
+  a.R = R;
+  a.s = s;
+  a.q = q;
+  a.dq = dq;
+  a.g = g;
+  a.y = y32;
+  a.d = d32;
+  a.Uw = Uw32;
+  a.contrib = contrib;
+  a.z = z;
+  a.sc = sc;
+  a.partials = part_grad;
+  return a;
+}
+
+namespace {
+
+uint64_t splitmix64(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric N x N matrix (row-major):
+// A is overwritten (its diagonal holds the eigenvalues), V receives the
+// eigenvectors as columns.
+void host_jacobi_eig(std::vector<double>& A, std::vector<double>& V, int N) {
+  V.assign(N * N, 0.0);
+  for (int i = 0; i < N; ++i) V[N * i + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        tot += A[N * i + j] * A[N * i + j];
+        if (i != j) off += A[N * i + j] * A[N * i + j];
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < N; ++p)
+      for (int q = p + 1; q < N; ++q) {
+        const double apq = A[N * p + q];
+        if (apq == 0.0) continue;
+        const double theta = (A[N * q + q] - A[N * p + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s_ = t * c;
+        for (int k = 0; k < N; ++k) {  // A <- J^T A J
+          const double akp = A[N * k + p], akq = A[N * k + q];
+          A[N * k + p] = c * akp - s_ * akq;
+          A[N * k + q] = s_ * akp + c * akq;
+        }
+        for (int k = 0; k < N; ++k) {
+          const double apk = A[N * p + k], aqk = A[N * q + k];
+          A[N * p + k] = c * apk - s_ * aqk;
+          A[N * q + k] = s_ * apk + c * aqk;
+        }
+        for (int k = 0; k < N; ++k) {
+          const double vkp = V[N * k + p], vkq = V[N * k + q];
+          V[N * k + p] = c * vkp - s_ * vkq;
+          V[N * k + q] = s_ * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+int validate_mesh(const emu_mesh_desc* d) {
+  if (!d) return fail(EMU_ERR_INVALID_ARG, "mesh is NULL");
+  if (d->n_verts < 4 || d->n_tets < 1) return fail(EMU_ERR_INVALID_ARG, "need n_verts >= 4 and n_tets >= 1");
+  if (d->n_verts > (int64_t)1 << 30 || d->n_tets > (int64_t)1 << 28)
+    return fail(EMU_ERR_INVALID_ARG, "mesh too large for 32-bit indexing");
+  if (!d->rest_pos || !d->tets || !d->youngs || !d->poisson || !d->material_id)
+    return fail(EMU_ERR_INVALID_ARG, "missing mesh array");
+  if (d->n_materials < 1) return fail(EMU_ERR_INVALID_ARG, "n_materials < 1");
+  for (int32_t k = 0; k < d->n_materials; ++k) {
+    if (!(d->youngs[k] > 0.0) || !std::isfinite(d->youngs[k])) return fail(EMU_ERR_INVALID_ARG, "youngs must be > 0");
+    if (!(d->poisson[k] >= 0.0 && d->poisson[k] < 0.5)) return fail(EMU_ERR_INVALID_ARG, "poisson must be in [0, 0.5)");
+  }
+  for (int64_t i = 0; i < 4 * d->n_tets; ++i)
+    if (d->tets[i] < 0 || d->tets[i] >= d->n_verts) return fail(EMU_ERR_INVALID_ARG, "tet index out of range");
+  for (int64_t i = 0; i < d->n_tets; ++i)
+    if (d->material_id[i] >= d->n_materials) return fail(EMU_ERR_INVALID_ARG, "material_id out of range");
+  if (d->n_fixed < 1 || !d->fixed_verts) return fail(EMU_ERR_INVALID_ARG, "at least one pinned vertex is required");
+  for (int64_t i = 0; i < d->n_fixed; ++i)
+    if (d->fixed_verts[i] < 0 || d->fixed_verts[i] >= d->n_verts) return fail(EMU_ERR_INVALID_ARG, "fixed vertex out of range");
+  for (int64_t i = 0; i < 3 * d->n_verts; ++i)
+    if (!std::isfinite(d->rest_pos[i])) return fail(EMU_ERR_INVALID_ARG, "non-finite rest position");
+  return EMU_OK;
+}
+
+int validate_params(const emu_params* p) {
+  if (!(p->alpha_rel > 0.0) || !std::isfinite(p->alpha_rel)) return fail(EMU_ERR_INVALID_ARG, "alpha_rel must be > 0");
+  if (p->weight_mode != 0 && p->weight_mode != 1) return fail(EMU_ERR_INVALID_ARG, "weight_mode must be 0 or 1");
+  if (p->k_modes < 3 || p->k_modes > 48 || p->k_modes % 3) return fail(EMU_ERR_INVALID_ARG, "k_modes must be 3..48, multiple of 3");
+  if (!(p->fiber_scale >= 0.0)) return fail(EMU_ERR_INVALID_ARG, "fiber_scale must be >= 0");
+  if (!(p->tol_rel_residual >= 0.0)) return fail(EMU_ERR_INVALID_ARG, "tol_rel_residual must be >= 0");
+  if (p->max_newton < 0) return fail(EMU_ERR_INVALID_ARG, "max_newton must be >= 0");
+  if (!(p->ls_sigma0 > 0.0) || !(p->ls_rho > 0.0 && p->ls_rho < 1.0) || !(p->ls_c > 0.0 && p->ls_c < 1.0))
+    return fail(EMU_ERR_INVALID_ARG, "bad line-search constants");
+  if (p->ls_max_trials < 1) return fail(EMU_ERR_INVALID_ARG, "ls_max_trials must be >= 1");
+  if (!(p->pcg_tol > 0.0 && p->pcg_tol < 1.0) || p->pcg_max < 1) return fail(EMU_ERR_INVALID_ARG, "bad pcg settings");
+  if (p->precision != EMU_PRECISION_FP64 && p->precision != EMU_PRECISION_MIXED)
+    return fail(EMU_ERR_INVALID_ARG, "precision must be FP64 or MIXED");
+  if (p->mode_iters < 1 || p->mode_iters > 50) return fail(EMU_ERR_INVALID_ARG, "mode_iters must be 1..50");
+  return EMU_OK;
+}
+
+// Runs the coupling solve q = q*(R S) with q as the warm start.
+int coupling_solve(emu_handle* h) {
+  TetArgs<double> a = h->args<double>();
+  h->ph_begin();
+  launch_rhs_from_state(a, h->grid_tet, h->st);
+  h->ph_end(EMU_PHASE_RHS, 1);
+  h->ph_begin();
+  launch_assemble(h->n, h->slot_ptr, h->slot_idx, h->contrib, h->bfix, h->is_fixed, h->qfix, 0, h->b, h->st);
+  h->ph_end(EMU_PHASE_ASSEMBLE, 1);
+  EMU_CK(cudaGetLastError());
+  h->ph_begin();
+  EMU_CK(launch_pcg(3, h->pcg_args(h->b, h->q, 3), h->grid_pcg3, h->st));
+  h->ph_end(EMU_PHASE_PCG, 1);
+  return EMU_OK;
+}
+
+int set_rest_state(emu_handle* h) {
+  std::vector<double> Rh(9 * h->m, 0.0), sh(6 * h->m, 0.0);
+  for (int64_t i = 0; i < h->m; ++i) {
+    Rh[0 * h->m + i] = Rh[4 * h->m + i] = Rh[8 * h->m + i] = 1.0;
+    sh[0 * h->m + i] = sh[1 * h->m + i] = sh[2 * h->m + i] = 1.0;
+  }
+  EMU_CK(cudaMemcpyAsync(h->R, Rh.data(), Rh.size() * 8, cudaMemcpyHostToDevice, h->st));
+  EMU_CK(cudaMemcpyAsync(h->s, sh.data(), sh.size() * 8, cudaMemcpyHostToDevice, h->st));
+  EMU_CK(cudaMemsetAsync(h->dq, 0, 3 * h->n * 8, h->st));
+  EMU_CK(cudaStreamSynchronize(h->st));
+  return EMU_OK;
+}
+
+int read_scalars(emu_handle* h) {
+  EMU_CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st));
+  EMU_CK(cudaStreamSynchronize(h->st));
+  h->prof_flush();
+  return EMU_OK;
+}
+
+// Low-rank basis of Eq. 9: block inverse (subspace) iteration on the scalar
+// ACAP Laplacian, X <- orth(L^-1 X), from a seeded random start. Any
+// full-rank basis keeps the quasi-Newton matrix positive definite; better
+// approximations of the lowest eigenvectors only speed up convergence.
+int build_modes(emu_handle* h) {
+  const int64_t n = h->n;
+  std::vector<double> X(n * 16, 0.0);
+  std::vector<uint8_t> fixed(n);
+  EMU_CK(cudaMemcpy(fixed.data(), h->is_fixed, n, cudaMemcpyDeviceToHost));
+  uint64_t seed = h->prm.seed ^ 0x5EEDF00Dull;
+  for (int64_t v = 0; v < n; ++v)
+    for (int j = 0; j < 16; ++j) {
+      double r = (double)(splitmix64(seed) >> 11) * (1.0 / 9007199254740992.0);
+      X[v * 16 + j] = fixed[v] ? 0.0 : 2.0 * r - 1.0;
+    }
+  double* Xd = h->scratch16;
+  double* Yd = h->scratch16 + n * 16;
+  EMU_CK(cudaMemcpyAsync(Xd, X.data(), X.size() * 8, cudaMemcpyHostToDevice, h->st));
+  const int ggrid = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 511) / 512), 2 * h->sms);
+  for (int it = 0; it < h->prm.mode_iters; ++it) {
+    // Y = L^-1 X (pinned rows: right-hand side 0)
+    EMU_CK(cudaMemsetAsync(Yd, 0, n * 16 * 8, h->st));
+    PcgArgs a = h->pcg_args(Xd, Yd, 16);
+    a.tol = 1e-6;
+    a.max_iter = std::max(h->prm.pcg_max, 1000);
+    a.iters_out = nullptr;
+    a.fail_out = nullptr;
+    EMU_CK(launch_pcg(16, a, h->grid_pcg16, h->st));
+    // orthonormalise: Y^T Y = L L^T, X = Y L^-T
+    launch_gram16(n, Yd, ggrid, h->part_pcg, h->st);
+    launch_reduce_cols(h->part_pcg, ggrid, 256, h->small, h->st);
+    std::vector<double> Gm(256);
+    EMU_CK(cudaMemcpyAsync(Gm.data(), h->small, 256 * 8, cudaMemcpyDeviceToHost, h->st));
+    EMU_CK(cudaStreamSynchronize(h->st));
+    for (int i = 0; i < 16; ++i)
+      for (int j = 0; j < 16; ++j) Gm[16 * i + j] = 0.5 * (Gm[16 * i + j] + Gm[16 * j + i]);
+    // X = Y T with T = V diag(lambda^-1/2): orthonormal columns; directions
+    // with a negligible Gram eigenvalue (fewer free vertices than modes)
+    // are dropped as zero columns.
+    std::vector<double> Ev;
+    host_jacobi_eig(Gm, Ev, 16);
+    double lmax = 0.0;
+    for (int i = 0; i < 16; ++i) lmax = std::max(lmax, Gm[17 * i]);
+    if (!(lmax > 0.0)) return fail(EMU_ERR_CUDA, "mode basis is empty");
+    std::vector<double> T(256, 0.0);
+    for (int j = 0; j < 16; ++j) {
+      const double lj = Gm[17 * j];
+      if (!(lj > 1e-12 * lmax)) continue;
+      const double sc_ = 1.0 / std::sqrt(lj);
+      for (int i = 0; i < 16; ++i) T[16 * i + j] = Ev[16 * i + j] * sc_;
+    }
+    // drop unused modes (k_modes < 48) after the last iteration
+    if (it + 1 == h->prm.mode_iters)
+      for (int i = 0; i < 16; ++i)
+        for (int j = h->kmodes; j < 16; ++j) T[16 * i + j] = 0.0;
+    EMU_CK(cudaMemcpyAsync(h->small, T.data(), 256 * 8, cudaMemcpyHostToDevice, h->st));
+    EMU_CK(cudaMemcpyAsync(Xd, Yd, n * 16 * 8, cudaMemcpyDeviceToDevice, h->st));
+    launch_xform16(n, h->small, Xd, h->st);
+    EMU_CK(cudaGetLastError());
+    EMU_CK(cudaStreamSynchronize(h->st));
+  }
+  if (h->mixed)
+    launch_gamma<float>(h->m, h->tet, h->Dinv, Xd, h->gam32, h->st);
+  else
+    launch_gamma<double>(h->m, h->tet, h->Dinv, Xd, h->gam64, h->st);
+  EMU_CK(cudaGetLastError());
+  EMU_CK(cudaStreamSynchronize(h->st));
+  return EMU_OK;
+}
+
+int compute_gref(emu_handle* h) {
+  TetArgs<double> a = h->args<double>();
+  launch_gref(a, h->q0, h->grid_tet, h->part_grad, h->small, h->st);
+  double g2 = 0.0;
+  EMU_CK(cudaMemcpyAsync(&g2, h->small, 8, cudaMemcpyDeviceToHost, h->st));
+  EMU_CK(cudaStreamSynchronize(h->st));
+  h->gref = std::sqrt(g2);
+  h->gref_valid = true;
+  return EMU_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI =====
+extern "C" {
+
+void emu_default_params(emu_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->alpha_rel = 1.0;
+  p->weight_mode = 0;
+  p->k_modes = 48;
+  p->fiber_scale = 1.0;
+  p->tol_rel_residual = 1e-6;
+  p->max_newton = 2000;
+  p->ls_sigma0 = 1.0;
+  p->ls_c = 1e-4;
+  p->ls_rho = 0.5;
+  p->ls_max_trials = 40;
+  p->pcg_tol = 1e-12;
+  p->pcg_max = 5000;
+  p->precision = EMU_PRECISION_FP64;
+  p->mode_iters = 4;
+  p->seed = 12345;
+}
+
+const char* emu_status_string(int status) {
+  switch (status) {
+    case EMU_OK: return "ok";
+    case EMU_ERR_INVALID_ARG: return "invalid argument";
+    case EMU_ERR_DEGENERATE_TET: return "degenerate tet";
+    case EMU_ERR_OOM: return "out of device memory";
+    case EMU_ERR_NOT_CONVERGED: return "not converged";
+    case EMU_ERR_LINESEARCH: return "line search failed";
+    case EMU_ERR_PCG: return "ACAP solve did not converge";
+    case EMU_ERR_INVERTED: return "non-finite gradient or inverted element";
+    case EMU_ERR_TIMEOUT: return "device wait timed out";
+    case EMU_ERR_CUDA: return "CUDA error";
+    case EMU_ERR_NOT_IMPLEMENTED: return "not implemented";
+    default: return "unknown status";
+  }
+}
+
+const char* emu_last_error(void) { return g_last_error.c_str(); }
+
+int emu_destroy(emu_handle* h) {
+  if (!h) return EMU_OK;
+  h->release();
+  delete h;
+  return EMU_OK;
+}
+
+int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_allocator* alloc, void* stream,
+               emu_handle** out) {
+  if (!out) return fail(EMU_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = validate_mesh(desc);
+  if (rc) return rc;
+  emu_params prm;
+  if (params)
+    prm = *params;
+  else
+    emu_default_params(&prm);
+  rc = validate_params(&prm);
+  if (rc) return rc;
+
+  emu_handle* h = new (std::nothrow) emu_handle();
+  if (!h) return fail(EMU_ERR_OOM, "host allocation failed");
+  h->prm = prm;
+  h->st = (cudaStream_t)stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    h->alloc = *alloc;
+    h->has_alloc = true;
+  }
+  h->mixed = prm.precision == EMU_PRECISION_MIXED;
+  h->kmodes = prm.k_modes / 3;
+  const int64_t n = desc->n_verts, m = desc->n_tets;
+  h->n = n;
+  h->m = m;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    delete h;
+    return fail(EMU_ERR_CUDA, "no CUDA device");
+  }
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+
+  // ---- geometry (Eq. 2), volumes, orientation ----
+  const double* Q = desc->rest_pos;
+  std::vector<int32_t> tet(4 * m);
+  std::vector<double> Dinv(9 * m), V(m);
+  for (int64_t i = 0; i < m; ++i) {
+    int32_t t[4] = {desc->tets[4 * i], desc->tets[4 * i + 1], desc->tets[4 * i + 2], desc->tets[4 * i + 3]};
+    auto build = [&](double* Dm) {
+      for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) Dm[3 * r + k] = Q[3 * t[k] + r] - Q[3 * t[3] + r];
+    };
+    double Dm[9];
+    build(Dm);
+    double det = Dm[0] * (Dm[4] * Dm[8] - Dm[5] * Dm[7]) - Dm[1] * (Dm[3] * Dm[8] - Dm[5] * Dm[6]) +
+                 Dm[2] * (Dm[3] * Dm[7] - Dm[4] * Dm[6]);
+    if (det < 0.0) {
+      std::swap(t[1], t[2]);
+      build(Dm);
+      det = -det;
+    }
+    double hmax = 0.0;
+    for (int a_ = 0; a_ < 4; ++a_)
+      for (int b_ = a_ + 1; b_ < 4; ++b_) {
+        double dx = Q[3 * t[a_]] - Q[3 * t[b_]], dy = Q[3 * t[a_] + 1] - Q[3 * t[b_] + 1],
+               dz = Q[3 * t[a_] + 2] - Q[3 * t[b_] + 2];
+        hmax = std::max(hmax, std::sqrt(dx * dx + dy * dy + dz * dz));
+      }
+    if (!(det > 1e-14 * hmax * hmax * hmax)) {
+      delete h;
+      return fail(EMU_ERR_DEGENERATE_TET, "degenerate tet " + std::to_string(i));
+    }
+    double Di[9];
+    Di[0] = (Dm[4] * Dm[8] - Dm[5] * Dm[7]) / det;
+    Di[1] = (Dm[2] * Dm[7] - Dm[1] * Dm[8]) / det;
+    Di[2] = (Dm[1] * Dm[5] - Dm[2] * Dm[4]) / det;
+    Di[3] = (Dm[5] * Dm[6] - Dm[3] * Dm[8]) / det;
+    Di[4] = (Dm[0] * Dm[8] - Dm[2] * Dm[6]) / det;
+    Di[5] = (Dm[2] * Dm[3] - Dm[0] * Dm[5]) / det;
+    Di[6] = (Dm[3] * Dm[7] - Dm[4] * Dm[6]) / det;
+    Di[7] = (Dm[1] * Dm[6] - Dm[0] * Dm[7]) / det;
+    Di[8] = (Dm[0] * Dm[4] - Dm[1] * Dm[3]) / det;
+    for (int k = 0; k < 9; ++k) Dinv[k * m + i] = Di[k];
+    V[i] = det / 6.0;
+    for (int k = 0; k < 4; ++k) tet[4 * i + k] = t[k];
+  }
+
+  // ---- materials, weights (Eq. 3 with the Sec. 3.3 weights option) ----
+  std::vector<double> mu(m), lam(m), wv(m), cv(m), uv(3 * m, 0.0);
+  double mu_ref = 1e300;
+  for (int64_t i = 0; i < m; ++i) {
+    const int k = desc->material_id[i];
+    const double E = desc->youngs[k], nu = desc->poisson[k];
+    mu[i] = E / (2.0 * (1.0 + nu));
+    lam[i] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    mu_ref = std::min(mu_ref, mu[i]);
+  }
+  h->mu_ref = mu_ref;
+  h->alpha = prm.alpha_rel * mu_ref;
+  h->kappa = prm.fiber_scale * mu_ref;
+  double fl = 0.0;
+  for (int64_t i = 0; i < m; ++i) {
+    wv[i] = prm.weight_mode == 1 ? V[i] * std::max(1.0, mu[i] / mu_ref) : V[i];
+    cv[i] = h->alpha * wv[i];
+    fl += (V[i] * mu[i]) * (V[i] * mu[i]);
+    if (desc->fiber_dir) {
+      double x = desc->fiber_dir[3 * i], y = desc->fiber_dir[3 * i + 1], z = desc->fiber_dir[3 * i + 2];
+      double nrm = std::sqrt(x * x + y * y + z * z);
+      if (!(nrm > 0.0) || !std::isfinite(nrm)) {
+        delete h;
+        return fail(EMU_ERR_INVALID_ARG, "fiber direction must be non-zero and finite");
+      }
+      uv[i] = x / nrm;
+      uv[m + i] = y / nrm;
+      uv[2 * m + i] = z / nrm;
+    }
+  }
+  h->floor = 1e-12 * std::sqrt(fl);
+  h->V_h = V;
+
+  // ---- pins ----
+  std::vector<uint8_t> is_fixed(n, 0);
+  std::vector<double> qfix(Q, Q + 3 * n);
+  for (int64_t k = 0; k < desc->n_fixed; ++k) {
+    const int32_t v = desc->fixed_verts[k];
+    is_fixed[v] = 1;
+    if (desc->fixed_pos)
+      for (int r = 0; r < 3; ++r) qfix[3 * v + r] = desc->fixed_pos[3 * k + r];
+  }
+
+  // ---- scalar ACAP Laplacian L_ab = sum_i w_i gradN_a . gradN_b (Eq. 4) ----
+  std::vector<std::pair<int64_t, double>> trip;
+  trip.reserve(16 * m);
+  std::vector<double> bfix(3 * n, 0.0);
+  for (int64_t i = 0; i < m; ++i) {
+    double gN[4][3];
+    for (int k = 0; k < 3; ++k)
+      for (int c2 = 0; c2 < 3; ++c2) gN[k][c2] = Dinv[(3 * k + c2) * m + i];
+    for (int c2 = 0; c2 < 3; ++c2) gN[3][c2] = -(gN[0][c2] + gN[1][c2] + gN[2][c2]);
+    for (int a_ = 0; a_ < 4; ++a_) {
+      const int32_t va = tet[4 * i + a_];
+      if (is_fixed[va]) continue;
+      for (int b_ = 0; b_ < 4; ++b_) {
+        const int32_t vb = tet[4 * i + b_];
+        const double lv = wv[i] * (gN[a_][0] * gN[b_][0] + gN[a_][1] * gN[b_][1] + gN[a_][2] * gN[b_][2]);
+        if (is_fixed[vb]) {
+          for (int r = 0; r < 3; ++r) bfix[3 * va + r] += lv * qfix[3 * vb + r];
+        } else {
+          trip.push_back({(int64_t)va * n + vb, lv});
+        }
+      }
+    }
+  }
+  for (int64_t v = 0; v < n; ++v)
+    if (is_fixed[v]) trip.push_back({v * n + v, 1.0});
+  std::sort(trip.begin(), trip.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+  std::vector<int32_t> rowptr(n + 1, 0), colv;
+  std::vector<double> valv, ldinv(n, 1.0);
+  colv.reserve(trip.size());
+  valv.reserve(trip.size());
+  for (size_t k = 0; k < trip.size();) {
+    const int64_t key = trip[k].first;
+    double s_ = 0.0;
+    while (k < trip.size() && trip[k].first == key) s_ += trip[k++].second;
+    const int64_t r = key / n, cc = key % n;
+    colv.push_back((int32_t)cc);
+    valv.push_back(s_);
+    rowptr[r + 1]++;
+    if (r == cc) ldinv[r] = 1.0 / s_;
+  }
+  for (int64_t v = 0; v < n; ++v) rowptr[v + 1] += rowptr[v];
+  for (int64_t v = 0; v < n; ++v)
+    if (!is_fixed[v] && rowptr[v + 1] == rowptr[v]) {
+      delete h;
+      return fail(EMU_ERR_INVALID_ARG, "vertex " + std::to_string(v) + " is in no tet and not pinned");
+    }
+
+  // ---- corner slots per vertex (atomic-free gather of G^T W X) ----
+  std::vector<int32_t> slot_ptr(n + 1, 0), slot_idx(4 * m);
+  for (int64_t k = 0; k < 4 * m; ++k) slot_ptr[tet[k] + 1]++;
+  for (int64_t v = 0; v < n; ++v) slot_ptr[v + 1] += slot_ptr[v];
+  {
+    std::vector<int32_t> fillp(slot_ptr.begin(), slot_ptr.end() - 1);
+    for (int64_t k = 0; k < 4 * m; ++k) slot_idx[fillp[tet[k]]++] = (int32_t)k;
+  }
+
+  // ---- device allocation ----
+  bool ok = true;
+  const int64_t nnz = (int64_t)colv.size();
+  ok = ok && h->get(h->tet, m) && h->get(h->Dinv, 9 * m) && h->get(h->V, m) && h->get(h->c, m) && h->get(h->w, m) &&
+       h->get(h->mu, m) && h->get(h->lam, m) && h->get(h->u, 3 * m) && h->get(h->ka, m);
+  ok = ok && h->get(h->R, 9 * m) && h->get(h->s, 6 * m) && h->get(h->q, 3 * n) && h->get(h->dq, 3 * n) &&
+       h->get(h->q0, 3 * n) && h->get(h->g, 9 * m) && h->get(h->contrib, 12 * m) && h->get(h->b, 16 * n);
+  if (h->mixed)
+    ok = ok && h->get(h->gam32, 48 * m) && h->get(h->y32, 9 * m) && h->get(h->d32, 9 * m) && h->get(h->Uw32, 54 * m);
+  else
+    ok = ok && h->get(h->gam64, 48 * m) && h->get(h->y64, 9 * m) && h->get(h->d64, 9 * m) && h->get(h->Uw64, 54 * m);
+  ok = ok && h->get(h->pr, 16 * n) && h->get(h->pu, 16 * n) && h->get(h->pw, 16 * n) && h->get(h->pp, 16 * n) &&
+       h->get(h->ps, 16 * n) && h->get(h->scratch16, 32 * n);
+  h->grid_tet = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 127) / 128), 8 * (int64_t)h->sms);
+  h->grid_syrk = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 15) / 16), 2 * (int64_t)h->sms);
+  h->grid_pcg3 = pcg_max_grid(3, n);
+  h->grid_pcg16 = pcg_max_grid(16, n);
+  const int pcg_part = std::max(h->grid_pcg3 * 12, h->grid_pcg16 * 64);
+  const int64_t gpart = std::max<int64_t>(h->grid_tet * (int64_t)kLsNV, 256 * (int64_t)(2 * h->sms + 1));
+  ok = ok && h->get(h->part_grad, gpart) && h->get(h->part_dir, h->grid_tet) && h->get(h->part_ls, h->grid_tet * kLsNV) &&
+       h->get(h->part_pcg, std::max<int64_t>(pcg_part, 256 * (int64_t)(2 * h->sms + 1))) &&
+       h->get(h->cpart, (int64_t)h->grid_syrk * (kCapEntries + kK)) && h->get(h->z, kK) && h->get(h->small, 256) &&
+       h->get(h->sc, 1) && h->get(h->bar, 1);
+  ok = ok && h->get(h->rowptr, n + 1) && h->get(h->col, nnz) && h->get(h->val, nnz) && h->get(h->ldinv, n) &&
+       h->get(h->bfix, 3 * n) && h->get(h->qfix, 3 * n) && h->get(h->is_fixed, n) && h->get(h->slot_ptr, n + 1) &&
+       h->get(h->slot_idx, 4 * m);
+  if (!ok) {
+    h->release();
+    delete h;
+    return fail(EMU_ERR_OOM, "device allocation failed");
+  }
+  if (cudaMallocHost(&h->sc_host, sizeof(DevScalars)) != cudaSuccess) {
+    h->release();
+    delete h;
+    return fail(EMU_ERR_OOM, "pinned host allocation failed");
+  }
+
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->st) == cudaSuccess;
+  };
+  std::vector<double> zeros(m, 0.0);
+  ok = up(h->tet, tet.data(), 16 * m) && up(h->Dinv, Dinv.data(), 72 * m) && up(h->V, V.data(), 8 * m) &&
+       up(h->c, cv.data(), 8 * m) && up(h->w, wv.data(), 8 * m) && up(h->mu, mu.data(), 8 * m) &&
+       up(h->lam, lam.data(), 8 * m) && up(h->u, uv.data(), 24 * m) && up(h->ka, zeros.data(), 8 * m) &&
+       up(h->rowptr, rowptr.data(), 4 * (n + 1)) && up(h->col, colv.data(), 4 * nnz) && up(h->val, valv.data(), 8 * nnz) &&
+       up(h->ldinv, ldinv.data(), 8 * n) && up(h->bfix, bfix.data(), 24 * n) && up(h->qfix, qfix.data(), 24 * n) &&
+       up(h->is_fixed, is_fixed.data(), n) && up(h->slot_ptr, slot_ptr.data(), 4 * (n + 1)) &&
+       up(h->slot_idx, slot_idx.data(), 16 * m) && up(h->q, qfix.data(), 24 * n);
+  if (!ok || cudaMemsetAsync(h->sc, 0, sizeof(DevScalars), h->st) != cudaSuccess) {
+    h->release();
+    delete h;
+    return fail(EMU_ERR_CUDA, "upload failed");
+  }
+
+  // ---- rest state: R = I, S = I, q = q*(I) ----
+  rc = set_rest_state(h);
+  if (!rc) rc = coupling_solve(h);
+  if (!rc && cudaMemcpyAsync(h->q0, h->q, 24 * n, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess)
+    rc = fail(EMU_ERR_CUDA, "copy q0");
+  if (!rc) rc = build_modes(h);
+  if (!rc) rc = read_scalars(h);
+  if (!rc && h->sc_host->barrier_timeout) rc = fail(EMU_ERR_TIMEOUT, "grid barrier timed out during setup");
+  if (rc) {
+    h->release();
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return EMU_OK;
+}
+
+int emu_set_activation(emu_handle* h, const double* a, int64_t count) {
+  if (!h || !a) return fail(EMU_ERR_INVALID_ARG, "NULL argument");
+  if (count != h->m) return fail(EMU_ERR_INVALID_ARG, "activation count must equal n_tets");
+  std::vector<double> ka(h->m);
+  for (int64_t i = 0; i < h->m; ++i) {
+    if (!(a[i] >= 0.0) || !std::isfinite(a[i])) return fail(EMU_ERR_INVALID_ARG, "activation must be finite and >= 0");
+    ka[i] = h->kappa * a[i];
+  }
+  EMU_CK(cudaMemcpyAsync(h->ka, ka.data(), 8 * h->m, cudaMemcpyHostToDevice, h->st));
+  EMU_CK(cudaStreamSynchronize(h->st));
+  h->gref_valid = false;
+  return EMU_OK;
+}
+
+int emu_set_activation_device(emu_handle* h, const double* a_device, int64_t count) {
+  if (!h || !a_device) return fail(EMU_ERR_INVALID_ARG, "NULL argument");
+  if (count != h->m) return fail(EMU_ERR_INVALID_ARG, "activation count must equal n_tets");
+  std::vector<double> a(h->m);
+  EMU_CK(cudaMemcpyAsync(a.data(), a_device, 8 * h->m, cudaMemcpyDeviceToHost, h->st));
+  EMU_CK(cudaStreamSynchronize(h->st));
+  return emu_set_activation(h, a.data(), count);
+}
+
+int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats) {
+  if (!h) return fail(EMU_ERR_INVALID_ARG, "NULL handle");
+  auto t0 = std::chrono::steady_clock::now();
+  int rc = EMU_OK;
+  if (!h->gref_valid) {
+    rc = compute_gref(h);
+    if (rc) return rc;
+  }
+  DevScalars init;
+  memset(&init, 0, sizeof(init));
+  init.sigma_start = h->prm.ls_sigma0;
+  EMU_CK(cudaMemcpyAsync(h->sc, &init, sizeof(init), cudaMemcpyHostToDevice, h->st));
+  double gnorm_ref = h->gref > h->floor ? h->gref : 0.0;
+  int it = 0;
+  double res = 0.0;
+  int status = EMU_OK;
+  const double tol = h->prm.tol_rel_residual;
+  TetArgs<double> a64 = h->args<double>();
+  TetArgs<float> a32 = h->args<float>();
+  for (;;) {
+    rc = coupling_solve(h);
+    if (rc) return rc;
+    h->ph_begin();
+    if (h->mixed)
+      launch_grad<float>(a32, h->grid_tet, h->st);
+    else
+      launch_grad<double>(a64, h->grid_tet, h->st);
+    h->ph_end(EMU_PHASE_GRAD, 1);
+    h->ph_begin();
+    launch_reduce_grad(h->part_grad, h->grid_tet, h->sc, nullptr, nullptr, h->st);
+    h->ph_end(EMU_PHASE_SMALL, 1);
+    EMU_CK(cudaGetLastError());
+    rc = read_scalars(h);
+    if (rc) return rc;
+    const DevScalars& hs = *h->sc_host;
+    if (hs.barrier_timeout) {
+      status = fail(EMU_ERR_TIMEOUT, "grid barrier timed out");
+      break;
+    }
+    if (hs.nonfinite || !std::isfinite(hs.gnorm2)) {
+      status = fail(EMU_ERR_INVERTED, "non-finite gradient");
+      break;
+    }
+    const double gn = std::sqrt(hs.gnorm2);
+    if (it == 0 && gnorm_ref == 0.0) gnorm_ref = gn > h->floor ? gn : 0.0;
+    res = gnorm_ref > 0.0 ? gn / gnorm_ref : 0.0;
+    if (res <= tol) break;
+    if (hs.pcg_fail) {
+      status = fail(EMU_ERR_PCG, "ACAP solve hit pcg_max");
+      break;
+    }
+    if (hs.ls_fail * kLsTrials >= h->prm.ls_max_trials) {
+      status = fail(EMU_ERR_LINESEARCH, "no Armijo step");
+      break;
+    }
+    if (it >= h->prm.max_newton) {
+      status = fail(EMU_ERR_NOT_CONVERGED, "max_newton reached");
+      break;
+    }
+    // Woodbury direction (Eqs. 9-12)
+    h->ph_begin();
+    if (h->mixed) {
+      launch_syrk<float>(a32, h->grid_syrk, h->cpart, h->st);
+    } else {
+      launch_syrk<double>(a64, h->grid_syrk, h->cpart, h->st);
+    }
+    h->ph_end(EMU_PHASE_SYRK, 1);
+    h->ph_begin();
+    launch_cap_solve(h->cpart, h->grid_syrk, nullptr, h->z, h->sc, h->st);
+    h->ph_end(EMU_PHASE_SMALL, 1);
+    {
+      TetArgs<double> ad = a64;
+      TetArgs<float> af = a32;
+      ad.partials = h->part_dir;
+      af.partials = h->part_dir;
+      h->ph_begin();
+      if (h->mixed)
+        launch_dir<float>(af, h->grid_tet, h->st);
+      else
+        launch_dir<double>(ad, h->grid_tet, h->st);
+      h->ph_end(EMU_PHASE_DIR, 1);
+    }
+    h->ph_begin();
+    launch_assemble(h->n, h->slot_ptr, h->slot_idx, h->contrib, h->bfix, h->is_fixed, h->qfix, 1, h->b, h->st);
+    h->ph_end(EMU_PHASE_ASSEMBLE, 1);
+    EMU_CK(cudaGetLastError());
+    h->ph_begin();
+    EMU_CK(launch_pcg(3, h->pcg_args(h->b, h->dq, 3), h->grid_pcg3, h->st));
+    h->ph_end(EMU_PHASE_PCG, 1);
+    // Armijo line search (Algorithm 1)
+    {
+      TetArgs<double> al = a64;
+      TetArgs<float> af = a32;
+      al.partials = h->part_ls;
+      af.partials = h->part_ls;
+      h->ph_begin();
+      if (h->mixed)
+        launch_ls<float>(af, h->grid_tet, h->prm.ls_rho, h->st);
+      else
+        launch_ls<double>(al, h->grid_tet, h->prm.ls_rho, h->st);
+      h->ph_end(EMU_PHASE_LS, 1);
+    }
+    h->ph_begin();
+    launch_ls_select(h->part_dir, h->grid_tet, h->part_ls, h->grid_tet, h->sc, h->prm.ls_sigma0, h->prm.ls_rho,
+                     h->prm.ls_c, h->st);
+    h->ph_end(EMU_PHASE_SMALL, 1);
+    h->ph_begin();
+    if (h->mixed)
+      launch_update_tets<float>(a32, h->grid_tet, h->st);
+    else
+      launch_update_tets<double>(a64, h->grid_tet, h->st);
+    launch_update_verts(h->n, h->sc, h->dq, h->q, h->st);
+    h->ph_end(EMU_PHASE_UPDATE, 2);
+    EMU_CK(cudaGetLastError());
+    ++it;
+  }
+  EMU_CK(cudaStreamSynchronize(h->st));
+  h->prof_flush();
+  auto t1 = std::chrono::steady_clock::now();
+  if (stats) {
+    stats->newton_iters = it;
+    stats->ls_trials = h->sc_host->ls_trials;
+    stats->pcg_iters = h->sc_host->pcg_iters;
+    stats->status = status;
+    stats->rel_residual = res;
+    stats->energy_change = h->sc_host->dE;
+    stats->ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  }
+  return status;
+}
+
+int emu_get_positions(emu_handle* h, double* out, int32_t out_is_device) {
+  if (!h || !out) return fail(EMU_ERR_INVALID_ARG, "NULL argument");
+  EMU_CK(cudaMemcpyAsync(out, h->q, 24 * h->n, out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+  EMU_CK(cudaStreamSynchronize(h->st));
+  return EMU_OK;
+}
+
+int emu_get_element_state(emu_handle* h, double* R, double* s, double* F) {
+  if (!h) return fail(EMU_ERR_INVALID_ARG, "NULL handle");
+  const int64_t m = h->m;
+  std::vector<double> tmp(9 * m);
+  auto soa_to_aos = [&](const double* dsrc, int k, double* dst) -> int {
+    EMU_CK(cudaMemcpyAsync(tmp.data(), dsrc, 8 * k * m, cudaMemcpyDeviceToHost, h->st));
+    EMU_CK(cudaStreamSynchronize(h->st));
+    for (int64_t i = 0; i < m; ++i)
+      for (int j = 0; j < k; ++j) dst[k * i + j] = tmp[j * m + i];
+    return EMU_OK;
+  };
+  int rc;
+  if (R && (rc = soa_to_aos(h->R, 9, R))) return rc;
+  if (s && (rc = soa_to_aos(h->s, 6, s))) return rc;
+  if (F) {
+    launch_compose_F(m, h->R, h->s, h->contrib, h->st);
+    EMU_CK(cudaGetLastError());
+    if ((rc = soa_to_aos(h->contrib, 9, F))) return rc;
+  }
+  return EMU_OK;
+}
+
+int emu_set_element_state(emu_handle* h, const double* R, const double* s, const double* q) {
+  if (!h) return fail(EMU_ERR_INVALID_ARG, "NULL handle");
+  const int64_t m = h->m;
+  std::vector<double> tmp(9 * m);
+  if (R) {
+    for (int64_t i = 0; i < m; ++i)
+      for (int j = 0; j < 9; ++j) tmp[j * m + i] = R[9 * i + j];
+    EMU_CK(cudaMemcpyAsync(h->R, tmp.data(), 72 * m, cudaMemcpyHostToDevice, h->st));
+    EMU_CK(cudaStreamSynchronize(h->st));
+  }
+  if (s) {
+    for (int64_t i = 0; i < m; ++i)
+      for (int j = 0; j < 6; ++j) tmp[j * m + i] = s[6 * i + j];
+    EMU_CK(cudaMemcpyAsync(h->s, tmp.data(), 48 * m, cudaMemcpyHostToDevice, h->st));
+    EMU_CK(cudaStreamSynchronize(h->st));
+  }
+  if (q) {
+    EMU_CK(cudaMemcpyAsync(h->q, q, 24 * h->n, cudaMemcpyHostToDevice, h->st));
+    EMU_CK(cudaStreamSynchronize(h->st));
+  }
+  return EMU_OK;
+}
+
+int emu_reset(emu_handle* h) {
+  if (!h) return fail(EMU_ERR_INVALID_ARG, "NULL handle");
+  int rc = set_rest_state(h);
+  if (rc) return rc;
+  EMU_CK(cudaMemcpyAsync(h->q, h->q0, 24 * h->n, cudaMemcpyDeviceToDevice, h->st));
+  EMU_CK(cudaStreamSynchronize(h->st));
+  return EMU_OK;
+}
+
+int emu_get_sizes(emu_handle* h, int64_t* n_verts, int64_t* n_tets, int32_t* k_modes) {
+  if (!h) return fail(EMU_ERR_INVALID_ARG, "NULL handle");
+  if (n_verts) *n_verts = h->n;
+  if (n_tets) *n_tets = h->m;
+  if (k_modes) *k_modes = 3 * h->kmodes;
+  return EMU_OK;
+}
+
+int emu_set_profiling(emu_handle* h, int32_t enable) {
+  if (!h) return fail(EMU_ERR_INVALID_ARG, "NULL handle");
+  EMU_CK(cudaStreamSynchronize(h->st));
+  h->prof_flush();
+  h->prof_on = enable != 0;
+  for (int k = 0; k < EMU_N_PHASES; ++k) {
+    h->prof_ms[k] = 0.0;
+    h->prof_cnt[k] = 0;
+  }
+  h->launches = 0;
+  return EMU_OK;
+}
+
+int emu_get_profile(emu_handle* h, double* phase_ms, int32_t* phase_launches, int32_t n_phases,
+                    int64_t* total_launches) {
+  if (!h || n_phases < 0 || n_phases > EMU_N_PHASES) return fail(EMU_ERR_INVALID_ARG, "bad arguments");
+  EMU_CK(cudaStreamSynchronize(h->st));
+  h->prof_flush();
+  for (int k = 0; k < n_phases; ++k) {
+    if (phase_ms) phase_ms[k] = h->prof_ms[k];
+    if (phase_launches) phase_launches[k] = h->prof_cnt[k];
+  }
+  if (total_launches) *total_launches = h->launches;
+  return EMU_OK;
+}
+
+int emu_eval_stretch_terms(const double* s, const double* params, int64_t n, int32_t mixed, double* psi,
+                           double* grad, double* hess, void* stream) {
+  if (!s || !params || n < 0) return fail(EMU_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return EMU_OK;
+  launch_eval_stretch(s, params, n, mixed, psi, grad, hess, (cudaStream_t)stream);
+  EMU_CK(cudaGetLastError());
+  EMU_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return EMU_OK;
+}
+
+int emu_eval_polar(const double* F, int64_t n, double* R, double* s, void* stream) {
+  if (!F || !R || !s || n < 0) return fail(EMU_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return EMU_OK;
+  launch_eval_polar(F, n, R, s, (cudaStream_t)stream);
+  EMU_CK(cudaGetLastError());
+  EMU_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return EMU_OK;
+}
+
+}  // extern "C"

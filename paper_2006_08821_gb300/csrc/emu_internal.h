@@ -1,0 +1,57 @@
+// Internal declarations shared by the host code and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/emu.h"
+
+namespace emu {
+
+constexpr int kModes = 16;          // scalar low-rank modes (k = 3 * kModes = 48)
+constexpr int kK = 3 * kModes;      // Woodbury size k of Eq. 9
+constexpr int kLsTrials = 4;        // line-search trials evaluated per pass
+constexpr int kRedBlock = 256;      // threads of the single-block reducers
+
+// Device-side scalars of one Newton iteration (one struct per handle).
+struct DevScalars {
+  double gnorm2;        // ||dE/dF||^2 (FP64)
+  double gtd;           // g . d
+  double sigma;         // accepted step (0 = rejected)
+  double sigma_start;   // first trial of the next line search
+  double dE;            // accumulated energy change of accepted steps
+  double cap_ok;        // 1 if the capacitance Cholesky succeeded
+  int32_t ls_trials;    // total trials evaluated
+  int32_t ls_fail;      // consecutive rejected passes
+  int32_t pcg_iters;    // CG iterations, summed
+  int32_t pcg_fail;     // a CG solve hit pcg_max
+  int32_t barrier_timeout;
+  int32_t nonfinite;    // a non-finite value was produced
+  int32_t pad[2];
+};
+
+// Mesh constants on the device (structure of arrays, index i = tet).
+template <typename T> struct MeshArrays {
+  int64_t m, n;
+  const int4* tet;      // m
+  const T* Dinv;        // 9 m: Dinv[k * m + i], row-major 3x3 per tet
+  const T* V;           // m
+  const T* c;           // m: alpha * w_i
+  const T* w;           // m
+  const T* mu;          // m
+  const T* lam;         // m
+  const T* u;           // 3 m
+  const T* ka;          // m: kappa * a_i
+  const T* gam;         // 48 m: gam[(3 j + c) * m + i] = d phi_j / dx_c on tet i
+};
+
+// CSR of the scalar ACAP Laplacian (Eq. 4 with full-vertex pins: the
+// 3n x 3n matrix is L (x) I_3). Pinned rows are identity.
+struct Laplacian {
+  int64_t n;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const double* dinv;   // 1 / L_vv
+};
+
+}  // namespace emu

@@ -1,0 +1,849 @@
+// Per-tet and per-vertex kernels of one Newton iteration of EMU's
+// quasi-static solve in rotation/stretch form (arXiv 2006.08821, Sec. 3).
+//
+// One iteration (the host drives the order, everything stays on the device):
+//   rhs_from_state -> assemble -> PCG          q = q*(R S)              (Eq. 4)
+//   grad            g = V P(F) + alpha w (F - G q), |g|^2, Uw, y = H^-1 g  (Eqs. 6-7)
+//   syrk + cap      C = sum w (G Phi)^T N (G Phi), B y, z = C^-1 B y    (Eqs. 9-12)
+//   dir             d = -(y + (I - N) (G Phi) z), corner RHS of G^T W d
+//   assemble -> PCG dq = q*(d) linear part
+//   ls + select     Armijo backtracking on E(F + sigma d)              (Algorithm 1)
+//   update          F <- F + sigma d, polar re-extraction of R, S; q += sigma dq
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "emu_kernels.cuh"
+#include "emu_math.cuh"
+
+namespace emu {
+
+// ------------------------------------------------------------ reductions --
+template <int NV>
+__device__ __forceinline__ void block_reduce_write(double (&v)[NV], double* out) {
+  __shared__ double sm[8 * NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sm[warp * NV + k] = x;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    double x = 0.0;
+    for (int w = 0; w < nw; ++w) x += sm[w * NV + k];
+    out[k] = x;
+  }
+}
+
+// ------------------------------------------------------------ gathers ----
+__device__ __forceinline__ void load_dinv(const double* __restrict__ Dinv, int64_t m, int64_t i, double* D) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) D[k] = Dinv[k * m + i];
+}
+
+// A = G_i q = D_s(q) D_m^-1 (Eq. 2): A[r][c] = sum_k (q_k - q_3)[r] Dinv[k][c]
+__device__ __forceinline__ void gather_defgrad(const double* __restrict__ q, int4 t, const double* D, double* A) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const double q3 = q[3 * (int64_t)t.w + r];
+    const double e0 = q[3 * (int64_t)t.x + r] - q3;
+    const double e1 = q[3 * (int64_t)t.y + r] - q3;
+    const double e2 = q[3 * (int64_t)t.z + r] - q3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A[3 * r + c] = e0 * D[c] + e1 * D[3 + c] + e2 * D[6 + c];
+  }
+}
+
+// Corner contributions of w G_i^T X: for corner k < 3 the shape gradient is
+// row k of D_m^-1; corner 3 has minus their sum.
+template <typename TX>
+__device__ __forceinline__ void write_corners(double* __restrict__ contrib, int64_t i, double w, const TX* X,
+                                              const double* D) {
+  double s0 = 0, s1 = 0, s2 = 0;
+  double* out = contrib + 12 * i;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double v[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      v[r] = w * ((double)X[3 * r] * D[3 * k] + (double)X[3 * r + 1] * D[3 * k + 1] + (double)X[3 * r + 2] * D[3 * k + 2]);
+    out[3 * k] = v[0];
+    out[3 * k + 1] = v[1];
+    out[3 * k + 2] = v[2];
+    s0 += v[0];
+    s1 += v[1];
+    s2 += v[2];
+  }
+  out[9] = -s0;
+  out[10] = -s1;
+  out[11] = -s2;
+}
+
+template <typename T>
+__device__ __forceinline__ ElemMat<T> load_mat(const double* V, const double* mu, const double* lam,
+                                               const double* ka, const double* u, int64_t m, int64_t i) {
+  ElemMat<T> e;
+  e.V = (T)V[i];
+  e.mu = (T)mu[i];
+  e.lam = (T)lam[i];
+  e.ka = (T)ka[i];
+  e.u[0] = (T)u[i];
+  e.u[1] = (T)u[m + i];
+  e.u[2] = (T)u[2 * m + i];
+  return e;
+}
+
+// ------------------------------------------------- coupling-solve RHS ----
+__global__ void __launch_bounds__(256) k_rhs_from_state(TetArgs<double> a) {
+  const int64_t m = a.m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double D[9], R[9], sv[6], S[9], F[9];
+    load_dinv(a.Dinv, m, i, D);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = a.R[k * m + i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sv[k] = a.s[k * m + i];
+    sym_from_s(sv, S);
+    matmul3(R, S, F);
+    write_corners(a.contrib, i, a.w[i], F, D);
+  }
+}
+
+void launch_rhs_from_state(const TetArgs<double>& a, int grid, cudaStream_t st) {
+  k_rhs_from_state<<<grid, 256, 0, st>>>(a);
+}
+
+__global__ void __launch_bounds__(256) k_assemble(int64_t n, const int32_t* __restrict__ slot_ptr,
+                                                  const int32_t* __restrict__ slot_idx,
+                                                  const double* __restrict__ contrib, const double* __restrict__ bfix,
+                                                  const uint8_t* __restrict__ is_fixed,
+                                                  const double* __restrict__ qfix, int mode, double* __restrict__ b) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    if (is_fixed[v]) {
+      if (mode == 0) {
+        s0 = qfix[3 * v];
+        s1 = qfix[3 * v + 1];
+        s2 = qfix[3 * v + 2];
+      }
+    } else {
+      const int32_t e0 = slot_ptr[v], e1 = slot_ptr[v + 1];
+      for (int32_t e = e0; e < e1; ++e) {
+        const int64_t sl = slot_idx[e];
+        s0 += contrib[3 * sl];
+        s1 += contrib[3 * sl + 1];
+        s2 += contrib[3 * sl + 2];
+      }
+      if (mode == 0) {
+        s0 -= bfix[3 * v];
+        s1 -= bfix[3 * v + 1];
+        s2 -= bfix[3 * v + 2];
+      }
+    }
+    b[3 * v] = s0;
+    b[3 * v + 1] = s1;
+    b[3 * v + 2] = s2;
+  }
+}
+
+void launch_assemble(int64_t n, const int32_t* slot_ptr, const int32_t* slot_idx, const double* contrib,
+                     const double* bfix, const uint8_t* is_fixed, const double* qfix, int mode, double* b,
+                     cudaStream_t st) {
+  int grid = (int)((n + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_assemble<<<grid, 256, 0, st>>>(n, slot_ptr, slot_idx, contrib, bfix, is_fixed, qfix, mode, b);
+}
+
+// ------------------------------------------------------------ gradient ----
+// g = V R Pr(S) + alpha w (R S - G_i q) in FP64 (Eqs. 6-7); the chart factor
+// Uw and y = H_F^-1 g = (g - N g) / (alpha w) in TW.
+template <typename TW>
+__global__ void __launch_bounds__(128) k_grad(TetArgs<TW> a) {
+  const int64_t m = a.m;
+  double acc[1] = {0.0};
+  int bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 t = a.tet[i];
+    double D[9], R[9], sv[6], S[9], F[9], A[9];
+    load_dinv(a.Dinv, m, i, D);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = a.R[k * m + i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sv[k] = a.s[k * m + i];
+    sym_from_s(sv, S);
+    matmul3(R, S, F);
+    gather_defgrad(a.q, t, D, A);
+    const ElemMat<double> md = load_mat<double>(a.V, a.mu, a.lam, a.ka, a.u, m, i);
+    const double c = a.c[i];
+    double Pr[9], Sinv[9], lnJ;
+    piola_rotated(S, md, Pr, Sinv, lnJ);
+    double RP[9];
+    matmul3(R, Pr, RP);
+    double g[9];
+    double gg = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      g[k] = md.V * RP[k] + c * (F[k] - A[k]);
+      gg += g[k] * g[k];
+      a.g[k * m + i] = g[k];
+    }
+    if (!isfinite(gg)) bad = 1;
+    acc[0] += gg;
+
+    // Hessian / Woodbury quantities in TW
+    TW Sw[9], Siw[9], Rw[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      Sw[k] = (TW)S[k];
+      Siw[k] = (TW)Sinv[k];
+      Rw[k] = (TW)R[k];
+    }
+    const ElemMat<TW> mw = load_mat<TW>(a.V, a.mu, a.lam, a.ka, a.u, m, i);
+    TW M6[36];
+    stretch_hessian(Siw, (TW)lnJ, mw, M6);
+    TW U[54];
+    bool ok = true;
+    chart_factor(Rw, Sw, M6, (TW)c, U, ok);
+    if (!ok) bad = 1;
+    TW yv[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) yv[k] = (TW)g[k];
+    apply_I_minus_N(U, yv);
+    const TW ic = (TW)(1.0 / c);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) a.y[k * m + i] = yv[k] * ic;
+#pragma unroll
+    for (int k = 0; k < 54; ++k) a.Uw[k * m + i] = U[k];
+  }
+  block_reduce_write<1>(acc, a.partials + blockIdx.x);
+  if (bad) atomicExch(&a.sc->nonfinite, 1);
+}
+
+template <typename TW> void launch_grad(const TetArgs<TW>& a, int grid, cudaStream_t st) {
+  k_grad<TW><<<grid, 128, 0, st>>>(a);
+}
+
+__global__ void k_reduce_grad(const double* partials, int nblk, DevScalars* sc) {
+  // single warp: deterministic fixed-order sum
+  if (threadIdx.x == 0) {
+    double x = 0.0;
+    for (int b = 0; b < nblk; ++b) x += partials[b];
+    sc->gnorm2 = x;
+  }
+}
+
+void launch_reduce_grad(const double* partials, int nblk, DevScalars* sc, double*, double*, cudaStream_t st) {
+  k_reduce_grad<<<1, 32, 0, st>>>(partials, nblk, sc);
+}
+
+// ------------------------------------------------------------ capacitance --
+// C = sum_i w_i (G_i Phi^T)^T N_i (G_i Phi^T) = sum_i Yh_i^T Yh_i with
+// Yh_i = sqrt(w_i) Uw_i (G_i Phi^T) (6 x 48): column 16 r + j of (G_i Phi^T) is
+// the matrix e_r gam_j^T, so Yh[k][16r+j] = sqrt(w) sum_b Uw[k][3r+b] gam_j[b].
+// Also B y = sum_i w_i (G_i Phi^T)^T y_i: By[16r+j] = sum_i w_i sum_b y[r][b] gam_j[b].
+template <typename TW>
+__global__ void __launch_bounds__(256) k_syrk(TetArgs<TW> a, double* __restrict__ cpart) {
+  constexpr int CH = sizeof(TW) == 8 ? 8 : 16;  // tets per chunk
+  constexpr int KR = CH * 6;
+  __shared__ TW sY[KR][kK + 1];
+  __shared__ TW sU[CH][54];
+  __shared__ TW sg[CH][48];
+  __shared__ TW sy[CH][9];
+  __shared__ double sw[CH];
+  const int tid = threadIdx.x;
+  const int tr = tid >> 4, tc = tid & 15;
+  TW acc[3][3];  // per-block partial sums in TW; across blocks in FP64
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) acc[p][q] = TW(0);
+  double by = 0.0;
+  const int64_t m = a.m;
+  const int64_t nch = (m + CH - 1) / CH;
+  for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const int64_t base = ch * CH;
+    for (int e = tid; e < CH * 54; e += 256) {
+      const int tt = e / 54, k = e % 54;
+      const int64_t i = base + tt;
+      sU[tt][k] = i < m ? a.Uw[k * m + i] : TW(0);
+    }
+    for (int e = tid; e < CH * 48; e += 256) {
+      const int tt = e / 48, k = e % 48;
+      const int64_t i = base + tt;
+      sg[tt][k] = i < m ? a.gam[k * m + i] : TW(0);
+    }
+    for (int e = tid; e < CH * 9; e += 256) {
+      const int tt = e / 9, k = e % 9;
+      const int64_t i = base + tt;
+      sy[tt][k] = i < m ? a.y[k * m + i] : TW(0);
+    }
+    if (tid < CH) sw[tid] = (base + tid) < m ? a.w[base + tid] : 0.0;
+    __syncthreads();
+    for (int e = tid; e < CH * 6 * kK; e += 256) {
+      const int tt = e / (6 * kK), rem = e % (6 * kK);
+      const int k = rem / kK, col = rem % kK;
+      const int r = col >> 4, j = col & 15;
+      TW v = sU[tt][9 * k + 3 * r] * sg[tt][3 * j] + sU[tt][9 * k + 3 * r + 1] * sg[tt][3 * j + 1] +
+             sU[tt][9 * k + 3 * r + 2] * sg[tt][3 * j + 2];
+      sY[tt * 6 + k][col] = v * (TW)sqrt(sw[tt]);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kr = 0; kr < KR; ++kr) {
+      const TW a0 = sY[kr][3 * tr], a1 = sY[kr][3 * tr + 1], a2 = sY[kr][3 * tr + 2];
+      const TW b0 = sY[kr][3 * tc], b1 = sY[kr][3 * tc + 1], b2 = sY[kr][3 * tc + 2];
+      acc[0][0] += a0 * b0;
+      acc[0][1] += a0 * b1;
+      acc[0][2] += a0 * b2;
+      acc[1][0] += a1 * b0;
+      acc[1][1] += a1 * b1;
+      acc[1][2] += a1 * b2;
+      acc[2][0] += a2 * b0;
+      acc[2][1] += a2 * b1;
+      acc[2][2] += a2 * b2;
+    }
+    if (tid < kK) {
+      const int r = tid >> 4, j = tid & 15;
+      for (int tt = 0; tt < CH; ++tt) {
+        by += sw[tt] * ((double)sy[tt][3 * r] * (double)sg[tt][3 * j] + (double)sy[tt][3 * r + 1] * (double)sg[tt][3 * j + 1] +
+                        (double)sy[tt][3 * r + 2] * (double)sg[tt][3 * j + 2]);
+      }
+    }
+    __syncthreads();
+  }
+  double* out = cpart + (size_t)blockIdx.x * (kCapEntries + kK);
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) out[(3 * tr + p) * kK + 3 * tc + q] = (double)acc[p][q];
+  if (tid < kK) out[kCapEntries + tid] = by;
+}
+
+template <typename TW> void launch_syrk(const TetArgs<TW>& a, int grid, double* cpart, cudaStream_t st) {
+  k_syrk<TW><<<grid, 256, 0, st>>>(a, cpart);
+}
+
+// Sum the capacitance partials, factor C = L L^T in FP64, z = C^-1 (B y).
+__global__ void __launch_bounds__(256) k_cap_solve(const double* __restrict__ cpart, int nblk, double* z,
+                                                    DevScalars* sc) {
+  __shared__ double C[kK][kK + 1];
+  __shared__ double by[kK];
+  __shared__ int s_ok;
+  const int tid = threadIdx.x;
+  constexpr int stride = kCapEntries + kK;
+  for (int e = tid; e < kCapEntries + kK; e += blockDim.x) {
+    double x = 0.0;
+    for (int b = 0; b < nblk; ++b) x += cpart[(size_t)b * stride + e];
+    if (e < kCapEntries)
+      C[e / kK][e % kK] = x;
+    else
+      by[e - kCapEntries] = x;
+  }
+  if (tid == 0) s_ok = 1;
+  __syncthreads();
+  // unused modes (k_modes < 48) have zero rows: make them identity rows
+  if (tid < kK && C[tid][tid] == 0.0) {
+    C[tid][tid] = 1.0;
+    by[tid] = 0.0;
+  }
+  __syncthreads();
+  // symmetrise
+  for (int e = tid; e < kCapEntries; e += blockDim.x) {
+    const int i = e / kK, j = e % kK;
+    if (j > i) {
+      const double v = 0.5 * (C[i][j] + C[j][i]);
+      C[i][j] = v;
+      C[j][i] = v;
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < kK; ++j) {
+    if (tid == 0) {
+      double d = C[j][j];
+      for (int k = 0; k < j; ++k) d -= C[j][k] * C[j][k];
+      if (!(d > 0.0)) {
+        s_ok = 0;
+        d = 1.0;
+      }
+      C[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < kK; i += blockDim.x) {
+      double v = C[i][j];
+      for (int k = 0; k < j; ++k) v -= C[i][k] * C[j][k];
+      C[i][j] = v / C[j][j];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    double x[kK];
+    for (int i = 0; i < kK; ++i) {
+      double v = by[i];
+      for (int k = 0; k < i; ++k) v -= C[i][k] * x[k];
+      x[i] = v / C[i][i];
+    }
+    for (int i = kK - 1; i >= 0; --i) {
+      double v = x[i];
+      for (int k = i + 1; k < kK; ++k) v -= C[k][i] * x[k];
+      x[i] = v / C[i][i];
+    }
+    const bool ok = s_ok != 0;
+    for (int i = 0; i < kK; ++i) z[i] = ok ? x[i] : 0.0;
+    sc->cap_ok = ok ? 1.0 : 0.0;
+  }
+}
+
+void launch_cap_solve(const double* cpart, int nblk, const double*, double* z, DevScalars* sc, cudaStream_t st) {
+  k_cap_solve<<<1, 256, 0, st>>>(cpart, nblk, z, sc);
+}
+
+// ------------------------------------------------------------ direction ---
+// d = -(y + alpha H_F^-1 w (G Phi^T) z) = -(y + (I - N) v), v = (G_i Phi^T) z.
+template <typename TW>
+__global__ void __launch_bounds__(128) k_dir(TetArgs<TW> a) {
+  __shared__ double sz[kK];
+  if (threadIdx.x < kK) sz[threadIdx.x] = a.z[threadIdx.x];
+  __syncthreads();
+  const int64_t m = a.m;
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    TW gm[48];
+#pragma unroll
+    for (int k = 0; k < 48; ++k) gm[k] = a.gam[k * m + i];
+    TW v[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        TW x = TW(0);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x += (TW)sz[16 * r + j] * gm[3 * j + cc];
+        v[3 * r + cc] = x;
+      }
+    TW U[54];
+#pragma unroll
+    for (int k = 0; k < 54; ++k) U[k] = a.Uw[k * m + i];
+    apply_I_minus_N(U, v);
+    TW dv[9];
+    double gtd = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      dv[k] = -(a.y[k * m + i] + v[k]);
+      a.d[k * m + i] = dv[k];
+      gtd += a.g[k * m + i] * (double)dv[k];
+    }
+    acc[0] += gtd;
+    double D[9];
+    load_dinv(a.Dinv, m, i, D);
+    write_corners(a.contrib, i, a.w[i], dv, D);
+  }
+  block_reduce_write<1>(acc, a.partials + blockIdx.x);
+}
+
+template <typename TW> void launch_dir(const TetArgs<TW>& a, int grid, cudaStream_t st) {
+  k_dir<TW><<<grid, 128, 0, st>>>(a);
+}
+
+// ------------------------------------------------------------ line search --
+// Per trial sigma_j = sigma_start rho^j: V [Psi(F + sigma d) - Psi(F)] in FP64,
+// written term by term (Algorithm 1's Armijo test needs the difference
+// itself): with M = F^-1 d, ln det(I + sigma M) = log1p(sigma tr M
+// + sigma^2 e2(M) + sigma^3 det M). The ACAP part is the exact quadratic
+// alpha/2 sum w |D + sigma dD|^2 - |D|^2, D = G q - F, dD = G dq - d.
+template <typename TW>
+__global__ void __launch_bounds__(128) k_ls(TetArgs<TW> a, double rho) {
+  const int64_t m = a.m;
+  const double s0 = a.sc->sigma_start;
+  double acc[kLsNV];
+#pragma unroll
+  for (int k = 0; k < kLsNV; ++k) acc[k] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 t = a.tet[i];
+    double D9[9], R[9], sv[6], S[9], F[9], A[9], dA[9], d[9];
+    load_dinv(a.Dinv, m, i, D9);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = a.R[k * m + i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sv[k] = a.s[k * m + i];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d[k] = (double)a.d[k * m + i];
+    sym_from_s(sv, S);
+    matmul3(R, S, F);
+    gather_defgrad(a.q, t, D9, A);
+    gather_defgrad(a.dq, t, D9, dA);
+    const double c = a.c[i];
+    double cDd = 0.0, cdd = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double Dk = A[k] - F[k], dDk = dA[k] - d[k];
+      cDd += Dk * dDk;
+      cdd += dDk * dDk;
+    }
+    acc[kLsTrials] += c * cDd;
+    acc[kLsTrials + 1] += c * cdd;
+    const ElemMat<double> md = load_mat<double>(a.V, a.mu, a.lam, a.ka, a.u, m, i);
+    double Sinv[9];
+    const double J = inv3(S, Sinv);
+    const double lnJ = log(J);
+    double Rtd[9], M[9];
+    matTmul3(R, d, Rtd);
+    matmul3(Sinv, Rtd, M);
+    const double trM = M[0] + M[4] + M[8];
+    const double trM2 = M[0] * M[0] + M[4] * M[4] + M[8] * M[8] + 2.0 * (M[1] * M[3] + M[2] * M[6] + M[5] * M[7]);
+    const double e2 = 0.5 * (trM * trM - trM2);
+    const double detM = det3(M);
+    double Fd = 0.0, dd = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      Fd += F[k] * d[k];
+      dd += d[k] * d[k];
+    }
+    double Fu[3], du[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      Fu[r] = F[3 * r] * md.u[0] + F[3 * r + 1] * md.u[1] + F[3 * r + 2] * md.u[2];
+      du[r] = d[3 * r] * md.u[0] + d[3 * r + 1] * md.u[1] + d[3 * r + 2] * md.u[2];
+    }
+    const double Fudu = Fu[0] * du[0] + Fu[1] * du[1] + Fu[2] * du[2];
+    const double dudu = du[0] * du[0] + du[1] * du[1] + du[2] * du[2];
+    double sig = s0;
+#pragma unroll
+    for (int j = 0; j < kLsTrials; ++j) {
+      const double x = sig * trM + sig * sig * e2 + sig * sig * sig * detM;
+      double dpsi;
+      if (x > -1.0) {
+        const double dl = log1p(x);
+        dpsi = md.mu * (sig * Fd + 0.5 * sig * sig * dd) - md.mu * dl + 0.5 * md.lam * dl * (2.0 * lnJ + dl) +
+               md.ka * (2.0 * sig * Fudu + sig * sig * dudu);
+        dpsi *= md.V;
+      } else {
+        dpsi = 1e300;
+      }
+      acc[j] += dpsi;
+      sig *= rho;
+    }
+  }
+  block_reduce_write<kLsNV>(acc, a.partials + (size_t)blockIdx.x * kLsNV);
+}
+
+template <typename TW> void launch_ls(const TetArgs<TW>& a, int grid, double rho, cudaStream_t st) {
+  k_ls<TW><<<grid, 128, 0, st>>>(a, rho);
+}
+
+__global__ void k_ls_select(const double* dir_partials, int nblk_dir, const double* ls_partials, int nblk_ls,
+                            DevScalars* sc, double sigma0, double rho, double c_armijo) {
+  if (threadIdx.x != 0) return;
+  double gtd = 0.0;
+  for (int b = 0; b < nblk_dir; ++b) gtd += dir_partials[b];
+  double v[kLsNV];
+  for (int k = 0; k < kLsNV; ++k) {
+    double x = 0.0;
+    for (int b = 0; b < nblk_ls; ++b) x += ls_partials[(size_t)b * kLsNV + k];
+    v[k] = x;
+  }
+  sc->gtd = gtd;
+  double sig = sc->sigma_start;
+  int accepted = -1;
+  double dE = 0.0;
+  if (gtd < 0.0) {
+    for (int j = 0; j < kLsTrials; ++j) {
+      const double dEj = v[j] + sig * v[kLsTrials] + 0.5 * sig * sig * v[kLsTrials + 1];
+      if (dEj <= c_armijo * sig * gtd) {
+        accepted = j;
+        dE = dEj;
+        break;
+      }
+      sig *= rho;
+    }
+  }
+  if (accepted >= 0) {
+    sc->sigma = sig;
+    sc->sigma_start = sigma0;
+    sc->dE += dE;
+    sc->ls_trials += accepted + 1;
+    sc->ls_fail = 0;
+  } else {
+    sc->sigma = 0.0;
+    double st = sc->sigma_start;
+    for (int j = 0; j < kLsTrials; ++j) st *= rho;
+    sc->sigma_start = st;
+    sc->ls_trials += kLsTrials;
+    sc->ls_fail += 1;
+  }
+}
+
+void launch_ls_select(const double* dir_partials, int nblk_dir, const double* ls_partials, int nblk_ls,
+                      DevScalars* sc, double sigma0, double rho, double c_armijo, cudaStream_t st) {
+  k_ls_select<<<1, 32, 0, st>>>(dir_partials, nblk_dir, ls_partials, nblk_ls, sc, sigma0, rho, c_armijo);
+}
+
+// ------------------------------------------------------------ update ------
+// F' = R S + sigma d; X = R^T F' = S + sigma R^T d is nearly symmetric, so its
+// polar factor Rx is close to I; R' = R Rx, S' = sym(Rx^T X).
+template <typename TW>
+__global__ void __launch_bounds__(128) k_update_tets(TetArgs<TW> a) {
+  const double sig = a.sc->sigma;
+  if (sig == 0.0) return;
+  const int64_t m = a.m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double R[9], sv[6], S[9], d[9], Rtd[9], X[9], Rx[9], Rn[9], Sn[9], sn[6];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = a.R[k * m + i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sv[k] = a.s[k * m + i];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d[k] = (double)a.d[k * m + i];
+    sym_from_s(sv, S);
+    matTmul3(R, d, Rtd);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] = S[k] + sig * Rtd[k];
+    polar_rotation(X, Rx, 1e-15, 40);
+    matTmul3(Rx, X, Sn);
+    s_from_mat(Sn, sn);
+    matmul3(R, Rx, Rn);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) a.R[k * m + i] = Rn[k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.s[k * m + i] = sn[k];
+  }
+}
+
+template <typename TW> void launch_update_tets(const TetArgs<TW>& a, int grid, cudaStream_t st) {
+  k_update_tets<TW><<<grid, 128, 0, st>>>(a);
+}
+
+__global__ void __launch_bounds__(256) k_update_verts(int64_t n3, const DevScalars* sc, const double* dq, double* q) {
+  const double sig = sc->sigma;
+  if (sig == 0.0) return;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x)
+    q[k] += sig * dq[k];
+}
+
+void launch_update_verts(int64_t n, const DevScalars* sc, const double* dq, double* q, cudaStream_t st) {
+  int64_t n3 = 3 * n;
+  int grid = (int)((n3 + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_update_verts<<<grid, 256, 0, st>>>(n3, sc, dq, q);
+}
+
+// ------------------------------------------------------------ normaliser --
+// ||g(F = I, q0)||: g = V * 2 ka u u^T + alpha w (I - G q0) (the neo-Hookean
+// stress vanishes at I).
+__global__ void __launch_bounds__(128) k_gref(TetArgs<double> a, const double* q0, double* partials) {
+  const int64_t m = a.m;
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double D[9], A[9];
+    load_dinv(a.Dinv, m, i, D);
+    gather_defgrad(q0, a.tet[i], D, A);
+    const double V = a.V[i], c = a.c[i], ka = a.ka[i];
+    const double u[3] = {a.u[i], a.u[m + i], a.u[2 * m + i]};
+    double gg = 0.0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        const double gv = V * 2.0 * ka * u[r] * u[cc] + c * ((r == cc ? 1.0 : 0.0) - A[3 * r + cc]);
+        gg += gv * gv;
+      }
+    acc[0] += gg;
+  }
+  block_reduce_write<1>(acc, partials + blockIdx.x);
+}
+
+__global__ void k_sum_scalar(const double* partials, int nblk, double* out) {
+  if (threadIdx.x == 0) {
+    double x = 0.0;
+    for (int b = 0; b < nblk; ++b) x += partials[b];
+    out[0] = x;
+  }
+}
+
+void launch_gref(const TetArgs<double>& a, const double* q0, int grid, double* partials, double* out,
+                 cudaStream_t st) {
+  k_gref<<<grid, 128, 0, st>>>(a, q0, partials);
+  k_sum_scalar<<<1, 32, 0, st>>>(partials, grid, out);
+}
+
+// ------------------------------------------------------------ modes -------
+__global__ void __launch_bounds__(256) k_gram16(int64_t n, const double* __restrict__ X, double* partials) {
+  const int a = threadIdx.x >> 4, b = threadIdx.x & 15;
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t v0 = blockIdx.x * per;
+  const int64_t v1 = v0 + per < n ? v0 + per : n;
+  double acc = 0.0;
+  for (int64_t v = v0; v < v1; ++v) acc += X[v * 16 + a] * X[v * 16 + b];
+  partials[(size_t)blockIdx.x * 256 + threadIdx.x] = acc;
+}
+
+void launch_gram16(int64_t n, const double* X, int grid, double* partials, cudaStream_t st) {
+  k_gram16<<<grid, 256, 0, st>>>(n, X, partials);
+}
+
+__global__ void k_reduce_cols(const double* partials, int nblk, int nv, double* out) {
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    double x = 0.0;
+    for (int b = 0; b < nblk; ++b) x += partials[(size_t)b * nv + k];
+    out[k] = x;
+  }
+}
+
+void launch_reduce_cols(const double* partials, int nblk, int nv, double* out, cudaStream_t st) {
+  k_reduce_cols<<<1, 256, 0, st>>>(partials, nblk, nv, out);
+}
+
+__global__ void __launch_bounds__(256) k_xform16(int64_t n, const double* __restrict__ T, double* X) {
+  __shared__ double sT[256];
+  sT[threadIdx.x] = T[threadIdx.x];
+  __syncthreads();
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    double x[16], y[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = X[v * 16 + k];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) s += x[k] * sT[16 * k + j];
+      y[j] = s;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) X[v * 16 + k] = y[k];
+  }
+}
+
+void launch_xform16(int64_t n, const double* T, double* X, cudaStream_t st) {
+  int grid = (int)((n + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_xform16<<<grid, 256, 0, st>>>(n, T, X);
+}
+
+// gam_j = gradient of mode j on tet i: sum_k (phi_j(v_k) - phi_j(v_3)) Dinv[k][:]
+template <typename TW>
+__global__ void __launch_bounds__(256) k_gamma(int64_t m, const int4* __restrict__ tet, const double* __restrict__ Dinv,
+                                               const double* __restrict__ X, TW* gam) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 t = tet[i];
+    double D[9];
+    load_dinv(Dinv, m, i, D);
+    for (int j = 0; j < 16; ++j) {
+      const double x3 = X[(int64_t)t.w * 16 + j];
+      const double e0 = X[(int64_t)t.x * 16 + j] - x3;
+      const double e1 = X[(int64_t)t.y * 16 + j] - x3;
+      const double e2 = X[(int64_t)t.z * 16 + j] - x3;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gam[(3 * j + c) * m + i] = (TW)(e0 * D[c] + e1 * D[3 + c] + e2 * D[6 + c]);
+    }
+  }
+}
+
+template <typename TW>
+void launch_gamma(int64_t m, const int4* tet, const double* Dinv, const double* X, TW* gam, cudaStream_t st) {
+  int grid = (int)((m + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_gamma<TW><<<grid, 256, 0, st>>>(m, tet, Dinv, X, gam);
+}
+
+// ------------------------------------------------------------ element API --
+template <typename T>
+__global__ void k_eval_stretch(const double* s, const double* prm, int64_t n, double* psi, double* grad, double* hess) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T sv[6], S[9], Sinv[9];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sv[k] = (T)s[6 * i + k];
+    ElemMat<T> e;
+    e.V = (T)prm[8 * i];
+    e.mu = (T)prm[8 * i + 1];
+    e.lam = (T)prm[8 * i + 2];
+    e.ka = (T)prm[8 * i + 3];
+    e.u[0] = (T)prm[8 * i + 4];
+    e.u[1] = (T)prm[8 * i + 5];
+    e.u[2] = (T)prm[8 * i + 6];
+    sym_from_s(sv, S);
+    const T J = inv3(S, Sinv);
+    const T lnJ = log(J);
+    if (psi) psi[i] = (double)(e.V * psi_stretch(S, e));
+    if (grad) {
+      T g[6];
+      stretch_gradient(S, Sinv, lnJ, e, g);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) grad[6 * i + k] = (double)g[k];
+    }
+    if (hess) {
+      T H[36];
+      stretch_hessian(Sinv, lnJ, e, H);
+#pragma unroll
+      for (int k = 0; k < 36; ++k) hess[36 * i + k] = (double)H[k];
+    }
+  }
+}
+
+void launch_eval_stretch(const double* s, const double* prm, int64_t n, int mixed, double* psi, double* grad,
+                         double* hess, cudaStream_t st) {
+  int grid = (int)((n + 127) / 128);
+  if (grid < 1) grid = 1;
+  if (mixed)
+    k_eval_stretch<float><<<grid, 128, 0, st>>>(s, prm, n, psi, grad, hess);
+  else
+    k_eval_stretch<double><<<grid, 128, 0, st>>>(s, prm, n, psi, grad, hess);
+}
+
+__global__ void k_eval_polar(const double* F, int64_t n, double* R, double* s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double X[9], Rr[9], S[9], sv[6];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] = F[9 * i + k];
+    polar_rotation(X, Rr, 1e-15, 60);
+    matTmul3(Rr, X, S);
+    s_from_mat(S, sv);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[9 * i + k] = Rr[k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s[6 * i + k] = sv[k];
+  }
+}
+
+void launch_eval_polar(const double* F, int64_t n, double* R, double* s, cudaStream_t st) {
+  int grid = (int)((n + 127) / 128);
+  if (grid < 1) grid = 1;
+  k_eval_polar<<<grid, 128, 0, st>>>(F, n, R, s);
+}
+
+__global__ void k_compose_F(int64_t m, const double* R, const double* s, double* F) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double Rr[9], sv[6], S[9], Fi[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Rr[k] = R[k * m + i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sv[k] = s[k * m + i];
+    sym_from_s(sv, S);
+    matmul3(Rr, S, Fi);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k * m + i] = Fi[k];
+  }
+}
+
+void launch_compose_F(int64_t m, const double* R, const double* s, double* F, cudaStream_t st) {
+  int grid = (int)((m + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_compose_F<<<grid, 256, 0, st>>>(m, R, s, F);
+}
+
+// explicit instantiations
+template void launch_grad<double>(const TetArgs<double>&, int, cudaStream_t);
+template void launch_grad<float>(const TetArgs<float>&, int, cudaStream_t);
+template void launch_syrk<double>(const TetArgs<double>&, int, double*, cudaStream_t);
+template void launch_syrk<float>(const TetArgs<float>&, int, double*, cudaStream_t);
+template void launch_dir<double>(const TetArgs<double>&, int, cudaStream_t);
+template void launch_dir<float>(const TetArgs<float>&, int, cudaStream_t);
+template void launch_ls<double>(const TetArgs<double>&, int, double, cudaStream_t);
+template void launch_ls<float>(const TetArgs<float>&, int, double, cudaStream_t);
+template void launch_update_tets<double>(const TetArgs<double>&, int, cudaStream_t);
+template void launch_update_tets<float>(const TetArgs<float>&, int, cudaStream_t);
+template void launch_gamma<double>(int64_t, const int4*, const double*, const double*, double*, cudaStream_t);
+template void launch_gamma<float>(int64_t, const int4*, const double*, const double*, float*, cudaStream_t);
+
+}  // namespace emu

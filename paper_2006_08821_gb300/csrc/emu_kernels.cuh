@@ -1,0 +1,81 @@
+// Declarations of the per-tet and per-vertex kernels of one Newton iteration.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "emu_internal.h"
+
+namespace emu {
+
+// Arrays the per-tet kernels read and write. FP64 path: TW = double.
+// Mixed path: TW = float for the Hessian / Woodbury quantities (Uw, y, d, gam).
+template <typename TW> struct TetArgs {
+  int64_t m, n;
+  const int4* tet;
+  const double* Dinv;   // 9m  (k*m + i)
+  const double* V;      // m
+  const double* c;      // m  alpha * w
+  const double* w;      // m
+  const double* mu;     // m
+  const double* lam;    // m
+  const double* u;      // 3m
+  const double* ka;     // m  kappa * a
+  const TW* gam;        // 48m (3j + c)*m + i
+  double* R;            // 9m
+  double* s;            // 6m
+  const double* q;      // 3n
+  const double* dq;     // 3n
+  double* g;            // 9m  F-space gradient
+  TW* y;                // 9m  H_F^-1 g
+  TW* d;                // 9m  search direction
+  TW* Uw;               // 54m chart factor
+  double* contrib;      // 12m corner contributions (slot 4i+k, 3 values)
+  const double* z;      // 48 Woodbury coefficients
+  DevScalars* sc;
+  double* partials;     // per-block partial sums
+};
+
+void launch_rhs_from_state(const TetArgs<double>& a, int grid, cudaStream_t st);
+template <typename TW> void launch_grad(const TetArgs<TW>& a, int grid, cudaStream_t st);
+template <typename TW> void launch_syrk(const TetArgs<TW>& a, int grid, double* cpart, cudaStream_t st);
+template <typename TW> void launch_dir(const TetArgs<TW>& a, int grid, cudaStream_t st);
+template <typename TW> void launch_ls(const TetArgs<TW>& a, int grid, double rho, cudaStream_t st);
+template <typename TW> void launch_update_tets(const TetArgs<TW>& a, int grid, cudaStream_t st);
+
+// Per-vertex RHS gather: b_v = sum over incident corner slots, minus the
+// pinned-column term (mode 0, coupling solve for q) or not (mode 1, dq).
+void launch_assemble(int64_t n, const int32_t* slot_ptr, const int32_t* slot_idx, const double* contrib,
+                     const double* bfix, const uint8_t* is_fixed, const double* qfix, int mode, double* b,
+                     cudaStream_t st);
+void launch_update_verts(int64_t n, const DevScalars* sc, const double* dq, double* q, cudaStream_t st);
+
+// Single-block reducers.
+void launch_reduce_grad(const double* partials, int nblk, DevScalars* sc, double* By, double* gsum,
+                        cudaStream_t st);
+void launch_cap_solve(const double* cpart, int nblk, const double* By, double* z, DevScalars* sc,
+                      cudaStream_t st);
+void launch_ls_select(const double* dir_partials, int nblk_dir, const double* ls_partials, int nblk_ls,
+                      DevScalars* sc, double sigma0, double rho, double c_armijo, cudaStream_t st);
+
+// Normaliser of the residual: ||g(F = I, q0)||^2 into out[0].
+void launch_gref(const TetArgs<double>& a, const double* q0, int grid, double* partials, double* out,
+                 cudaStream_t st);
+
+// Setup kernels for the low-rank basis.
+void launch_gram16(int64_t n, const double* X, int grid, double* partials, cudaStream_t st);
+void launch_reduce_cols(const double* partials, int nblk, int nv, double* out, cudaStream_t st);
+void launch_xform16(int64_t n, const double* T, double* X, cudaStream_t st);
+template <typename TW>
+void launch_gamma(int64_t m, const int4* tet, const double* Dinv, const double* X, TW* gam, cudaStream_t st);
+
+// Element-level evaluation entry points.
+void launch_eval_stretch(const double* s, const double* prm, int64_t n, int mixed, double* psi, double* grad,
+                         double* hess, cudaStream_t st);
+void launch_eval_polar(const double* F, int64_t n, double* R, double* s, cudaStream_t st);
+void launch_compose_F(int64_t m, const double* R, const double* s, double* F, cudaStream_t st);
+
+constexpr int kGradNV = 1 + kK;        // gnorm2 + By
+constexpr int kLsNV = kLsTrials + 2;   // dPsi per trial + c<D,dD> + c|dD|^2
+constexpr int kCapEntries = kK * kK;   // 48 x 48 partial capacitance
+
+}  // namespace emu

@@ -1,0 +1,93 @@
+"""Host-only checks of the C ABI: the library builds, loads and exports every
+entry point declared in include/emu.h; argument validation runs without a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from emu_inputs import box_beam
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2006_08821_gb300 import build as b
+
+    b.build()
+    from paper_2006_08821_gb300 import binding
+
+    return binding.load_library()
+
+
+def _header_functions():
+    text = open(os.path.join(ROOT, "include", "emu.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(emu_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_entry_point_is_exported(lib):
+    names = _header_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    from paper_2006_08821_gb300.binding import EXPORTED
+
+    assert sorted(EXPORTED) == names
+
+
+def test_default_params_and_status_strings(lib):
+    from paper_2006_08821_gb300 import binding
+
+    p = binding.default_params()
+    assert p.k_modes == 48 and p.alpha_rel == 1.0 and p.weight_mode == 0
+    assert p.ls_c == 1e-4 and p.ls_rho == 0.5  # Algorithm 1 constants
+    assert lib.emu_status_string(0) == b"ok"
+    assert lib.emu_status_string(-4) == b"not converged"
+
+
+def _desc(mesh):
+    from paper_2006_08821_gb300 import binding as B
+
+    keep = [np.ascontiguousarray(x) for x in (mesh.rest_pos, mesh.tets.astype(np.int32), mesh.youngs,
+                                                mesh.poisson, mesh.material_id.astype(np.uint8),
+                                                mesh.fiber_dir, mesh.fixed_verts.astype(np.int32))]
+    d = B.emu_mesh_desc()
+    d.n_verts, d.n_tets = mesh.n_verts, mesh.n_tets
+    d.rest_pos = keep[0].ctypes.data_as(C.POINTER(C.c_double))
+    d.tets = keep[1].ctypes.data_as(C.POINTER(C.c_int32))
+    d.n_materials = 1
+    d.youngs = keep[2].ctypes.data_as(C.POINTER(C.c_double))
+    d.poisson = keep[3].ctypes.data_as(C.POINTER(C.c_double))
+    d.material_id = keep[4].ctypes.data_as(C.POINTER(C.c_uint8))
+    d.fiber_dir = keep[5].ctypes.data_as(C.POINTER(C.c_double))
+    d.n_fixed = len(keep[6])
+    d.fixed_verts = keep[6].ctypes.data_as(C.POINTER(C.c_int32))
+    return d, keep
+
+
+@pytest.mark.parametrize("mutate,code", [
+    ("bad_index", -1), ("no_pins", -1), ("bad_poisson", -1), ("bad_kmodes", -1),
+])
+def test_create_rejects_invalid_input_before_touching_the_device(lib, mutate, code):
+    from paper_2006_08821_gb300 import binding as B
+
+    mesh = box_beam(1, 1, 2)
+    if mutate == "bad_index":
+        mesh.tets = mesh.tets.copy()
+        mesh.tets[0, 0] = mesh.n_verts + 5
+    if mutate == "bad_poisson":
+        mesh.poisson = np.array([0.5])
+    d, keep = _desc(mesh)
+    if mutate == "no_pins":
+        d.n_fixed = 0
+    p = B.Params().to_c()
+    if mutate == "bad_kmodes":
+        p.k_modes = 50
+    h = C.c_void_p()
+    rc = lib.emu_create(C.byref(d), C.byref(p), None, None, C.byref(h))
+    assert rc == code
+    assert not h.value
+    assert len(lib.emu_last_error()) > 0

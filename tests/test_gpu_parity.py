@@ -1,0 +1,187 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (positions, max over vertices, relative to the rest bounding-box
+diagonal):
+  * FP64 path: 1e-9 with both sides converged to a relative residual of
+    1e-11 (the oracle) / 1e-11 (GPU);
+  * mixed path: 1e-4 at the GPU's relative residual 1e-6.
+Converged positions are compared, never iterates: the oracle iterates on F
+(Sec. 3.2.1), the GPU on rotation/stretch pairs, and both reach the same
+stationary point of Eq. 5.
+"""
+import numpy as np
+import pytest
+
+from emu_inputs import box_beam, muscle_tendon_unit
+from oracle import EmuOracle, OracleParams, element_terms_s, lame, stretch_from_s
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def emu():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2006_08821_gb300 import build as b
+
+    b.build()
+    import paper_2006_08821_gb300 as emu
+
+    emu.load_library()
+    return emu
+
+
+def _diag(mesh):
+    return float(np.linalg.norm(mesh.rest_pos.max(0) - mesh.rest_pos.min(0)))
+
+
+def _solve_gpu(emu, mesh, a, precision=0, tol=1e-11, **kw):
+    p = emu.Params(tol_rel_residual=tol, precision=precision, **kw)
+    s = emu.Solver(mesh, p)
+    s.set_activation(a)
+    st = s.solve()
+    return s, st
+
+
+def _oracle(mesh, a, tol=1e-11):
+    o = EmuOracle(mesh, OracleParams(alpha_rel=1.0, weight_mode=0))
+    return o, o.solve(a, tol=tol)
+
+
+# ----------------------------------------------------------- element level --
+def test_stretch_terms_match_oracle(emu):
+    import torch
+
+    rng = np.random.default_rng(7)
+    n = 257  # several blocks and a ragged tail
+    B = rng.normal(size=(n, 3, 3)) * 0.15
+    S = np.eye(3) + 0.5 * (B + np.swapaxes(B, 1, 2))
+    from oracle import s_from_stretch
+
+    s = s_from_stretch(S)
+    mu, lam = lame(np.full(n, 6e5), np.full(n, 0.45))
+    ka = rng.uniform(0, 1, n) * mu
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    V = rng.uniform(1e-7, 2e-7, n)
+    prm = np.zeros((n, 8))
+    prm[:, 0], prm[:, 1], prm[:, 2], prm[:, 3], prm[:, 4:7] = V, mu, lam, ka, u
+    val, g, H = element_terms_s(s, mu, lam, ka, u, V)
+    # the definiteness fix only changes states with mu - lam ln J < 0
+    J = np.linalg.det(S)
+    exact = (mu - lam * np.log(J)) >= 0
+    dev = torch.device("cuda:0")
+    ts = torch.tensor(s, device=dev)
+    tp = torch.tensor(prm, device=dev)
+    for mixed, rtol in [(0, 1e-11), (1, 2e-4)]:
+        psi = torch.empty(n, dtype=torch.float64, device=dev)
+        grad = torch.empty((n, 6), dtype=torch.float64, device=dev)
+        hess = torch.empty((n, 36), dtype=torch.float64, device=dev)
+        emu.eval_stretch_terms(ts.data_ptr(), tp.data_ptr(), n, mixed, psi.data_ptr(), grad.data_ptr(),
+                               hess.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        scale = np.abs(V * mu).max()
+        np.testing.assert_allclose(psi.cpu().numpy(), val, rtol=rtol, atol=rtol * scale)
+        np.testing.assert_allclose(grad.cpu().numpy(), g, rtol=rtol, atol=rtol * scale)
+        Hg = hess.cpu().numpy().reshape(n, 6, 6)
+        np.testing.assert_allclose(Hg[exact], H[exact], rtol=rtol, atol=rtol * scale)
+        ev = np.linalg.eigvalsh(Hg)
+        assert np.all(ev >= (1 - 1e-3) * (V * mu)[:, None])
+
+
+def test_polar_decomposition_invariants(emu):
+    import torch
+
+    rng = np.random.default_rng(11)
+    n = 1000
+    A = rng.normal(size=(n, 3, 3))
+    Qr, _ = np.linalg.qr(A)
+    Qr *= np.sign(np.linalg.det(Qr))[:, None, None]
+    B = rng.normal(size=(n, 3, 3)) * 0.3
+    S0 = np.eye(3) + 0.5 * (B + np.swapaxes(B, 1, 2))
+    S0 = S0 @ S0  # SPD
+    F = Qr @ S0
+    dev = torch.device("cuda:0")
+    tF = torch.tensor(F.reshape(n, 9), device=dev)
+    tR = torch.empty((n, 9), dtype=torch.float64, device=dev)
+    ts = torch.empty((n, 6), dtype=torch.float64, device=dev)
+    emu.eval_polar(tF.data_ptr(), n, tR.data_ptr(), ts.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    R = tR.cpu().numpy().reshape(n, 3, 3)
+    S = stretch_from_s(ts.cpu().numpy())
+    np.testing.assert_allclose(R, Qr, atol=1e-12)  # polar of R0 S0 recovers R0
+    np.testing.assert_allclose(np.einsum("nji,njk->nik", R, R), np.broadcast_to(np.eye(3), R.shape), atol=1e-13)
+    np.testing.assert_allclose(np.linalg.det(R), 1.0, atol=1e-13)
+    np.testing.assert_allclose(R @ S, F, atol=1e-12 * np.abs(F).max())
+    assert np.all(np.linalg.eigvalsh(S) > 0)
+
+
+# ------------------------------------------------------------- full solves --
+def test_rest_state_takes_zero_iterations(emu):
+    mesh = box_beam(2, 2, 4)
+    s, st = _solve_gpu(emu, mesh, 0.0)
+    assert st.newton_iters == 0
+    np.testing.assert_allclose(s.positions(), mesh.rest_pos, atol=1e-13)
+
+
+@pytest.mark.parametrize("dims,act", [((2, 2, 6), 0.5), ((4, 4, 16), 0.5), ((3, 5, 7), 0.8)])
+def test_fp64_path_matches_oracle(emu, dims, act):
+    mesh = box_beam(*dims, activation=act)
+    o, r = _oracle(mesh, act)
+    s, st = _solve_gpu(emu, mesh, act)
+    q = s.positions()
+    err = np.abs(q - r.q).max() / _diag(mesh)
+    assert st.rel_residual <= 1e-11
+    assert err <= 1e-9, (err, st.newton_iters, r.iterations)
+    # element invariants of the final state
+    R, sv, F = s.element_state()
+    np.testing.assert_allclose(np.einsum("nji,njk->nik", R, R), np.broadcast_to(np.eye(3), R.shape), atol=1e-12)
+    np.testing.assert_allclose(np.linalg.det(R), 1.0, atol=1e-12)
+    assert np.all(np.linalg.eigvalsh(stretch_from_s(sv)) > 0)
+    np.testing.assert_allclose(F, r.F, atol=1e-8)
+
+
+def test_fp64_muscle_tendon_unit_matches_oracle(emu):
+    mesh = muscle_tendon_unit(4, 4, 14, h=0.01, radius_cells=1.9, frames=1, a_max=0.6)
+    a = mesh.activations[0]
+    o, r = _oracle(mesh, a, tol=1e-10)
+    s, st = _solve_gpu(emu, mesh, a, tol=1e-10)
+    err = np.abs(s.positions() - r.q).max() / _diag(mesh)
+    assert err <= 1e-8, (err, st.newton_iters, r.iterations)
+
+
+def test_mixed_path_matches_oracle_at_1e6(emu):
+    mesh = box_beam(4, 4, 16, activation=0.5)
+    o, r = _oracle(mesh, 0.5)
+    s, st = _solve_gpu(emu, mesh, 0.5, precision=1, tol=1e-6)
+    assert st.rel_residual <= 1e-6
+    err = np.abs(s.positions() - r.q).max() / _diag(mesh)
+    assert err <= 1e-4, err
+
+
+def test_warm_started_frames_match_oracle(emu):
+    mesh = muscle_tendon_unit(3, 3, 10, h=0.01, radius_cells=1.6, frames=4, a_max=0.8)
+    o = EmuOracle(mesh, OracleParams(alpha_rel=1.0, weight_mode=0))
+    s = emu.Solver(mesh, emu.Params(tol_rel_residual=1e-11))
+    F = None
+    for f in range(mesh.activations.shape[0]):
+        a = mesh.activations[f]
+        r = o.solve(a, F0=F, tol=1e-11)
+        F = r.F
+        s.set_activation(a)
+        s.solve()
+        err = np.abs(s.positions() - r.q).max() / _diag(mesh)
+        assert err <= 1e-9, (f, err)
+
+
+def test_affine_patch_on_gpu(emu):
+    mesh = box_beam(3, 3, 3, h=0.01, activation=0.3)
+    Q = mesh.rest_pos
+    bnd = np.nonzero(np.any((Q < 1e-12) | (Q > 0.03 - 1e-12), axis=1))[0].astype(np.int32)
+    A = np.array([[1.05, 0.08, 0.0], [-0.03, 0.97, 0.05], [0.02, 0.0, 1.02]])
+    b = np.array([0.001, -0.002, 0.003])
+    mesh.fixed_verts = bnd
+    mesh.fixed_pos = Q[bnd] @ A.T + b
+    s, st = _solve_gpu(emu, mesh, 0.3, tol=1e-12)
+    np.testing.assert_allclose(s.positions(), Q @ A.T + b, atol=1e-13)
+    _, _, F = s.element_state()
+    np.testing.assert_allclose(F, np.broadcast_to(F[0], F.shape), atol=1e-11)
