@@ -77,30 +77,31 @@ def make_workload(name):
     raise ValueError(name)
 
 
-def algorithmic_bytes_per_tet(phase, mixed, n_over_m, nnz_per_row):
-    """Minimum HBM bytes per tet of one launch of a per-tet phase (one pass over
-    the per-tet records; vertex arrays counted once per vertex)."""
-    tw = 4 if mixed else 8
-    rec = 16 + 72 + 8 * 8  # tet indices, D_m^-1, V, c, w, mu, lam, ka, 2 of u ... (u counted below)
-    u = 24
-    state = 72 + 48        # R, s
-    vert = 24 * n_over_m   # q gathered, each vertex once
-    if phase == "grad":
-        return rec + u + state + vert + 72 + 9 * tw + 54 * tw   # + write g, y, Uw
-    if phase == "dir":
-        return 48 * tw + 54 * tw + 9 * tw + 72 + 72 + 8 + 9 * tw + 96  # gam, Uw, y, g, Dinv, w -> d, corner terms
-    if phase == "ls":
-        return rec + u + state + 9 * tw + 2 * vert
-    if phase == "update":
-        return state + 9 * tw + state + 48 * n_over_m
-    if phase == "syrk":
-        return 54 * tw + 48 * tw + 9 * tw + 8
-    if phase == "rhs":
-        return 16 + 72 + state + 8 + 96
+def algorithmic_bytes(phase, mixed, m, n, nnz, cg_iters):
+    """Minimum bytes one launch of a phase must move (each array read or
+    written once; vertex arrays once per vertex), for the roofline.
+
+    Per-tet phases count per-tet records of the mixed (FP32) or FP64 layout;
+    the ACAP solve counts, per CG iteration, the CSR matrix (value + column
+    index), D^-1, the 16 coarse-basis values and six 3-vectors read and
+    written once, times the CG iterations of the launch."""
+    f = 4 if mixed else 8
+    rec = 16 + 9 * f + 6 * f + 3 * f          # tet, D^-1, V c w mu lam ka, u
+    state = (16 + 6 * 4) if mixed else (72 + 48)
+    vert = 24 * n / m                          # q gathered, each vertex once
+    per_tet = {
+        "grad": rec + state + vert + 9 * f + 9 * f + 9 * f + 54 * f,   # + E0 (mixed), write g, y, Uw
+        "dir": 48 * f + 54 * f + 9 * f + 9 * f + 9 * f + f + 9 * f + 96,  # gam, Uw, y, g, D^-1, w -> d, corner terms
+        "ls": rec + state + 9 * f + 2 * vert + (9 * 4 if mixed else 0),
+        "update": 2 * state + 9 * f,
+        "syrk": 54 * f + 48 * f + 9 * f + f,
+        "rhs": 16 + 9 * f + state + f + 96,
+    }
+    if phase in per_tet:
+        return per_tet[phase] * m
     if phase == "pcg":
-        # per CG iteration and vertex: matrix (12 B/nnz + rowptr) and the
-        # x, p, r, s, u, w vectors (3 RHS) read and written once, D^-1
-        return n_over_m * (12 * nnz_per_row + 4 + 8 + 6 * 48)
+        per_iter = nnz * (f + 4) + n * (4 + f + 16 * f + 6 * 2 * 3 * f)
+        return per_iter * cg_iters
     return None
 
 
@@ -157,6 +158,19 @@ class ClockSampler:
         out.update(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
                    reasons=sorted(reasons), samples=len(rows))
         return out
+
+
+def solver_nnz(mesh):
+    """Non-zeros of the scalar ACAP Laplacian (free-free couplings plus the
+    pinned identity rows), counted from the tet connectivity."""
+    T = np.asarray(mesh.tets, dtype=np.int64)
+    fixed = np.zeros(mesh.n_verts, dtype=bool)
+    fixed[np.asarray(mesh.fixed_verts)] = True
+    a = T[:, :, None].repeat(4, 2).reshape(-1)
+    b = T[:, None, :].repeat(4, 1).reshape(-1)
+    keep = ~fixed[a] & ~fixed[b]
+    pairs = np.unique(a[keep] * mesh.n_verts + b[keep])
+    return int(pairs.size + fixed.sum())
 
 
 def cpu_baseline(workload_name, budget_s=15.0):
@@ -260,7 +274,7 @@ def main():
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    frame_ms, e2e_s, iters, resid = [], [], [], []
+    frame_ms, e2e_s, iters, resid, cg = [], [], [], [], []
     act_pinned = torch.empty(m, dtype=torch.float64).pin_memory()
     for f in range(1 + args.warmup, 1 + args.warmup + args.steps):
         with torch.cuda.stream(stream):
@@ -281,6 +295,7 @@ def main():
         e2e_s.append(t1 - t0)
         iters.append(st.newton_iters)
         resid.append(st.rel_residual)
+        cg.append(st.pcg_iters)
     torch.cuda.synchronize()
     clk = clocks.stop()
     prof, launches = solver.profile()
@@ -294,23 +309,23 @@ def main():
     value = tet_iters / (total_ms / 1e3)
     e2e_value = tet_iters / total_e2e
 
-    # roofline of the dominant kernel phase
+    # roofline of the dominant kernel phase (device time from the library's
+    # per-phase CUDA events on the solver's stream)
     peak, peak_kind = hbm_peak()
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     name, (ms_tot, nl) = dom
-    nnz_per_row = 15.0
-    per = algorithmic_bytes_per_tet(name, mixed, n / m, nnz_per_row)
+    nnz = solver_nnz(mesh)
+    total_bytes = algorithmic_bytes(name, mixed, m, n, nnz, float(np.sum(cg)))
     roof = None
-    if per is not None and nl > 0:
-        if name == "pcg":
-            units = m * prof["pcg"][1]  # placeholder: per-launch iterations unknown here
-            roof = None
-        else:
-            bytes_per_launch = per * m
-            achieved = bytes_per_launch / (ms_tot / nl / 1e3) / 1e9
-            roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                    "bytes_per_launch": bytes_per_launch, "avg_launch_ms": ms_tot / nl}
+    if total_bytes is not None and nl > 0 and ms_tot > 0:
+        # per-tet phases: one launch moves total_bytes; the ACAP solve's
+        # bytes are summed over all its CG iterations
+        bytes_per_launch = total_bytes / nl if name == "pcg" else total_bytes
+        achieved = bytes_per_launch / (ms_tot / nl / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": ms_tot / nl,
+                "share_of_device_time": ms_tot / max(1e-9, sum(v[0] for v in prof.values()))}
     line = {
         "metric": "tet-iters/s", "value": value, "unit": "tet-iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -320,6 +335,7 @@ def main():
         "ms_per_converged_frame_p50": float(np.median(frame_ms)),
         "frame_ms_p99": float(np.percentile(frame_ms, 99)),
         "newton_iters_per_frame": [int(x) for x in iters],
+        "cg_iters_per_frame": [int(x) for x in cg],
         "max_rel_residual": float(np.max(resid)),
         "setup_s": setup_s,
         "phase_ms": {k: round(v[0], 3) for k, v in prof.items()},

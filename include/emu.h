@@ -113,13 +113,22 @@ typedef struct {
  *   max_newton      Newton iteration cap per solve.
  *   ls_sigma0, ls_c, ls_rho, ls_max_trials   Armijo backtracking
  *                   (Algorithm 1 uses 10, 1e-4, 0.5).
- *   pcg_tol         relative residual of each ACAP solve.
+ *   pcg_tol         relative residual of the exact coupling solve q = q*(F)
+ *                   (Eq. 4); the solve used is min(pcg_tol, 1e-2 * tol),
+ *                   floored at 1e-13.
  *   pcg_max         CG iteration cap per ACAP solve.
  *   precision       EMU_PRECISION_FP64 or EMU_PRECISION_MIXED (per-tet
  *                   Hessian/Woodbury work in FP32; state, gradient,
  *                   residual, line-search sums and ACAP solve in FP64).
  *   mode_iters      subspace iterations used to build the low-rank basis.
- *   seed            seeds the random start of the subspace iteration. */
+ *   seed            seeds the random start of the subspace iteration.
+ *   dq_tol          relative residual of the per-iteration solve for the
+ *                   change of q along the search direction (q*(F + s d) =
+ *                   q + s dq, q* being affine); q itself is then updated by
+ *                   linearity (default 1e-4).
+ *   q_refresh       every q_refresh iterations, and before convergence is
+ *                   declared, q is re-solved exactly from the current F
+ *                   (default 16). */
 typedef struct {
   double alpha_rel;
   int32_t weight_mode;
@@ -136,6 +145,8 @@ typedef struct {
   int32_t precision;
   int32_t mode_iters;
   uint64_t seed;
+  double dq_tol;
+  int32_t q_refresh;
 } emu_params;
 
 /* Per-solve statistics. */

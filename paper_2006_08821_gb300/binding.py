@@ -90,6 +90,8 @@ class emu_params(C.Structure):
         ("precision", C.c_int32),
         ("mode_iters", C.c_int32),
         ("seed", C.c_uint64),
+        ("dq_tol", C.c_double),
+        ("q_refresh", C.c_int32),
     ]
 
 
@@ -170,11 +172,13 @@ class Params:
     ls_c: float = 1e-4
     ls_rho: float = 0.5
     ls_max_trials: int = 40
-    pcg_tol: float = 1e-12
+    pcg_tol: float = 1e-8
     pcg_max: int = 5000
     precision: int = PRECISION_FP64
     mode_iters: int = 4
     seed: int = 12345
+    dq_tol: float = 1e-4
+    q_refresh: int = 16
 
     def to_c(self) -> emu_params:
         p = emu_params()

@@ -13,6 +13,7 @@
 
 #include "emu_internal.h"
 #include "emu_kernels.cuh"
+#include "emu_mixed.cuh"
 #include "emu_pcg.h"
 
 using namespace emu;
@@ -68,8 +69,25 @@ struct emu_handle {
   double* contrib = nullptr;
   double* b = nullptr;
   double *pr = nullptr, *pu = nullptr, *pw = nullptr, *pp = nullptr, *ps = nullptr;
+  // mixed path: FP32 constants and state, FP32 CG work vectors
+  float *Dinv32 = nullptr, *V32 = nullptr, *c32 = nullptr, *w32 = nullptr, *mu32 = nullptr, *lam32 = nullptr,
+        *u32 = nullptr, *ka32 = nullptr, *E32 = nullptr, *g32 = nullptr, *dq32 = nullptr, *b32 = nullptr,
+        *r32 = nullptr, *e32 = nullptr;
+  float4* quat = nullptr;
+  float* E0 = nullptr;     // 9m: G_i Q - I of the FP32 D_m^-1
+  double* Qrest = nullptr;  // 3n rest positions
+  float *val32 = nullptr, *ldinv32 = nullptr;
+  float *fr = nullptr, *fu = nullptr, *fw = nullptr, *fp = nullptr, *fs = nullptr;
+  // coarse space of the ACAP preconditioner: the low-rank basis Phi (n x 16)
+  // and the pseudo-inverse of Phi^T L Phi
+  double* phi64 = nullptr;
+  float* phi32 = nullptr;
+  double* Einv = nullptr;
+  bool coarse_ready = false;
+  double q_tol = 1e-8;
   double *part_grad = nullptr, *part_dir = nullptr, *part_ls = nullptr, *part_pcg = nullptr, *cpart = nullptr;
   double* z = nullptr;
+  double* cfull = nullptr;  // summed capacitance entries
   double* scratch16 = nullptr;  // n x 16 mode vectors
   double* small = nullptr;      // 256 doubles of small-matrix exchange
   DevScalars* sc = nullptr;
@@ -169,13 +187,13 @@ struct emu_handle {
 
   template <typename TW> TetArgs<TW> args();
 
-  PcgArgs pcg_args(const double* rhs, double* x, int nrhs) {
-    PcgArgs a;
-    a.L.n = n;
-    a.L.rowptr = rowptr;
-    a.L.col = col;
-    a.L.val = val;
-    a.L.dinv = ldinv;
+  PcgArgsT<double> pcg64(const double* rhs, double* x, double tol) {
+    PcgArgsT<double> a;
+    a.n = n;
+    a.rowptr = rowptr;
+    a.col = col;
+    a.val = val;
+    a.dinv = ldinv;
     a.b = rhs;
     a.x = x;
     a.r = pr;
@@ -185,13 +203,73 @@ struct emu_handle {
     a.s = ps;
     a.partials = part_pcg;
     a.bar = bar;
-    a.tol = prm.pcg_tol;
+    a.tol = tol;
     a.max_iter = prm.pcg_max;
     a.iters_out = &sc->pcg_iters;
     a.fail_out = &sc->pcg_fail;
     a.timeout_out = &sc->barrier_timeout;
     a.last_iters = nullptr;
-    (void)nrhs;
+    a.relres_out = nullptr;
+    a.phi = coarse_ready ? phi64 : nullptr;
+    a.Einv = coarse_ready ? Einv : nullptr;
+    return a;
+  }
+  PcgArgsT<float> pcg32(const float* rhs, float* x, double tol) {
+    PcgArgsT<float> a;
+    a.n = n;
+    a.rowptr = rowptr;
+    a.col = col;
+    a.val = val32;
+    a.dinv = ldinv32;
+    a.b = rhs;
+    a.x = x;
+    a.r = fr;
+    a.u = fu;
+    a.w = fw;
+    a.p = fp;
+    a.s = fs;
+    a.partials = part_pcg;
+    a.bar = bar;
+    a.tol = tol;
+    a.max_iter = prm.pcg_max;
+    a.iters_out = &sc->pcg_iters;
+    a.fail_out = &sc->pcg_fail;
+    a.timeout_out = &sc->barrier_timeout;
+    a.last_iters = nullptr;
+    a.relres_out = nullptr;
+    a.phi = coarse_ready ? phi32 : nullptr;
+    a.Einv = coarse_ready ? Einv : nullptr;
+    return a;
+  }
+  MixArgs margs() {
+    MixArgs a;
+    a.m = m;
+    a.n = n;
+    a.tet = tet;
+    a.Dinv = Dinv32;
+    a.V = V32;
+    a.c = c32;
+    a.w = w32;
+    a.mu = mu32;
+    a.lam = lam32;
+    a.ka = ka32;
+    a.u = u32;
+    a.gam = gam32;
+    a.quat = quat;
+    a.E = E32;
+    a.q = q;
+    a.Q = Qrest;
+    a.E0 = E0;
+    a.dq = dq32;
+    a.g = g32;
+    a.y = y32;
+    a.d = d32;
+    a.Uw = Uw32;
+    a.contrib = contrib;
+    a.b32 = b32;
+    a.z = z;
+    a.sc = sc;
+    a.partials = part_grad;
     return a;
   }
 };
@@ -340,21 +418,80 @@ int validate_params(const emu_params* p) {
   if (p->precision != EMU_PRECISION_FP64 && p->precision != EMU_PRECISION_MIXED)
     return fail(EMU_ERR_INVALID_ARG, "precision must be FP64 or MIXED");
   if (p->mode_iters < 1 || p->mode_iters > 50) return fail(EMU_ERR_INVALID_ARG, "mode_iters must be 1..50");
+  if (!(p->dq_tol > 0.0 && p->dq_tol < 1.0)) return fail(EMU_ERR_INVALID_ARG, "dq_tol must be in (0, 1)");
+  if (p->q_refresh < 1) return fail(EMU_ERR_INVALID_ARG, "q_refresh must be >= 1");
   return EMU_OK;
 }
 
-// Runs the coupling solve q = q*(R S) with q as the warm start.
-int coupling_solve(emu_handle* h) {
-  TetArgs<double> a = h->args<double>();
+int read_scalars(emu_handle* h);
+
+// Exact coupling solve q = q*(F) of Eq. 4 from the current F, warm-started
+// from the current q, to relative residual ``tol``. FP64 path: FP64 CG.
+// Mixed path: iterative refinement, the residual b - K q in FP64 and the
+// correction from an FP32 CG, until the FP64 residual meets ``tol``.
+int refresh_q(emu_handle* h, double tol) {
+  if (!h->mixed) {
+    TetArgs<double> a = h->args<double>();
+    h->ph_begin();
+    launch_rhs_from_state(a, h->grid_tet, h->st);
+    h->ph_end(EMU_PHASE_RHS, 1);
+    h->ph_begin();
+    launch_assemble(h->n, h->slot_ptr, h->slot_idx, h->contrib, h->bfix, h->is_fixed, h->qfix, 0, h->b, h->st);
+    h->ph_end(EMU_PHASE_ASSEMBLE, 1);
+    EMU_CK(cudaGetLastError());
+    h->ph_begin();
+    EMU_CK(launch_pcg<double>(3, h->pcg64(h->b, h->q, tol), h->grid_pcg3, h->st));
+    h->ph_end(EMU_PHASE_PCG, 1);
+    return EMU_OK;
+  }
+  MixArgs ma = h->margs();
   h->ph_begin();
-  launch_rhs_from_state(a, h->grid_tet, h->st);
+  launch_rhs_state_mixed(ma, h->grid_tet, h->st);
   h->ph_end(EMU_PHASE_RHS, 1);
   h->ph_begin();
   launch_assemble(h->n, h->slot_ptr, h->slot_idx, h->contrib, h->bfix, h->is_fixed, h->qfix, 0, h->b, h->st);
   h->ph_end(EMU_PHASE_ASSEMBLE, 1);
   EMU_CK(cudaGetLastError());
+  const int rgrid = (int)std::min<int64_t>(std::max<int64_t>(1, (h->n + 255) / 256), 2 * (int64_t)h->sms);
+  for (int round = 0; round < 8; ++round) {
+    h->ph_begin();
+    EMU_CK(launch_residual64(h->n, h->rowptr, h->col, h->val, h->b, h->q, h->r32, h->part_pcg, rgrid, h->small, h->st));
+    h->ph_end(EMU_PHASE_PCG, 2);
+    double o6[6];
+    EMU_CK(cudaMemcpyAsync(o6, h->small, sizeof(o6), cudaMemcpyDeviceToHost, h->st));
+    int rc = read_scalars(h);
+    if (rc) return rc;
+    bool done = true;
+    for (int j = 0; j < 3; ++j) done = done && (o6[j] <= tol * tol * o6[3 + j]);
+    if (done) break;
+    EMU_CK(cudaMemsetAsync(h->e32, 0, 12 * h->n, h->st));
+    h->ph_begin();
+    EMU_CK(launch_pcg<float>(3, h->pcg32(h->r32, h->e32, 1e-5), h->grid_pcg3, h->st));
+    EMU_CK(launch_axpy_f2d(3 * h->n, h->e32, h->q, h->st));
+    h->ph_end(EMU_PHASE_PCG, 2);
+  }
+  return EMU_OK;
+}
+
+// dq: the linear change of q* along the direction d, to dq_tol (loose).
+int solve_dq(emu_handle* h) {
+  const double tol = h->prm.dq_tol;
+  if (!h->mixed) {
+    h->ph_begin();
+    launch_assemble(h->n, h->slot_ptr, h->slot_idx, h->contrib, h->bfix, h->is_fixed, h->qfix, 1, h->b, h->st);
+    h->ph_end(EMU_PHASE_ASSEMBLE, 1);
+    EMU_CK(cudaGetLastError());
+    h->ph_begin();
+    EMU_CK(launch_pcg<double>(3, h->pcg64(h->b, h->dq, tol), h->grid_pcg3, h->st));
+    h->ph_end(EMU_PHASE_PCG, 1);
+    return EMU_OK;
+  }
   h->ph_begin();
-  EMU_CK(launch_pcg(3, h->pcg_args(h->b, h->q, 3), h->grid_pcg3, h->st));
+  launch_assemble_f(h->n, h->slot_ptr, h->slot_idx, h->contrib, h->is_fixed, h->b32, h->st);
+  h->ph_end(EMU_PHASE_ASSEMBLE, 1);
+  EMU_CK(cudaGetLastError());
+  h->ph_begin();
+  EMU_CK(launch_pcg<float>(3, h->pcg32(h->b32, h->dq32, tol), h->grid_pcg3, h->st));
   h->ph_end(EMU_PHASE_PCG, 1);
   return EMU_OK;
 }
@@ -368,6 +505,11 @@ int set_rest_state(emu_handle* h) {
   EMU_CK(cudaMemcpyAsync(h->R, Rh.data(), Rh.size() * 8, cudaMemcpyHostToDevice, h->st));
   EMU_CK(cudaMemcpyAsync(h->s, sh.data(), sh.size() * 8, cudaMemcpyHostToDevice, h->st));
   EMU_CK(cudaMemsetAsync(h->dq, 0, 3 * h->n * 8, h->st));
+  if (h->mixed) {
+    launch_Rs_to_mixed(h->m, h->R, h->s, h->quat, h->E32, h->st);
+    EMU_CK(cudaGetLastError());
+    EMU_CK(cudaMemsetAsync(h->dq32, 0, 3 * h->n * 4, h->st));
+  }
   EMU_CK(cudaStreamSynchronize(h->st));
   return EMU_OK;
 }
@@ -401,12 +543,11 @@ int build_modes(emu_handle* h) {
   for (int it = 0; it < h->prm.mode_iters; ++it) {
     // Y = L^-1 X (pinned rows: right-hand side 0)
     EMU_CK(cudaMemsetAsync(Yd, 0, n * 16 * 8, h->st));
-    PcgArgs a = h->pcg_args(Xd, Yd, 16);
-    a.tol = 1e-6;
+    PcgArgsT<double> a = h->pcg64(Xd, Yd, 1e-6);
     a.max_iter = std::max(h->prm.pcg_max, 1000);
     a.iters_out = nullptr;
     a.fail_out = nullptr;
-    EMU_CK(launch_pcg(16, a, h->grid_pcg16, h->st));
+    EMU_CK(launch_pcg<double>(16, a, h->grid_pcg16, h->st));
     // orthonormalise: Y^T Y = L L^T, X = Y L^-T
     launch_gram16(n, Yd, ggrid, h->part_pcg, h->st);
     launch_reduce_cols(h->part_pcg, ggrid, 256, h->small, h->st);
@@ -445,7 +586,31 @@ int build_modes(emu_handle* h) {
   else
     launch_gamma<double>(h->m, h->tet, h->Dinv, Xd, h->gam64, h->st);
   EMU_CK(cudaGetLastError());
+  // coarse space of the ACAP preconditioner: Phi and (Phi^T L Phi)^+
+  EMU_CK(cudaMemcpyAsync(h->phi64, Xd, n * 16 * 8, cudaMemcpyDeviceToDevice, h->st));
+  if (h->mixed) launch_d2f(n * 16, h->phi64, h->phi32, h->st);
+  launch_galerkin16(n, h->rowptr, h->col, h->val, h->phi64, Yd, ggrid, h->part_pcg, h->st);
+  launch_reduce_cols(h->part_pcg, ggrid, 256, h->small, h->st);
+  EMU_CK(cudaGetLastError());
+  std::vector<double> Eg(256);
+  EMU_CK(cudaMemcpyAsync(Eg.data(), h->small, 256 * 8, cudaMemcpyDeviceToHost, h->st));
   EMU_CK(cudaStreamSynchronize(h->st));
+  for (int i = 0; i < 16; ++i)
+    for (int j = 0; j < 16; ++j) Eg[16 * i + j] = 0.5 * (Eg[16 * i + j] + Eg[16 * j + i]);
+  std::vector<double> Ev;
+  host_jacobi_eig(Eg, Ev, 16);
+  double emax = 0.0;
+  for (int i = 0; i < 16; ++i) emax = std::max(emax, Eg[17 * i]);
+  std::vector<double> Ei(256, 0.0);
+  for (int k = 0; k < 16; ++k) {
+    const double lk = Eg[17 * k];
+    if (!(lk > 1e-12 * emax)) continue;
+    for (int i = 0; i < 16; ++i)
+      for (int j = 0; j < 16; ++j) Ei[16 * i + j] += Ev[16 * i + k] * Ev[16 * j + k] / lk;
+  }
+  EMU_CK(cudaMemcpyAsync(h->Einv, Ei.data(), 256 * 8, cudaMemcpyHostToDevice, h->st));
+  EMU_CK(cudaStreamSynchronize(h->st));
+  h->coarse_ready = emax > 0.0;
   return EMU_OK;
 }
 
@@ -478,10 +643,12 @@ void emu_default_params(emu_params* p) {
   p->ls_c = 1e-4;
   p->ls_rho = 0.5;
   p->ls_max_trials = 40;
-  p->pcg_tol = 1e-12;
+  p->pcg_tol = 1e-8;
   p->pcg_max = 5000;
   p->precision = EMU_PRECISION_FP64;
   p->mode_iters = 4;
+  p->dq_tol = 1e-4;
+  p->q_refresh = 16;
   p->seed = 12345;
 }
 
@@ -590,6 +757,13 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     for (int k = 0; k < 4; ++k) tet[4 * i + k] = t[k];
   }
 
+  if (h->mixed) {
+    // The FP32 kernels see D_m^-1 and V rounded to FP32; the FP64 Laplacian
+    // and right-hand sides are built from the same rounded values.
+    for (int64_t k = 0; k < 9 * m; ++k) Dinv[k] = (double)(float)Dinv[k];
+    for (int64_t i = 0; i < m; ++i) V[i] = (double)(float)V[i];
+  }
+
   // ---- materials, weights (Eq. 3 with the Sec. 3.3 weights option) ----
   std::vector<double> mu(m), lam(m), wv(m), cv(m), uv(3 * m, 0.0);
   double mu_ref = 1e300;
@@ -606,6 +780,7 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
   double fl = 0.0;
   for (int64_t i = 0; i < m; ++i) {
     wv[i] = prm.weight_mode == 1 ? V[i] * std::max(1.0, mu[i] / mu_ref) : V[i];
+    if (h->mixed) wv[i] = (double)(float)wv[i];
     cv[i] = h->alpha * wv[i];
     fl += (V[i] * mu[i]) * (V[i] * mu[i]);
     if (desc->fiber_dir) {
@@ -622,6 +797,7 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
   }
   h->floor = 1e-12 * std::sqrt(fl);
   h->V_h = V;
+  h->q_tol = std::max(1e-13, std::min(prm.pcg_tol, 1e-2 * prm.tol_rel_residual));
 
   // ---- pins ----
   std::vector<uint8_t> is_fixed(n, 0);
@@ -696,22 +872,30 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
        h->get(h->mu, m) && h->get(h->lam, m) && h->get(h->u, 3 * m) && h->get(h->ka, m);
   ok = ok && h->get(h->R, 9 * m) && h->get(h->s, 6 * m) && h->get(h->q, 3 * n) && h->get(h->dq, 3 * n) &&
        h->get(h->q0, 3 * n) && h->get(h->g, 9 * m) && h->get(h->contrib, 12 * m) && h->get(h->b, 16 * n);
-  if (h->mixed)
+  if (h->mixed) {
     ok = ok && h->get(h->gam32, 48 * m) && h->get(h->y32, 9 * m) && h->get(h->d32, 9 * m) && h->get(h->Uw32, 54 * m);
-  else
+    ok = ok && h->get(h->Dinv32, 9 * m) && h->get(h->V32, m) && h->get(h->c32, m) && h->get(h->w32, m) &&
+         h->get(h->mu32, m) && h->get(h->lam32, m) && h->get(h->u32, 3 * m) && h->get(h->ka32, m) &&
+         h->get(h->E32, 6 * m) && h->get(h->g32, 9 * m) && h->get(h->quat, m) && h->get(h->dq32, 3 * n) &&
+         h->get(h->b32, 3 * n) && h->get(h->r32, 3 * n) && h->get(h->e32, 3 * n) && h->get(h->fr, 3 * n) &&
+         h->get(h->fu, 3 * n) && h->get(h->fw, 3 * n) && h->get(h->fp, 3 * n) && h->get(h->fs, 3 * n) &&
+         h->get(h->E0, 9 * m) && h->get(h->Qrest, 3 * n);
+  } else
     ok = ok && h->get(h->gam64, 48 * m) && h->get(h->y64, 9 * m) && h->get(h->d64, 9 * m) && h->get(h->Uw64, 54 * m);
   ok = ok && h->get(h->pr, 16 * n) && h->get(h->pu, 16 * n) && h->get(h->pw, 16 * n) && h->get(h->pp, 16 * n) &&
-       h->get(h->ps, 16 * n) && h->get(h->scratch16, 32 * n);
+       h->get(h->ps, 16 * n) && h->get(h->scratch16, 32 * n) && h->get(h->phi64, 16 * n) && h->get(h->Einv, 256);
+  if (h->mixed) ok = ok && h->get(h->phi32, 16 * n);
   h->grid_tet = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 127) / 128), 8 * (int64_t)h->sms);
-  h->grid_syrk = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 15) / 16), 2 * (int64_t)h->sms);
+  h->grid_syrk = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 23) / 24), 2 * (int64_t)h->sms);
   h->grid_pcg3 = pcg_max_grid(3, n);
   h->grid_pcg16 = pcg_max_grid(16, n);
-  const int pcg_part = std::max(h->grid_pcg3 * 12, h->grid_pcg16 * 64);
+  const int pcg_part = std::max(h->grid_pcg3 * (4 * 3 + 3 * kModes), h->grid_pcg16 * 64);  // per-block partials
   const int64_t gpart = std::max<int64_t>(h->grid_tet * (int64_t)kLsNV, 256 * (int64_t)(2 * h->sms + 1));
   ok = ok && h->get(h->part_grad, gpart) && h->get(h->part_dir, h->grid_tet) && h->get(h->part_ls, h->grid_tet * kLsNV) &&
        h->get(h->part_pcg, std::max<int64_t>(pcg_part, 256 * (int64_t)(2 * h->sms + 1))) &&
-       h->get(h->cpart, (int64_t)h->grid_syrk * (kCapEntries + kK)) && h->get(h->z, kK) && h->get(h->small, 256) &&
+       h->get(h->cpart, (int64_t)h->grid_syrk * (kCapEntries + kK)) && h->get(h->z, kK) && h->get(h->cfull, kCapEntries + kK) && h->get(h->small, 256) &&
        h->get(h->sc, 1) && h->get(h->bar, 1);
+  if (h->mixed) ok = ok && h->get(h->val32, nnz) && h->get(h->ldinv32, n);
   ok = ok && h->get(h->rowptr, n + 1) && h->get(h->col, nnz) && h->get(h->val, nnz) && h->get(h->ldinv, n) &&
        h->get(h->bfix, 3 * n) && h->get(h->qfix, 3 * n) && h->get(h->is_fixed, n) && h->get(h->slot_ptr, n + 1) &&
        h->get(h->slot_idx, 4 * m);
@@ -737,6 +921,31 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
        up(h->ldinv, ldinv.data(), 8 * n) && up(h->bfix, bfix.data(), 24 * n) && up(h->qfix, qfix.data(), 24 * n) &&
        up(h->is_fixed, is_fixed.data(), n) && up(h->slot_ptr, slot_ptr.data(), 4 * (n + 1)) &&
        up(h->slot_idx, slot_idx.data(), 16 * m) && up(h->q, qfix.data(), 24 * n);
+  if (ok && h->mixed) {
+    auto f32 = [](const std::vector<double>& v) {
+      std::vector<float> f(v.size());
+      for (size_t k = 0; k < v.size(); ++k) f[k] = (float)v[k];
+      return f;
+    };
+    std::vector<float> Df = f32(Dinv), Vf = f32(V), cf = f32(cv), wf = f32(wv), muf = f32(mu), lf = f32(lam),
+                       uf = f32(uv), valf = f32(valv), ldf = f32(ldinv);
+    std::vector<float> zf(m, 0.f);
+    // E0_i = D_m D_m^-1 - I with the rounded D_m^-1 (FP64 arithmetic)
+    std::vector<float> e0f(9 * m);
+    for (int64_t i = 0; i < m; ++i) {
+      const int32_t* t = &tet[4 * i];
+      for (int r = 0; r < 3; ++r)
+        for (int c2 = 0; c2 < 3; ++c2) {
+          double acc = (r == c2) ? -1.0 : 0.0;
+          for (int k = 0; k < 3; ++k) acc += (Q[3 * t[k] + r] - Q[3 * t[3] + r]) * Dinv[(3 * k + c2) * m + i];
+          e0f[(3 * r + c2) * m + i] = (float)acc;
+        }
+    }
+    ok = up(h->E0, e0f.data(), 36 * m) && up(h->Qrest, Q, 24 * n) && up(h->Dinv32, Df.data(), 36 * m) && up(h->V32, Vf.data(), 4 * m) && up(h->c32, cf.data(), 4 * m) &&
+         up(h->w32, wf.data(), 4 * m) && up(h->mu32, muf.data(), 4 * m) && up(h->lam32, lf.data(), 4 * m) &&
+         up(h->u32, uf.data(), 12 * m) && up(h->ka32, zf.data(), 4 * m) && up(h->val32, valf.data(), 4 * nnz) &&
+         up(h->ldinv32, ldf.data(), 4 * n) && cudaStreamSynchronize(h->st) == cudaSuccess;
+  }
   if (!ok || cudaMemsetAsync(h->sc, 0, sizeof(DevScalars), h->st) != cudaSuccess) {
     h->release();
     delete h;
@@ -745,7 +954,7 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
 
   // ---- rest state: R = I, S = I, q = q*(I) ----
   rc = set_rest_state(h);
-  if (!rc) rc = coupling_solve(h);
+  if (!rc) rc = refresh_q(h, h->q_tol);
   if (!rc && cudaMemcpyAsync(h->q0, h->q, 24 * n, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess)
     rc = fail(EMU_ERR_CUDA, "copy q0");
   if (!rc) rc = build_modes(h);
@@ -769,6 +978,12 @@ int emu_set_activation(emu_handle* h, const double* a, int64_t count) {
     ka[i] = h->kappa * a[i];
   }
   EMU_CK(cudaMemcpyAsync(h->ka, ka.data(), 8 * h->m, cudaMemcpyHostToDevice, h->st));
+  std::vector<float> kaf;
+  if (h->mixed) {
+    kaf.resize(h->m);
+    for (int64_t i = 0; i < h->m; ++i) kaf[i] = (float)ka[i];
+    EMU_CK(cudaMemcpyAsync(h->ka32, kaf.data(), 4 * h->m, cudaMemcpyHostToDevice, h->st));
+  }
   EMU_CK(cudaStreamSynchronize(h->st));
   h->gref_valid = false;
   return EMU_OK;
@@ -801,13 +1016,20 @@ int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats) {
   int status = EMU_OK;
   const double tol = h->prm.tol_rel_residual;
   TetArgs<double> a64 = h->args<double>();
-  TetArgs<float> a32 = h->args<float>();
+  MixArgs am = h->margs();
+  int since = h->prm.q_refresh;  // iterations since q was last solved exactly
+  bool first_eval = true;
   for (;;) {
-    rc = coupling_solve(h);
-    if (rc) return rc;
+    // q = q*(F) exactly every q_refresh iterations; in between q follows
+    // q*(F + s d) = q + s dq (Eq. 4 is affine in F).
+    if (since >= h->prm.q_refresh) {
+      rc = refresh_q(h, h->q_tol);
+      if (rc) return rc;
+      since = 0;
+    }
     h->ph_begin();
     if (h->mixed)
-      launch_grad<float>(a32, h->grid_tet, h->st);
+      launch_grad_mixed(am, h->grid_tet, h->st);
     else
       launch_grad<double>(a64, h->grid_tet, h->st);
     h->ph_end(EMU_PHASE_GRAD, 1);
@@ -827,11 +1049,14 @@ int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats) {
       break;
     }
     const double gn = std::sqrt(hs.gnorm2);
-    if (it == 0 && gnorm_ref == 0.0) gnorm_ref = gn > h->floor ? gn : 0.0;
+    if (first_eval && gnorm_ref == 0.0) gnorm_ref = gn > h->floor ? gn : 0.0;
+    first_eval = false;
     res = gnorm_ref > 0.0 ? gn / gnorm_ref : 0.0;
-    if (res <= tol) break;
-    if (hs.pcg_fail) {
-      status = fail(EMU_ERR_PCG, "ACAP solve hit pcg_max");
+    if (res <= tol) {
+      if (since > 0) {  // confirm with an exact q before declaring convergence
+        since = h->prm.q_refresh;
+        continue;
+      }
       break;
     }
     if (hs.ls_fail * kLsTrials >= h->prm.ls_max_trials) {
@@ -844,60 +1069,56 @@ int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats) {
     }
     // Woodbury direction (Eqs. 9-12)
     h->ph_begin();
-    if (h->mixed) {
-      launch_syrk<float>(a32, h->grid_syrk, h->cpart, h->st);
-    } else {
+    if (h->mixed)
+      launch_syrk_mixed(am, h->grid_syrk, h->cpart, h->st);
+    else
       launch_syrk<double>(a64, h->grid_syrk, h->cpart, h->st);
-    }
     h->ph_end(EMU_PHASE_SYRK, 1);
     h->ph_begin();
-    launch_cap_solve(h->cpart, h->grid_syrk, nullptr, h->z, h->sc, h->st);
-    h->ph_end(EMU_PHASE_SMALL, 1);
-    {
-      TetArgs<double> ad = a64;
-      TetArgs<float> af = a32;
+    launch_cap_solve(h->cpart, h->grid_syrk, h->cfull, h->z, h->sc, h->st);
+    h->ph_end(EMU_PHASE_SMALL, 2);
+    h->ph_begin();
+    if (h->mixed) {
+      MixArgs ad = am;
       ad.partials = h->part_dir;
-      af.partials = h->part_dir;
-      h->ph_begin();
-      if (h->mixed)
-        launch_dir<float>(af, h->grid_tet, h->st);
-      else
-        launch_dir<double>(ad, h->grid_tet, h->st);
-      h->ph_end(EMU_PHASE_DIR, 1);
+      launch_dir_mixed(ad, h->grid_tet, h->st);
+    } else {
+      TetArgs<double> ad = a64;
+      ad.partials = h->part_dir;
+      launch_dir<double>(ad, h->grid_tet, h->st);
     }
-    h->ph_begin();
-    launch_assemble(h->n, h->slot_ptr, h->slot_idx, h->contrib, h->bfix, h->is_fixed, h->qfix, 1, h->b, h->st);
-    h->ph_end(EMU_PHASE_ASSEMBLE, 1);
+    h->ph_end(EMU_PHASE_DIR, 1);
     EMU_CK(cudaGetLastError());
-    h->ph_begin();
-    EMU_CK(launch_pcg(3, h->pcg_args(h->b, h->dq, 3), h->grid_pcg3, h->st));
-    h->ph_end(EMU_PHASE_PCG, 1);
+    rc = solve_dq(h);
+    if (rc) return rc;
     // Armijo line search (Algorithm 1)
-    {
-      TetArgs<double> al = a64;
-      TetArgs<float> af = a32;
+    h->ph_begin();
+    if (h->mixed) {
+      MixArgs al = am;
       al.partials = h->part_ls;
-      af.partials = h->part_ls;
-      h->ph_begin();
-      if (h->mixed)
-        launch_ls<float>(af, h->grid_tet, h->prm.ls_rho, h->st);
-      else
-        launch_ls<double>(al, h->grid_tet, h->prm.ls_rho, h->st);
-      h->ph_end(EMU_PHASE_LS, 1);
+      launch_ls_mixed(al, h->grid_tet, h->prm.ls_rho, h->st);
+    } else {
+      TetArgs<double> al = a64;
+      al.partials = h->part_ls;
+      launch_ls<double>(al, h->grid_tet, h->prm.ls_rho, h->st);
     }
+    h->ph_end(EMU_PHASE_LS, 1);
     h->ph_begin();
     launch_ls_select(h->part_dir, h->grid_tet, h->part_ls, h->grid_tet, h->sc, h->prm.ls_sigma0, h->prm.ls_rho,
                      h->prm.ls_c, h->st);
     h->ph_end(EMU_PHASE_SMALL, 1);
     h->ph_begin();
-    if (h->mixed)
-      launch_update_tets<float>(a32, h->grid_tet, h->st);
-    else
+    if (h->mixed) {
+      launch_update_mixed(am, h->grid_tet, h->st);
+      launch_update_verts_f(h->n, h->sc, h->dq32, h->q, h->st);
+    } else {
       launch_update_tets<double>(a64, h->grid_tet, h->st);
-    launch_update_verts(h->n, h->sc, h->dq, h->q, h->st);
+      launch_update_verts(h->n, h->sc, h->dq, h->q, h->st);
+    }
     h->ph_end(EMU_PHASE_UPDATE, 2);
     EMU_CK(cudaGetLastError());
     ++it;
+    ++since;
   }
   EMU_CK(cudaStreamSynchronize(h->st));
   h->prof_flush();
@@ -933,6 +1154,10 @@ int emu_get_element_state(emu_handle* h, double* R, double* s, double* F) {
     return EMU_OK;
   };
   int rc;
+  if (h->mixed) {
+    launch_mixed_to_Rs(m, h->quat, h->E32, h->R, h->s, h->st);
+    EMU_CK(cudaGetLastError());
+  }
   if (R && (rc = soa_to_aos(h->R, 9, R))) return rc;
   if (s && (rc = soa_to_aos(h->s, 6, s))) return rc;
   if (F) {
@@ -957,6 +1182,18 @@ int emu_set_element_state(emu_handle* h, const double* R, const double* s, const
     for (int64_t i = 0; i < m; ++i)
       for (int j = 0; j < 6; ++j) tmp[j * m + i] = s[6 * i + j];
     EMU_CK(cudaMemcpyAsync(h->s, tmp.data(), 48 * m, cudaMemcpyHostToDevice, h->st));
+    EMU_CK(cudaStreamSynchronize(h->st));
+  }
+  if (h->mixed && (R || s)) {
+    if (!R || !s) {
+      // keep the untouched part: bring the current state to (R, s) first
+      std::vector<double> Rc(9 * m), sc_(6 * m);
+      int rc = emu_get_element_state(h, R ? nullptr : Rc.data(), s ? nullptr : sc_.data(), nullptr);
+      if (rc) return rc;
+      return emu_set_element_state(h, R ? R : Rc.data(), s ? s : sc_.data(), q);
+    }
+    launch_Rs_to_mixed(m, h->R, h->s, h->quat, h->E32, h->st);
+    EMU_CK(cudaGetLastError());
     EMU_CK(cudaStreamSynchronize(h->st));
   }
   if (q) {

@@ -15,28 +15,9 @@
 
 #include "emu_kernels.cuh"
 #include "emu_math.cuh"
+#include "emu_reduce.cuh"
 
 namespace emu {
-
-// ------------------------------------------------------------ reductions --
-template <int NV>
-__device__ __forceinline__ void block_reduce_write(double (&v)[NV], double* out) {
-  __shared__ double sm[8 * NV];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double x = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) sm[warp * NV + k] = x;
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
-    double x = 0.0;
-    for (int w = 0; w < nw; ++w) x += sm[w * NV + k];
-    out[k] = x;
-  }
-}
 
 // ------------------------------------------------------------ gathers ----
 __device__ __forceinline__ void load_dinv(const double* __restrict__ Dinv, int64_t m, int64_t i, double* D) {
@@ -226,17 +207,14 @@ template <typename TW> void launch_grad(const TetArgs<TW>& a, int grid, cudaStre
   k_grad<TW><<<grid, 128, 0, st>>>(a);
 }
 
-__global__ void k_reduce_grad(const double* partials, int nblk, DevScalars* sc) {
-  // single warp: deterministic fixed-order sum
-  if (threadIdx.x == 0) {
-    double x = 0.0;
-    for (int b = 0; b < nblk; ++b) x += partials[b];
-    sc->gnorm2 = x;
-  }
+__global__ void __launch_bounds__(256) k_reduce_grad(const double* partials, int nblk, DevScalars* sc) {
+  __shared__ double tot[1];
+  block_sum_partials<1>(partials, nblk, tot);
+  if (threadIdx.x == 0) sc->gnorm2 = tot[0];
 }
 
 void launch_reduce_grad(const double* partials, int nblk, DevScalars* sc, double*, double*, cudaStream_t st) {
-  k_reduce_grad<<<1, 32, 0, st>>>(partials, nblk, sc);
+  k_reduce_grad<<<1, 256, 0, st>>>(partials, nblk, sc);
 }
 
 // ------------------------------------------------------------ capacitance --
@@ -314,29 +292,40 @@ __global__ void __launch_bounds__(256) k_syrk(TetArgs<TW> a, double* __restrict_
     }
     __syncthreads();
   }
-  double* out = cpart + (size_t)blockIdx.x * (kCapEntries + kK);
+  // entry-major partials: cpart[e * gridDim.x + block]
+  const size_t nb = gridDim.x;
 #pragma unroll
   for (int p = 0; p < 3; ++p)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) out[(3 * tr + p) * kK + 3 * tc + q] = (double)acc[p][q];
-  if (tid < kK) out[kCapEntries + tid] = by;
+    for (int q = 0; q < 3; ++q) cpart[(size_t)((3 * tr + p) * kK + 3 * tc + q) * nb + blockIdx.x] = (double)acc[p][q];
+  if (tid < kK) cpart[(size_t)(kCapEntries + tid) * nb + blockIdx.x] = by;
 }
 
 template <typename TW> void launch_syrk(const TetArgs<TW>& a, int grid, double* cpart, cudaStream_t st) {
   k_syrk<TW><<<grid, 256, 0, st>>>(a, cpart);
 }
 
-// Sum the capacitance partials, factor C = L L^T in FP64, z = C^-1 (B y).
-__global__ void __launch_bounds__(256) k_cap_solve(const double* __restrict__ cpart, int nblk, double* z,
-                                                    DevScalars* sc) {
+// One warp per entry of C and B y sums that entry's per-block partials
+// (entry-major, coalesced) with a fixed shuffle tree.
+__global__ void __launch_bounds__(256) k_reduce_cpart(const double* __restrict__ cpart, int nblk, double* __restrict__ cfull) {
+  const int e = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= kCapEntries + kK) return;
+  double x = 0.0;
+  for (int b = lane; b < nblk; b += 32) x += cpart[(size_t)e * nblk + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if (lane == 0) cfull[e] = x;
+}
+
+// Factor C = L L^T in FP64 (C symmetrised) and solve z = C^-1 (B y).
+__global__ void __launch_bounds__(256) k_cap_solve(const double* __restrict__ cfull, double* z, DevScalars* sc) {
   __shared__ double C[kK][kK + 1];
   __shared__ double by[kK];
   __shared__ int s_ok;
   const int tid = threadIdx.x;
-  constexpr int stride = kCapEntries + kK;
   for (int e = tid; e < kCapEntries + kK; e += blockDim.x) {
-    double x = 0.0;
-    for (int b = 0; b < nblk; ++b) x += cpart[(size_t)b * stride + e];
+    const double x = cfull[e];
     if (e < kCapEntries)
       C[e / kK][e % kK] = x;
     else
@@ -396,8 +385,11 @@ __global__ void __launch_bounds__(256) k_cap_solve(const double* __restrict__ cp
   }
 }
 
-void launch_cap_solve(const double* cpart, int nblk, const double*, double* z, DevScalars* sc, cudaStream_t st) {
-  k_cap_solve<<<1, 256, 0, st>>>(cpart, nblk, z, sc);
+void launch_cap_solve(const double* cpart, int nblk, const double* cfull_scratch, double* z, DevScalars* sc,
+                      cudaStream_t st) {
+  double* cfull = const_cast<double*>(cfull_scratch);
+  k_reduce_cpart<<<(kCapEntries + kK + 7) / 8, 256, 0, st>>>(cpart, nblk, cfull);
+  k_cap_solve<<<1, 256, 0, st>>>(cfull, z, sc);
 }
 
 // ------------------------------------------------------------ direction ---
@@ -533,17 +525,15 @@ template <typename TW> void launch_ls(const TetArgs<TW>& a, int grid, double rho
   k_ls<TW><<<grid, 128, 0, st>>>(a, rho);
 }
 
-__global__ void k_ls_select(const double* dir_partials, int nblk_dir, const double* ls_partials, int nblk_ls,
-                            DevScalars* sc, double sigma0, double rho, double c_armijo) {
+__global__ void __launch_bounds__(256) k_ls_select(const double* dir_partials, int nblk_dir, const double* ls_partials,
+                                                    int nblk_ls, DevScalars* sc, double sigma0, double rho, double c_armijo) {
+  __shared__ double s_gtd[1], s_v[kLsNV];
+  block_sum_partials<1>(dir_partials, nblk_dir, s_gtd);
+  block_sum_partials<kLsNV>(ls_partials, nblk_ls, s_v);
   if (threadIdx.x != 0) return;
-  double gtd = 0.0;
-  for (int b = 0; b < nblk_dir; ++b) gtd += dir_partials[b];
+  const double gtd = s_gtd[0];
   double v[kLsNV];
-  for (int k = 0; k < kLsNV; ++k) {
-    double x = 0.0;
-    for (int b = 0; b < nblk_ls; ++b) x += ls_partials[(size_t)b * kLsNV + k];
-    v[k] = x;
-  }
+  for (int k = 0; k < kLsNV; ++k) v[k] = s_v[k];
   sc->gtd = gtd;
   double sig = sc->sigma_start;
   int accepted = -1;
@@ -577,7 +567,7 @@ __global__ void k_ls_select(const double* dir_partials, int nblk_dir, const doub
 
 void launch_ls_select(const double* dir_partials, int nblk_dir, const double* ls_partials, int nblk_ls,
                       DevScalars* sc, double sigma0, double rho, double c_armijo, cudaStream_t st) {
-  k_ls_select<<<1, 32, 0, st>>>(dir_partials, nblk_dir, ls_partials, nblk_ls, sc, sigma0, rho, c_armijo);
+  k_ls_select<<<1, 256, 0, st>>>(dir_partials, nblk_dir, ls_partials, nblk_ls, sc, sigma0, rho, c_armijo);
 }
 
 // ------------------------------------------------------------ update ------
@@ -654,18 +644,16 @@ __global__ void __launch_bounds__(128) k_gref(TetArgs<double> a, const double* q
   block_reduce_write<1>(acc, partials + blockIdx.x);
 }
 
-__global__ void k_sum_scalar(const double* partials, int nblk, double* out) {
-  if (threadIdx.x == 0) {
-    double x = 0.0;
-    for (int b = 0; b < nblk; ++b) x += partials[b];
-    out[0] = x;
-  }
+__global__ void __launch_bounds__(256) k_sum_scalar(const double* partials, int nblk, double* out) {
+  __shared__ double tot[1];
+  block_sum_partials<1>(partials, nblk, tot);
+  if (threadIdx.x == 0) out[0] = tot[0];
 }
 
 void launch_gref(const TetArgs<double>& a, const double* q0, int grid, double* partials, double* out,
                  cudaStream_t st) {
   k_gref<<<grid, 128, 0, st>>>(a, q0, partials);
-  k_sum_scalar<<<1, 32, 0, st>>>(partials, grid, out);
+  k_sum_scalar<<<1, 256, 0, st>>>(partials, grid, out);
 }
 
 // ------------------------------------------------------------ modes -------
@@ -681,6 +669,56 @@ __global__ void __launch_bounds__(256) k_gram16(int64_t n, const double* __restr
 
 void launch_gram16(int64_t n, const double* X, int grid, double* partials, cudaStream_t st) {
   k_gram16<<<grid, 256, 0, st>>>(n, X, partials);
+}
+
+// Y = L X for 16 columns (L in CSR, X and Y vertex-major n x 16)
+__global__ void __launch_bounds__(256) k_spmv16(int64_t n, const int32_t* __restrict__ rowptr,
+                                                const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                const double* __restrict__ X, double* __restrict__ Y) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    double acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+    for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+      const double a = val[e];
+      const int64_t c = col[e];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] += a * X[c * 16 + j];
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) Y[v * 16 + j] = acc[j];
+  }
+}
+
+// partials of X^T Y (16 x 16) over contiguous vertex ranges
+__global__ void __launch_bounds__(256) k_cross16(int64_t n, const double* __restrict__ X, const double* __restrict__ Y,
+                                                 double* partials) {
+  const int a = threadIdx.x >> 4, b = threadIdx.x & 15;
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t v0 = blockIdx.x * per;
+  const int64_t v1 = v0 + per < n ? v0 + per : n;
+  double acc = 0.0;
+  for (int64_t v = v0; v < v1; ++v) acc += X[v * 16 + a] * Y[v * 16 + b];
+  partials[(size_t)blockIdx.x * 256 + threadIdx.x] = acc;
+}
+
+void launch_galerkin16(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* X,
+                       double* Y, int grid, double* partials, cudaStream_t st) {
+  int g2 = (int)((n + 255) / 256);
+  if (g2 < 1) g2 = 1;
+  k_spmv16<<<g2, 256, 0, st>>>(n, rowptr, col, val, X, Y);
+  k_cross16<<<grid, 256, 0, st>>>(n, X, Y, partials);
+}
+
+__global__ void k_d2f(int64_t k, const double* a, float* b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+void launch_d2f(int64_t k, const double* a, float* b, cudaStream_t st) {
+  int grid = (int)((k + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_d2f<<<grid, 256, 0, st>>>(k, a, b);
 }
 
 __global__ void k_reduce_cols(const double* partials, int nblk, int nv, double* out) {

@@ -52,7 +52,9 @@ void launch_update_verts(int64_t n, const DevScalars* sc, const double* dq, doub
 // Single-block reducers.
 void launch_reduce_grad(const double* partials, int nblk, DevScalars* sc, double* By, double* gsum,
                         cudaStream_t st);
-void launch_cap_solve(const double* cpart, int nblk, const double* By, double* z, DevScalars* sc,
+// cpart: entry-major partials (kCapEntries + kK entries x nblk blocks);
+// cfull_scratch receives their sums.
+void launch_cap_solve(const double* cpart, int nblk, const double* cfull_scratch, double* z, DevScalars* sc,
                       cudaStream_t st);
 void launch_ls_select(const double* dir_partials, int nblk_dir, const double* ls_partials, int nblk_ls,
                       DevScalars* sc, double sigma0, double rho, double c_armijo, cudaStream_t st);
@@ -65,6 +67,10 @@ void launch_gref(const TetArgs<double>& a, const double* q0, int grid, double* p
 void launch_gram16(int64_t n, const double* X, int grid, double* partials, cudaStream_t st);
 void launch_reduce_cols(const double* partials, int nblk, int nv, double* out, cudaStream_t st);
 void launch_xform16(int64_t n, const double* T, double* X, cudaStream_t st);
+// partials of X^T (L X) for the 16-column basis X (Y receives L X)
+void launch_galerkin16(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* X,
+                       double* Y, int grid, double* partials, cudaStream_t st);
+void launch_d2f(int64_t k, const double* a, float* b, cudaStream_t st);
 template <typename TW>
 void launch_gamma(int64_t m, const int4* tet, const double* Dinv, const double* X, TW* gam, cudaStream_t st);
 

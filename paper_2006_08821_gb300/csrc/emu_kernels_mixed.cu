@@ -1,0 +1,542 @@
+// Mixed-precision kernels: per-tet work in FP32 on a (unit quaternion,
+// E = S - I) state, every global sum and the positions in FP64.
+//
+// Precision rules (they decide which expressions are used):
+//   * the residual terms V R Pr and alpha w (R S - G q) are formed from
+//     difference-free expressions in E (S - S^-1 = (2E + E^2) S^-1,
+//     ln J = log1p(tr E + e2(E) + det E)), so a stiff element with tiny strain
+//     keeps the relative precision of its stress;
+//   * the line-search energy change V [Psi(F + s d) - Psi(F)] is written
+//     term by term without the O(|d|) cancellation of mu <F, d> - mu tr(F^-1 d);
+//   * the polar update works on I + Y with the rotation kept as a quaternion
+//     and R - I written without cancellation.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "emu_kernels.cuh"
+#include "emu_math.cuh"
+#include "emu_mixed.cuh"
+#include "emu_reduce.cuh"
+
+namespace emu {
+
+__device__ __forceinline__ void load9f(const float* __restrict__ a, int64_t m, int64_t i, float* D) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) D[k] = a[k * m + i];
+}
+
+__device__ __forceinline__ ElemMat<float> load_mat_f(const MixArgs& a, int64_t i) {
+  ElemMat<float> e;
+  e.V = a.V[i];
+  e.mu = a.mu[i];
+  e.lam = a.lam[i];
+  e.ka = a.ka[i];
+  e.u[0] = a.u[i];
+  e.u[1] = a.u[a.m + i];
+  e.u[2] = a.u[2 * a.m + i];
+  return e;
+}
+
+// A - I = G_i (q - Q) + (G_i Q - I): the displacement edges are formed in
+// FP64 and rounded once, so A - I keeps its relative precision.
+__device__ __forceinline__ void defgrad_disp(const double* __restrict__ q, const double* __restrict__ Q, int4 t,
+                                             const float* D, const float* __restrict__ E0, int64_t m, int64_t i,
+                                             float* AmI) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const double u3 = q[3 * (int64_t)t.w + r] - Q[3 * (int64_t)t.w + r];
+    const float e0 = (float)((q[3 * (int64_t)t.x + r] - Q[3 * (int64_t)t.x + r]) - u3);
+    const float e1 = (float)((q[3 * (int64_t)t.y + r] - Q[3 * (int64_t)t.y + r]) - u3);
+    const float e2 = (float)((q[3 * (int64_t)t.z + r] - Q[3 * (int64_t)t.z + r]) - u3);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) AmI[3 * r + c] = e0 * D[c] + e1 * D[3 + c] + e2 * D[6 + c] + E0[(3 * r + c) * m + i];
+  }
+}
+
+// Mismatch D = G_i q - R S = (A - I) - (R - I) - R E, every term small.
+__device__ __forceinline__ void mismatch(const MixArgs& a, int4 t, const float* Dm, int64_t i, const float4 qq,
+                                         const float* RE, float* Dk) {
+  float AmI[9], RmI[9];
+  defgrad_disp(a.q, a.Q, t, Dm, a.E0, a.m, i, AmI);
+  quat_rot_minus_I(qq.x, qq.y, qq.z, qq.w, RmI);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Dk[k] = (AmI[k] - RmI[k]) - RE[k];
+}
+
+__device__ __forceinline__ void defgrad_ff(const float* __restrict__ q, int4 t, const float* D, float* A) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float q3 = q[3 * (int64_t)t.w + r];
+    const float e0 = q[3 * (int64_t)t.x + r] - q3;
+    const float e1 = q[3 * (int64_t)t.y + r] - q3;
+    const float e2 = q[3 * (int64_t)t.z + r] - q3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A[3 * r + c] = e0 * D[c] + e1 * D[3 + c] + e2 * D[6 + c];
+  }
+}
+
+__device__ __forceinline__ void load_state(const MixArgs& a, int64_t i, float* R, float* e6) {
+  const float4 qq = a.quat[i];
+  quat_to_R(qq.x, qq.y, qq.z, qq.w, R);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) e6[k] = a.E[k * a.m + i];
+}
+
+template <typename TX>
+__device__ __forceinline__ void corners_f(double* __restrict__ contrib, int64_t i, float w, const TX* X, const float* D) {
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  double* out = contrib + 12 * i;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float v[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) v[r] = w * (X[3 * r] * D[3 * k] + X[3 * r + 1] * D[3 * k + 1] + X[3 * r + 2] * D[3 * k + 2]);
+    out[3 * k] = v[0];
+    out[3 * k + 1] = v[1];
+    out[3 * k + 2] = v[2];
+    s0 += v[0];
+    s1 += v[1];
+    s2 += v[2];
+  }
+  out[9] = -s0;
+  out[10] = -s1;
+  out[11] = -s2;
+}
+
+// ------------------------------------------------------------ gradient ----
+__global__ void __launch_bounds__(128) k_grad_m(MixArgs a) {
+  const int64_t m = a.m;
+  double acc[1] = {0.0};
+  int bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 t = a.tet[i];
+    float D[9], R[9], e6[6];
+    load9f(a.Dinv, m, i, D);
+    load_state(a, i, R, e6);
+    StretchE st;
+    if (!stretch_from_E(e6, st)) bad = 1;
+    const ElemMat<float> mat = load_mat_f(a, i);
+    const float c = a.c[i];
+    float Pr[9], RP[9], Em[9], RE[9], Dk[9];
+    piola_rotated_E(st, mat, Pr);
+    matmul3(R, Pr, RP);
+    sym_from_s(e6, Em);
+    matmul3(R, Em, RE);
+    mismatch(a, t, D, i, a.quat[i], RE, Dk);
+    float g[9];
+    double gg = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      g[k] = mat.V * RP[k] - c * Dk[k];
+      gg += (double)g[k] * (double)g[k];
+      a.g[k * m + i] = g[k];
+    }
+    if (!isfinite(gg)) bad = 1;
+    acc[0] += gg;
+    float M6[36], U[54];
+    stretch_hessian(st.Sinv, st.lnJ, mat, M6);
+    bool ok = true;
+    chart_factor(R, st.S, M6, c, U, ok);
+    if (!ok) bad = 1;
+    apply_I_minus_N(U, g);
+    const float ic = 1.f / c;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) a.y[k * m + i] = g[k] * ic;
+#pragma unroll
+    for (int k = 0; k < 54; ++k) a.Uw[k * m + i] = U[k];
+  }
+  block_reduce_write<1>(acc, a.partials + blockIdx.x);
+  if (bad) atomicExch(&a.sc->nonfinite, 1);
+}
+
+void launch_grad_mixed(const MixArgs& a, int grid, cudaStream_t st) { k_grad_m<<<grid, 128, 0, st>>>(a); }
+
+// ------------------------------------------------------------ capacitance --
+// Upper-triangular 3x3 tiles of C = sum_i Yh_i^T Yh_i (FP32 within a block,
+// FP64 across blocks; mirrored into the full 48 x 48 partial), plus B y.
+__global__ void __launch_bounds__(256) k_syrk_m(MixArgs a, double* __restrict__ cpart) {
+  constexpr int CH = 24;  // 24 tets per chunk: 38.7 KB of static shared memory
+  constexpr int KR = CH * 6;
+  __shared__ float sY[KR][kK + 1];
+  __shared__ float sU[CH][54];
+  __shared__ float sg[CH][48];
+  __shared__ float sy[CH][9];
+  __shared__ float sw[CH];
+  const int tid = threadIdx.x;
+  // thread -> upper tile (tr <= tc) of the 16 x 16 grid of 3x3 tiles
+  int tr = -1, tc = -1;
+  if (tid < 136) {
+    int k = tid, r = 0;
+    while (k >= 16 - r) {
+      k -= 16 - r;
+      ++r;
+    }
+    tr = r;
+    tc = r + k;
+  }
+  float acc[3][3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) acc[p][q] = 0.f;
+  double by = 0.0;
+  const int bidx = tid - 136;  // 0..47 for the B y threads
+  const int64_t m = a.m;
+  const int64_t nch = (m + CH - 1) / CH;
+  for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const int64_t base = ch * CH;
+    for (int e = tid; e < CH * 54; e += 256) {
+      const int k = e / CH, tt = e % CH;
+      const int64_t i = base + tt;
+      sU[tt][k] = i < m ? a.Uw[k * m + i] : 0.f;
+    }
+    for (int e = tid; e < CH * 48; e += 256) {
+      const int k = e / CH, tt = e % CH;
+      const int64_t i = base + tt;
+      sg[tt][k] = i < m ? a.gam[k * m + i] : 0.f;
+    }
+    for (int e = tid; e < CH * 9; e += 256) {
+      const int k = e / CH, tt = e % CH;
+      const int64_t i = base + tt;
+      sy[tt][k] = i < m ? a.y[k * m + i] : 0.f;
+    }
+    if (tid < CH) sw[tid] = (base + tid) < m ? a.w[base + tid] : 0.f;
+    __syncthreads();
+    for (int e = tid; e < CH * 6 * kK; e += 256) {
+      const int tt = e / (6 * kK), rem = e % (6 * kK);
+      const int k = rem / kK, col = rem % kK;
+      const int r = col >> 4, j = col & 15;
+      const float v = sU[tt][9 * k + 3 * r] * sg[tt][3 * j] + sU[tt][9 * k + 3 * r + 1] * sg[tt][3 * j + 1] +
+                      sU[tt][9 * k + 3 * r + 2] * sg[tt][3 * j + 2];
+      sY[tt * 6 + k][col] = v * sqrtf(sw[tt]);
+    }
+    __syncthreads();
+    if (tr >= 0) {
+#pragma unroll 4
+      for (int kr = 0; kr < KR; ++kr) {
+        const float a0 = sY[kr][3 * tr], a1 = sY[kr][3 * tr + 1], a2 = sY[kr][3 * tr + 2];
+        const float b0 = sY[kr][3 * tc], b1 = sY[kr][3 * tc + 1], b2 = sY[kr][3 * tc + 2];
+        acc[0][0] += a0 * b0;
+        acc[0][1] += a0 * b1;
+        acc[0][2] += a0 * b2;
+        acc[1][0] += a1 * b0;
+        acc[1][1] += a1 * b1;
+        acc[1][2] += a1 * b2;
+        acc[2][0] += a2 * b0;
+        acc[2][1] += a2 * b1;
+        acc[2][2] += a2 * b2;
+      }
+    } else if (bidx >= 0 && bidx < kK) {
+      const int r = bidx >> 4, j = bidx & 15;
+      float loc = 0.f;
+      for (int tt = 0; tt < CH; ++tt)
+        loc += sw[tt] * (sy[tt][3 * r] * sg[tt][3 * j] + sy[tt][3 * r + 1] * sg[tt][3 * j + 1] + sy[tt][3 * r + 2] * sg[tt][3 * j + 2]);
+      by += (double)loc;
+    }
+    __syncthreads();
+  }
+  // entry-major partials: cpart[e * gridDim.x + block]
+  const size_t nb = gridDim.x;
+  if (tr >= 0) {
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        cpart[(size_t)((3 * tr + p) * kK + 3 * tc + q) * nb + blockIdx.x] = (double)acc[p][q];
+        if (tr != tc) cpart[(size_t)((3 * tc + q) * kK + 3 * tr + p) * nb + blockIdx.x] = (double)acc[p][q];
+      }
+  } else if (bidx >= 0 && bidx < kK) {
+    cpart[(size_t)(kCapEntries + bidx) * nb + blockIdx.x] = by;
+  }
+}
+
+void launch_syrk_mixed(const MixArgs& a, int grid, double* cpart, cudaStream_t st) {
+  k_syrk_m<<<grid, 256, 0, st>>>(a, cpart);
+}
+
+// ------------------------------------------------------------ direction ---
+__global__ void __launch_bounds__(128) k_dir_m(MixArgs a) {
+  __shared__ float sz[kK];
+  if (threadIdx.x < kK) sz[threadIdx.x] = (float)a.z[threadIdx.x];
+  __syncthreads();
+  const int64_t m = a.m;
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    float v[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float g0 = a.gam[(3 * j) * m + i], g1 = a.gam[(3 * j + 1) * m + i], g2 = a.gam[(3 * j + 2) * m + i];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const float zr = sz[16 * r + j];
+        v[3 * r] += zr * g0;
+        v[3 * r + 1] += zr * g1;
+        v[3 * r + 2] += zr * g2;
+      }
+    }
+    float U[54];
+#pragma unroll
+    for (int k = 0; k < 54; ++k) U[k] = a.Uw[k * m + i];
+    apply_I_minus_N(U, v);
+    float dv[9];
+    double gtd = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      dv[k] = -(a.y[k * m + i] + v[k]);
+      a.d[k * m + i] = dv[k];
+      gtd += (double)a.g[k * m + i] * (double)dv[k];
+    }
+    acc[0] += gtd;
+    float D[9];
+    load9f(a.Dinv, m, i, D);
+    corners_f(a.contrib, i, a.w[i], dv, D);
+  }
+  block_reduce_write<1>(acc, a.partials + blockIdx.x);
+}
+
+void launch_dir_mixed(const MixArgs& a, int grid, cudaStream_t st) { k_dir_m<<<grid, 128, 0, st>>>(a); }
+
+// ------------------------------------------------------------ line search --
+// V [Psi(F + s d) - Psi(F)] with M = F^-1 d = S^-1 R^T d and
+// x = s tr M + s^2 e2(M) + s^3 det M (= det(I + sM) - 1):
+//   mu [ s <F - F^-T, d> + s^2 |d|^2 / 2 - s^2 e2 - s^3 det M + (x - log1p x) ]
+//   + lam/2 log1p(x) (2 ln J + log1p(x)) + ka (2 s (Fu).(du) + s^2 |du|^2),
+// with F - F^-T = R (2E + E^2) S^-1; plus the ACAP coefficients.
+__global__ void __launch_bounds__(128) k_ls_m(MixArgs a, double rho) {
+  const int64_t m = a.m;
+  const double s0 = a.sc->sigma_start;
+  double acc[kLsNV];
+#pragma unroll
+  for (int k = 0; k < kLsNV; ++k) acc[k] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 t = a.tet[i];
+    float D[9], R[9], e6[6], dA[9], d[9];
+    load9f(a.Dinv, m, i, D);
+    load_state(a, i, R, e6);
+    load9f(a.d, m, i, d);
+    StretchE st;
+    stretch_from_E(e6, st);
+    defgrad_ff(a.dq, t, D, dA);
+    const float c = a.c[i];
+    float Em[9], RE[9], Dm[9];
+    sym_from_s(e6, Em);
+    matmul3(R, Em, RE);
+    mismatch(a, t, D, i, a.quat[i], RE, Dm);  // G q - R S
+    float cDd = 0.f, cdd = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float dDk = dA[k] - d[k];
+      cDd += Dm[k] * dDk;
+      cdd += dDk * dDk;
+    }
+    acc[kLsTrials] += (double)(c * cDd);
+    acc[kLsTrials + 1] += (double)(c * cdd);
+    const ElemMat<float> md = load_mat_f(a, i);
+    float Rtd[9], M[9], F[9];
+    matTmul3(R, d, Rtd);
+    matmul3(st.Sinv, Rtd, M);
+    matmul3(R, st.S, F);
+    const float trM = M[0] + M[4] + M[8];
+    const float e2 = inv2(M);
+    const float detM = det3(M);
+    float FFd = 0.f, dd = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      FFd += st.SmSi[k] * Rtd[k];  // <(S - S^-1), R^T d> = <F - F^-T, d>
+      dd += d[k] * d[k];
+    }
+    float Fu[3], du[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      Fu[r] = F[3 * r] * md.u[0] + F[3 * r + 1] * md.u[1] + F[3 * r + 2] * md.u[2];
+      du[r] = d[3 * r] * md.u[0] + d[3 * r + 1] * md.u[1] + d[3 * r + 2] * md.u[2];
+    }
+    const float Fudu = Fu[0] * du[0] + Fu[1] * du[1] + Fu[2] * du[2];
+    const float dudu = du[0] * du[0] + du[1] * du[1] + du[2] * du[2];
+    float sig = (float)s0;
+#pragma unroll
+    for (int j = 0; j < kLsTrials; ++j) {
+      const float x = sig * trM + sig * sig * e2 + sig * sig * sig * detM;
+      double dpsi;
+      if (x > -1.f) {
+        const float dl = log1pf(x);
+        const float nh = md.mu * (sig * FFd + 0.5f * sig * sig * dd - sig * sig * e2 - sig * sig * sig * detM +
+                                  x_minus_log1p(x));
+        const float vol = 0.5f * md.lam * dl * (2.f * st.lnJ + dl);
+        const float fib = md.ka * (2.f * sig * Fudu + sig * sig * dudu);
+        dpsi = (double)(md.V * (nh + vol + fib));
+      } else {
+        dpsi = 1e300;
+      }
+      acc[j] += dpsi;
+      sig *= (float)rho;
+    }
+  }
+  block_reduce_write<kLsNV>(acc, a.partials + (size_t)blockIdx.x * kLsNV);
+}
+
+void launch_ls_mixed(const MixArgs& a, int grid, double rho, cudaStream_t st) { k_ls_m<<<grid, 128, 0, st>>>(a, rho); }
+
+// ------------------------------------------------------------ update ------
+// F' = R (S + s R^T d) = R (I + Y), Y = E + s R^T d; I + Y = Rx (I + E'):
+// q' = q Rx, E' from the near-identity polar factor.
+__global__ void __launch_bounds__(128) k_update_m(MixArgs a) {
+  const double sigd = a.sc->sigma;
+  if (sigd == 0.0) return;
+  const float sig = (float)sigd;
+  const int64_t m = a.m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    float R[9], e6[6], d[9], Rtd[9], Y[9];
+    load_state(a, i, R, e6);
+    load9f(a.d, m, i, d);
+    matTmul3(R, d, Rtd);
+    sym_from_s(e6, Y);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Y[k] += sig * Rtd[k];
+    Quat qx;
+    float en[6];
+    polar_near_identity(Y, qx, en, 12);
+    const float4 q0 = a.quat[i];
+    const Quat qn = qnormalize(qmul(Quat{q0.x, q0.y, q0.z, q0.w}, qx));
+    a.quat[i] = make_float4(qn.x, qn.y, qn.z, qn.w);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.E[k * m + i] = en[k];
+  }
+}
+
+void launch_update_mixed(const MixArgs& a, int grid, cudaStream_t st) { k_update_m<<<grid, 128, 0, st>>>(a); }
+
+__global__ void __launch_bounds__(256) k_update_verts_f(int64_t n3, const DevScalars* sc, const float* dq, double* q) {
+  const double sig = sc->sigma;
+  if (sig == 0.0) return;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x)
+    q[k] += sig * (double)dq[k];
+}
+
+void launch_update_verts_f(int64_t n, const DevScalars* sc, const float* dq, double* q, cudaStream_t st) {
+  const int64_t n3 = 3 * n;
+  int grid = (int)((n3 + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_update_verts_f<<<grid, 256, 0, st>>>(n3, sc, dq, q);
+}
+
+// ------------------------------------------------------- coupling RHS ----
+// FP64 corner terms of G^T W (R S) for the exact coupling solve: the FP32
+// state values are exact in FP64, R is rebuilt from the normalised
+// quaternion in FP64.
+__global__ void __launch_bounds__(256) k_rhs_state_m(MixArgs a) {
+  const int64_t m = a.m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 qq = a.quat[i];
+    double qx = qq.x, qy = qq.y, qz = qq.z, qw = qq.w;
+    const double nn = 1.0 / sqrt(qx * qx + qy * qy + qz * qz + qw * qw);
+    qx *= nn;
+    qy *= nn;
+    qz *= nn;
+    qw *= nn;
+    double R[9], e6[6], S[9], F[9];
+    quat_to_R(qx, qy, qz, qw, R);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) e6[k] = (double)a.E[k * m + i];
+    sym_from_s(e6, S);
+    S[0] += 1.0;
+    S[4] += 1.0;
+    S[8] += 1.0;
+    matmul3(R, S, F);
+    double D[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) D[k] = (double)a.Dinv[k * m + i];
+    const double w = (double)a.w[i];
+    double s0 = 0, s1 = 0, s2 = 0;
+    double* out = a.contrib + 12 * i;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double v[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) v[r] = w * (F[3 * r] * D[3 * k] + F[3 * r + 1] * D[3 * k + 1] + F[3 * r + 2] * D[3 * k + 2]);
+      out[3 * k] = v[0];
+      out[3 * k + 1] = v[1];
+      out[3 * k + 2] = v[2];
+      s0 += v[0];
+      s1 += v[1];
+      s2 += v[2];
+    }
+    out[9] = -s0;
+    out[10] = -s1;
+    out[11] = -s2;
+  }
+}
+
+void launch_rhs_state_mixed(const MixArgs& a, int grid, cudaStream_t st) { k_rhs_state_m<<<grid, 256, 0, st>>>(a); }
+
+__global__ void __launch_bounds__(256) k_assemble_f(int64_t n, const int32_t* __restrict__ slot_ptr,
+                                                    const int32_t* __restrict__ slot_idx,
+                                                    const double* __restrict__ contrib,
+                                                    const uint8_t* __restrict__ is_fixed, float* __restrict__ b) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    if (!is_fixed[v]) {
+      const int32_t e0 = slot_ptr[v], e1 = slot_ptr[v + 1];
+      for (int32_t e = e0; e < e1; ++e) {
+        const int64_t sl = slot_idx[e];
+        s0 += contrib[3 * sl];
+        s1 += contrib[3 * sl + 1];
+        s2 += contrib[3 * sl + 2];
+      }
+    }
+    b[3 * v] = (float)s0;
+    b[3 * v + 1] = (float)s1;
+    b[3 * v + 2] = (float)s2;
+  }
+}
+
+void launch_assemble_f(int64_t n, const int32_t* slot_ptr, const int32_t* slot_idx, const double* contrib,
+                       const uint8_t* is_fixed, float* b, cudaStream_t st) {
+  int grid = (int)((n + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_assemble_f<<<grid, 256, 0, st>>>(n, slot_ptr, slot_idx, contrib, is_fixed, b);
+}
+
+// ------------------------------------------------------------ conversion --
+__global__ void k_mixed_to_Rs(int64_t m, const float4* quat, const float* E, double* R, double* s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 qq = quat[i];
+    double qx = qq.x, qy = qq.y, qz = qq.z, qw = qq.w;
+    const double nn = 1.0 / sqrt(qx * qx + qy * qy + qz * qz + qw * qw);
+    double Rr[9];
+    quat_to_R(qx * nn, qy * nn, qz * nn, qw * nn, Rr);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k * m + i] = Rr[k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s[k * m + i] = (double)E[k * m + i] + (k < 3 ? 1.0 : 0.0);
+  }
+}
+
+__global__ void k_Rs_to_mixed(int64_t m, const double* R, const double* s, float4* quat, float* E) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double Rr[9], qd[4];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Rr[k] = R[k * m + i];
+    R_to_quat(Rr, qd);
+    quat[i] = make_float4((float)qd[0], (float)qd[1], (float)qd[2], (float)qd[3]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) E[k * m + i] = (float)(s[k * m + i] - (k < 3 ? 1.0 : 0.0));
+  }
+}
+
+void launch_mixed_to_Rs(int64_t m, const float4* quat, const float* E, double* R, double* s, cudaStream_t st) {
+  int grid = (int)((m + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_mixed_to_Rs<<<grid, 256, 0, st>>>(m, quat, E, R, s);
+}
+
+void launch_Rs_to_mixed(int64_t m, const double* R, const double* s, float4* quat, float* E, cudaStream_t st) {
+  int grid = (int)((m + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_Rs_to_mixed<<<grid, 256, 0, st>>>(m, R, s, quat, E);
+}
+
+}  // namespace emu

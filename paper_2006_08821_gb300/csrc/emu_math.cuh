@@ -421,4 +421,196 @@ template <typename T> EMU_HD int polar_rotation(const T* X0, T* R, T tol, int ma
   return it;
 }
 
+// ================================================================ mixed ===
+// FP32 helpers of the mixed path. The state is a unit quaternion q (rotation)
+// and E = S - I; every quantity that enters the residual is written as a
+// difference-free expression in E so that stiff materials (tiny strains) keep
+// their relative precision.
+
+// Quaternion (x, y, z, w), w the scalar part.
+struct Quat {
+  float x, y, z, w;
+};
+
+EMU_HD Quat qmul(Quat a, Quat b) {  // R(a b) = R(a) R(b)
+  Quat r;
+  r.w = a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z;
+  r.x = a.w * b.x + b.w * a.x + a.y * b.z - a.z * b.y;
+  r.y = a.w * b.y + b.w * a.y + a.z * b.x - a.x * b.z;
+  r.z = a.w * b.z + b.w * a.z + a.x * b.y - a.y * b.x;
+  return r;
+}
+
+EMU_HD Quat qnormalize(Quat a) {
+  float n = rsqrtf(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w);
+  return Quat{a.x * n, a.y * n, a.z * n, a.w * n};
+}
+
+// R(q) - I = 2 w [v]x + 2 [v]x^2 for a unit quaternion; accurate for small
+// rotations (no 1 - ... cancellation).
+template <typename T> EMU_HD void quat_rot_minus_I(T x, T y, T z, T w, T* D) {
+  const T xx = x * x, yy = y * y, zz = z * z;
+  const T xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y, wz = w * z;
+  D[0] = -T(2) * (yy + zz);
+  D[1] = T(2) * (xy - wz);
+  D[2] = T(2) * (xz + wy);
+  D[3] = T(2) * (xy + wz);
+  D[4] = -T(2) * (xx + zz);
+  D[5] = T(2) * (yz - wx);
+  D[6] = T(2) * (xz - wy);
+  D[7] = T(2) * (yz + wx);
+  D[8] = -T(2) * (xx + yy);
+}
+
+template <typename T> EMU_HD void quat_to_R(T x, T y, T z, T w, T* R) {
+  quat_rot_minus_I(x, y, z, w, R);
+  R[0] += T(1);
+  R[4] += T(1);
+  R[8] += T(1);
+}
+
+// Rotation matrix -> unit quaternion (Shepperd's branch on the largest pivot).
+template <typename T> EMU_HD void R_to_quat(const T* R, T* q) {
+  const T tr = R[0] + R[4] + R[8];
+  if (tr > R[0] && tr > R[4] && tr > R[8]) {
+    T s = sqrt(T(1) + tr) * T(2);
+    q[3] = T(0.25) * s;
+    q[0] = (R[7] - R[5]) / s;
+    q[1] = (R[2] - R[6]) / s;
+    q[2] = (R[3] - R[1]) / s;
+  } else if (R[0] > R[4] && R[0] > R[8]) {
+    T s = sqrt(T(1) + R[0] - R[4] - R[8]) * T(2);
+    q[3] = (R[7] - R[5]) / s;
+    q[0] = T(0.25) * s;
+    q[1] = (R[1] + R[3]) / s;
+    q[2] = (R[2] + R[6]) / s;
+  } else if (R[4] > R[8]) {
+    T s = sqrt(T(1) + R[4] - R[0] - R[8]) * T(2);
+    q[3] = (R[2] - R[6]) / s;
+    q[0] = (R[1] + R[3]) / s;
+    q[1] = T(0.25) * s;
+    q[2] = (R[5] + R[7]) / s;
+  } else {
+    T s = sqrt(T(1) + R[8] - R[0] - R[4]) * T(2);
+    q[3] = (R[3] - R[1]) / s;
+    q[0] = (R[2] + R[6]) / s;
+    q[1] = (R[5] + R[7]) / s;
+    q[2] = T(0.25) * s;
+  }
+  if (q[3] < T(0)) {
+    q[0] = -q[0];
+    q[1] = -q[1];
+    q[2] = -q[2];
+    q[3] = -q[3];
+  }
+  T n = T(1) / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  q[0] *= n;
+  q[1] *= n;
+  q[2] *= n;
+  q[3] *= n;
+}
+
+// e2(M) = ((tr M)^2 - tr(M M)) / 2 (second invariant; det(I + M) =
+// 1 + tr M + e2(M) + det M).
+template <typename T> EMU_HD T inv2(const T* M) {
+  const T tr = M[0] + M[4] + M[8];
+  const T trMM = M[0] * M[0] + M[4] * M[4] + M[8] * M[8] + T(2) * (M[1] * M[3] + M[2] * M[6] + M[5] * M[7]);
+  return T(0.5) * (tr * tr - trMM);
+}
+
+// x - log1p(x) without cancellation: series for small |x|.
+EMU_HD float x_minus_log1p(float x) {
+  if (fabsf(x) < 0.1f) {
+    // x^2/2 - x^3/3 + x^4/4 - ... (error < 0.1^10 relative)
+    float t = x * x;
+    float s = 1.f / 2 - x * (1.f / 3 - x * (1.f / 4 - x * (1.f / 5 - x * (1.f / 6 - x * (1.f / 7 - x * (1.f / 8 - x * (1.f / 9)))))));
+    return t * s;
+  }
+  return x - log1pf(x);
+}
+
+// Stretch quantities from E = S - I (FP32, difference-free):
+//   S, S^-1, ln J = log1p(tr E + e2(E) + det E), and S - S^-1 = (2E + E^2) S^-1.
+struct StretchE {
+  float S[9], Sinv[9], SmSi[9], lnJ;
+};
+
+EMU_HD bool stretch_from_E(const float* e6, StretchE& st) {
+  float E[9];
+  sym_from_s(e6, E);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) st.S[k] = E[k];
+  st.S[0] += 1.f;
+  st.S[4] += 1.f;
+  st.S[8] += 1.f;
+  const float x = (E[0] + E[4] + E[8]) + inv2(E) + det3(E);
+  if (!(x > -1.f)) return false;
+  st.lnJ = log1pf(x);
+  inv3(st.S, st.Sinv);
+  float T2[9], EE[9];
+  matmul3(E, E, EE);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) T2[k] = 2.f * E[k] + EE[k];
+  matmul3(T2, st.Sinv, st.SmSi);
+  return true;
+}
+
+// Rotated-frame Piola from E: Pr = mu (S - S^-1) + lam ln J S^-1 + 2 ka S u u^T.
+EMU_HD void piola_rotated_E(const StretchE& st, const ElemMat<float>& m, float* Pr) {
+  float Su[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) Su[r] = st.S[3 * r] * m.u[0] + st.S[3 * r + 1] * m.u[1] + st.S[3 * r + 2] * m.u[2];
+  const float ll = m.lam * st.lnJ;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Pr[3 * r + c] = m.mu * st.SmSi[3 * r + c] + ll * st.Sinv[3 * r + c] + 2.f * m.ka * Su[r] * m.u[c];
+}
+
+// Polar factor of I + Y close to the identity, in FP32 with relative
+// precision in Y: I + Y = Rx (I + Ex), Rx returned as a unit quaternion, Ex
+// (symmetric) as six stretch coordinates. Newton iteration on the rotation:
+// with M = Rx^T (I + Y) = I + Z, the step w solves
+// ((2 + tr Z) I - sym Z) w = 2 axial(skew Z) and Rx <- Rx exp([w]x).
+// Z = (Rx^T - I) + Y + (Rx^T - I) Y uses the cancellation-free R - I.
+EMU_HD int polar_near_identity(const float* Y, Quat& qx, float* e6, int max_iter) {
+  qx = Quat{0.f, 0.f, 0.f, 1.f};
+  float Z[9];
+  int it = 0;
+  for (;; ++it) {
+    float D[9];
+    quat_rot_minus_I(qx.x, qx.y, qx.z, qx.w, D);
+    float DT[9] = {D[0], D[3], D[6], D[1], D[4], D[7], D[2], D[5], D[8]};
+    float DY[9];
+    matmul3(DT, Y, DY);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Z[k] = DT[k] + Y[k] + DY[k];
+    if (it >= max_iter) break;
+    const float k0 = Z[7] - Z[5], k1 = Z[2] - Z[6], k2 = Z[3] - Z[1];
+    const float trz = Z[0] + Z[4] + Z[8];
+    float Ms[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Ms[3 * r + c] = -0.5f * (Z[3 * r + c] + Z[3 * c + r]);
+    Ms[0] += 2.f + trz;
+    Ms[4] += 2.f + trz;
+    Ms[8] += 2.f + trz;
+    float Mi[9];
+    inv3(Ms, Mi);
+    const float w0 = Mi[0] * k0 + Mi[1] * k1 + Mi[2] * k2;
+    const float w1 = Mi[3] * k0 + Mi[4] * k1 + Mi[5] * k2;
+    const float w2 = Mi[6] * k0 + Mi[7] * k1 + Mi[8] * k2;
+    const float ang2 = w0 * w0 + w1 * w1 + w2 * w2;
+    if (!(ang2 > 1e-16f)) break;  // |w| < 1e-8: converged (also stops on NaN)
+    const float ang = sqrtf(ang2);
+    float sh, ch;
+    sincosf(0.5f * ang, &sh, &ch);
+    const float f = sh / ang;
+    qx = qnormalize(qmul(qx, Quat{w0 * f, w1 * f, w2 * f, ch}));
+  }
+  s_from_mat(Z, e6);
+  return it;
+}
+
 }  // namespace emu

@@ -1,0 +1,56 @@
+// Mixed-precision (FP32 per tet, FP64 global) kernels of the Newton iteration.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "emu_internal.h"
+
+namespace emu {
+
+// Device arrays of the mixed path. Per-tet constants and the stretch state
+// are FP32; positions q and every global sum are FP64. The discrete operator
+// G is defined by the FP32 D_m^-1 values, and the host builds the FP64 ACAP
+// Laplacian from the same rounded values, so both precisions see one mesh.
+struct MixArgs {
+  int64_t m, n;
+  const int4* tet;
+  const float* Dinv;   // 9m
+  const float* V;      // m
+  const float* c;      // m  alpha w
+  const float* w;      // m
+  const float* mu;     // m
+  const float* lam;    // m
+  const float* ka;     // m  kappa a
+  const float* u;      // 3m
+  const float* gam;    // 48m
+  float4* quat;        // m  rotation (x, y, z, w)
+  float* E;            // 6m stretch coordinates of S - I
+  const double* q;     // 3n
+  const double* Q;     // 3n rest positions
+  const float* E0;     // 9m: G_i Q - I (rounding of the FP32 D_m^-1, static)
+  const float* dq;     // 3n
+  float* g;            // 9m
+  float* y;            // 9m
+  float* d;            // 9m
+  float* Uw;           // 54m
+  double* contrib;     // 12m corner terms
+  float* b32;          // 3n float RHS (unused by the tet kernels)
+  const double* z;     // 48
+  DevScalars* sc;
+  double* partials;
+};
+
+void launch_grad_mixed(const MixArgs& a, int grid, cudaStream_t st);
+void launch_dir_mixed(const MixArgs& a, int grid, cudaStream_t st);
+void launch_ls_mixed(const MixArgs& a, int grid, double rho, cudaStream_t st);
+void launch_update_mixed(const MixArgs& a, int grid, cudaStream_t st);
+void launch_rhs_state_mixed(const MixArgs& a, int grid, cudaStream_t st);
+void launch_syrk_mixed(const MixArgs& a, int grid, double* cpart, cudaStream_t st);
+void launch_update_verts_f(int64_t n, const DevScalars* sc, const float* dq, double* q, cudaStream_t st);
+void launch_assemble_f(int64_t n, const int32_t* slot_ptr, const int32_t* slot_idx, const double* contrib,
+                       const uint8_t* is_fixed, float* b, cudaStream_t st);
+// state conversion: (quat, E) <-> (R 9m, s 6m) FP64 structure of arrays
+void launch_mixed_to_Rs(int64_t m, const float4* quat, const float* E, double* R, double* s, cudaStream_t st);
+void launch_Rs_to_mixed(int64_t m, const double* R, const double* s, float4* quat, float* E, cudaStream_t st);
+
+}  // namespace emu

@@ -90,70 +90,163 @@ __device__ __forceinline__ void sum_partials(const double* partials, double* s_o
   block_partials<NV>(loc, s_out, sm);
 }
 
-template <int NR>
-__device__ __forceinline__ void spmv_row(const Laplacian& L, const double* __restrict__ x, int64_t v, double* acc) {
+template <int NR, typename T>
+__device__ __forceinline__ void spmv_row(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                         const T* __restrict__ val, const T* __restrict__ x, int64_t v, T* acc) {
 #pragma unroll
-  for (int j = 0; j < NR; ++j) acc[j] = 0.0;
-  const int32_t e0 = L.rowptr[v], e1 = L.rowptr[v + 1];
-  for (int32_t e = e0; e < e1; ++e) {
-    const int64_t c = L.col[e];
-    const double a = L.val[e];
+  for (int j = 0; j < NR; ++j) acc[j] = T(0);
+  const int32_t e0 = rowptr[v], e1 = rowptr[v + 1];
+  int32_t e = e0;
+  // four entries per step keeps several independent L2 loads in flight
+  for (; e + 4 <= e1; e += 4) {
+    int64_t c[4];
+    T a[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      c[k] = col[e + k];
+      a[k] = val[e + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) acc[j] += a[k] * __ldcg(x + c[k] * NR + j);
+  }
+  for (; e < e1; ++e) {
+    const int64_t c = col[e];
+    const T a = val[e];
 #pragma unroll
     for (int j = 0; j < NR; ++j) acc[j] += a * __ldcg(x + c * NR + j);
   }
 }
 
-template <int NR>
-__global__ void __launch_bounds__(256) pcg_kernel(PcgArgs a) {
-  constexpr int NV0 = 4 * NR;  // gamma, delta, rr, bb
-  constexpr int NV = 3 * NR;   // gamma, delta, rr
+// Preconditioner M = D^-1 + Phi E^-1 Phi^T (Jacobi plus an additive coarse
+// correction on the low-rank basis Phi of Eq. 9, E = Phi^T L Phi), when
+// COARSE. Phi^T r and Phi^T s are carried as recurrences
+// (rho <- rho - alpha sigma, sigma <- Phi^T w + beta sigma), and Phi^T w is
+// summed in the same reduction as the CG dot products, so the coarse term
+// adds no grid barrier to the two per iteration.
+template <int NR, typename T, bool COARSE>
+__global__ void __launch_bounds__(256) pcg_kernel(PcgArgsT<T> a) {
+  constexpr int NC = COARSE ? kModes * NR : 0;  // coarse values (mode j, column c) at j * NR + c
+  constexpr int NV0 = 4 * NR + NC;              // gamma, delta, rr, bb, Phi^T w
+  constexpr int NV = 3 * NR + NC;               // gamma, delta, rr, Phi^T w
   __shared__ double sm[8 * NV0];
   __shared__ double sc[NV0];
   __shared__ int s_flag;
-  __shared__ double s_alpha[NR], s_beta[NR], s_gamma[NR], s_thr[NR];
+  __shared__ double s_alpha[NR], s_beta[NR], s_gamma[NR], s_thr[NR], s_bb[NR], s_rr[NR];
   __shared__ int s_active[NR];
+  __shared__ double s_rho[NC > 0 ? NC : 1], s_sig[NC > 0 ? NC : 1];
+  __shared__ T s_cc[NC > 0 ? NC : 1];        // E^-1 rho: coarse coefficients of u
+  __shared__ double s_Einv[COARSE ? kModes * kModes : 1];
   unsigned epoch = 0;
-  const Laplacian L = a.L;
-  const int64_t n = L.n;
+  const int64_t n = a.n;
+  const int32_t* __restrict__ rowptr = a.rowptr;
+  const int32_t* __restrict__ col = a.col;
+  const T* __restrict__ val = a.val;
+  const T* __restrict__ dinv = a.dinv;
+  const T* __restrict__ phi = a.phi;
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * per;
   const int64_t r1 = r0 + per < n ? r0 + per : n;
-  const double* __restrict__ b = a.b;
-  double* __restrict__ x = a.x;
-  double* __restrict__ r = a.r;
-  double* __restrict__ u = a.u;
-  double* __restrict__ w = a.w;
-  double* __restrict__ p = a.p;
-  double* __restrict__ s = a.s;
-
-  // r = b - A x ; u = D^-1 r
-  for (int64_t v = r0 + threadIdx.x; v < r1; v += blockDim.x) {
-    double acc[NR];
-    spmv_row<NR>(L, x, v, acc);
-    const double di = L.dinv[v];
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      const double rv = b[v * NR + j] - acc[j];
-      r[v * NR + j] = rv;
-      u[v * NR + j] = di * rv;
-    }
+  const T* __restrict__ b = a.b;
+  T* __restrict__ x = a.x;
+  T* __restrict__ r = a.r;
+  T* __restrict__ u = a.u;
+  T* __restrict__ w = a.w;
+  T* __restrict__ p = a.p;
+  T* __restrict__ s = a.s;
+  if constexpr (COARSE) {
+    for (int k = threadIdx.x; k < kModes * kModes; k += blockDim.x) s_Einv[k] = a.Einv[k];
   }
+
+  // u_v = D^-1 r_v + sum_j phi_vj cc_j (coarse term when COARSE)
+  auto precond_row = [&](int64_t v) {
+    const T di = dinv[v];
+    T acc[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[j] = di * r[v * NR + j];
+    if constexpr (COARSE) {
+#pragma unroll
+      for (int k = 0; k < kModes; ++k) {
+        const T ph = phi[v * kModes + k];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) acc[j] += ph * s_cc[k * NR + j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) u[v * NR + j] = acc[j];
+  };
+  auto coarse_coeffs = [&]() {  // s_cc = E^-1 rho (all blocks identically)
+    if constexpr (COARSE) {
+      for (int e = threadIdx.x; e < NC; e += blockDim.x) {
+        const int k = e / NR, j = e % NR;
+        double acc = 0.0;
+        for (int l = 0; l < kModes; ++l) acc += s_Einv[k * kModes + l] * s_rho[l * NR + j];
+        s_cc[e] = (T)acc;
+      }
+      __syncthreads();
+    }
+  };
+
+  // r = b - A x
+  for (int64_t v = r0 + threadIdx.x; v < r1; v += blockDim.x) {
+    T acc[NR];
+    spmv_row<NR, T>(rowptr, col, val, x, v, acc);
+#pragma unroll
+    for (int j = 0; j < NR; ++j) r[v * NR + j] = b[v * NR + j] - acc[j];
+  }
+  if constexpr (COARSE) {  // rho = Phi^T r
+    double loc[NC > 0 ? NC : 1];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) loc[k] = 0.0;
+    for (int64_t v = r0 + threadIdx.x; v < r1; v += blockDim.x) {
+#pragma unroll
+      for (int k = 0; k < kModes; ++k) {
+        const double ph = (double)phi[v * kModes + k];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) loc[k * NR + j] += ph * (double)r[v * NR + j];
+      }
+    }
+    block_partials<NC>(loc, a.partials + (size_t)blockIdx.x * NV0, sm);
+    if (!grid_sync(a.bar, epoch, &s_flag)) goto timeout;
+    {
+      double tmp[NC > 0 ? NC : 1];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) tmp[k] = 0.0;
+      for (unsigned bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) tmp[k] += __ldcg(a.partials + (size_t)bb * NV0 + k);
+      }
+      block_partials<NC>(tmp, s_rho, sm);
+    }
+    coarse_coeffs();
+    if (!grid_sync(a.bar, epoch, &s_flag)) goto timeout;  // partials are rewritten below
+  }
+  for (int64_t v = r0 + threadIdx.x; v < r1; v += blockDim.x) precond_row(v);
   if (!grid_sync(a.bar, epoch, &s_flag)) goto timeout;
   {
     double loc[NV0];
 #pragma unroll
     for (int k = 0; k < NV0; ++k) loc[k] = 0.0;
     for (int64_t v = r0 + threadIdx.x; v < r1; v += blockDim.x) {
-      double acc[NR];
-      spmv_row<NR>(L, u, v, acc);
+      T acc[NR];
+      spmv_row<NR, T>(rowptr, col, val, u, v, acc);
 #pragma unroll
       for (int j = 0; j < NR; ++j) {
         const double rv = r[v * NR + j], uv = u[v * NR + j], bv = b[v * NR + j];
         w[v * NR + j] = acc[j];
         loc[j] += rv * uv;
-        loc[NR + j] += acc[j] * uv;
+        loc[NR + j] += (double)acc[j] * uv;
         loc[2 * NR + j] += rv * rv;
         loc[3 * NR + j] += bv * bv;
+      }
+      if constexpr (COARSE) {
+#pragma unroll
+        for (int k = 0; k < kModes; ++k) {
+          const double ph = (double)phi[v * kModes + k];
+#pragma unroll
+          for (int j = 0; j < NR; ++j) loc[4 * NR + k * NR + j] += ph * (double)acc[j];
+        }
       }
     }
     block_partials<NV0>(loc, a.partials + (size_t)blockIdx.x * NV0, sm);
@@ -163,6 +256,8 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgs a) {
   if (threadIdx.x == 0) {
     for (int j = 0; j < NR; ++j) {
       const double bb = sc[3 * NR + j];
+      s_bb[j] = bb;
+      s_rr[j] = sc[2 * NR + j];
       s_thr[j] = a.tol * a.tol * bb;
       s_gamma[j] = sc[j];
       const bool done = (sc[2 * NR + j] <= s_thr[j]) || !(sc[NR + j] > 0.0);
@@ -171,13 +266,16 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgs a) {
       s_beta[j] = 0.0;
     }
   }
+  if constexpr (COARSE) {
+    for (int e = threadIdx.x; e < NC; e += blockDim.x) s_sig[e] = sc[4 * NR + e];
+  }
   __syncthreads();
   for (int64_t v = r0 + threadIdx.x; v < r1; v += blockDim.x) {
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
       p[v * NR + j] = u[v * NR + j];
       s[v * NR + j] = w[v * NR + j];
-      if (sc[3 * NR + j] == 0.0) x[v * NR + j] = 0.0;  // zero right-hand side: x = 0 exactly
+      if (s_bb[j] == 0.0) x[v * NR + j] = T(0);  // zero right-hand side: x = 0 exactly
     }
   }
   {
@@ -186,17 +284,23 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgs a) {
     for (int j = 0; j < NR; ++j) all_done = all_done && (s_active[j] == 0);
     while (!all_done && it < a.max_iter) {
       ++it;
+      if constexpr (COARSE) {  // rho <- rho - alpha sigma, then the coarse coefficients
+        for (int e = threadIdx.x; e < NC; e += blockDim.x) {
+          const int j = e % NR;
+          if (s_active[j]) s_rho[e] -= s_alpha[j] * s_sig[e];
+        }
+        __syncthreads();
+        coarse_coeffs();
+      }
       for (int64_t v = r0 + threadIdx.x; v < r1; v += blockDim.x) {
-        const double di = L.dinv[v];
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
           if (!s_active[j]) continue;
-          const double al = s_alpha[j];
+          const T al = (T)s_alpha[j];
           x[v * NR + j] += al * p[v * NR + j];
-          const double rv = r[v * NR + j] - al * s[v * NR + j];
-          r[v * NR + j] = rv;
-          u[v * NR + j] = di * rv;
+          r[v * NR + j] -= al * s[v * NR + j];
         }
+        precond_row(v);
       }
       if (!grid_sync(a.bar, epoch, &s_flag)) goto timeout;
       {
@@ -204,15 +308,23 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgs a) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) loc[k] = 0.0;
         for (int64_t v = r0 + threadIdx.x; v < r1; v += blockDim.x) {
-          double acc[NR];
-          spmv_row<NR>(L, u, v, acc);
+          T acc[NR];
+          spmv_row<NR, T>(rowptr, col, val, u, v, acc);
 #pragma unroll
           for (int j = 0; j < NR; ++j) {
             const double rv = r[v * NR + j], uv = u[v * NR + j];
             w[v * NR + j] = acc[j];
             loc[j] += rv * uv;
-            loc[NR + j] += acc[j] * uv;
+            loc[NR + j] += (double)acc[j] * uv;
             loc[2 * NR + j] += rv * rv;
+          }
+          if constexpr (COARSE) {
+#pragma unroll
+            for (int k = 0; k < kModes; ++k) {
+              const double ph = (double)phi[v * kModes + k];
+#pragma unroll
+              for (int j = 0; j < NR; ++j) loc[3 * NR + k * NR + j] += ph * (double)acc[j];
+            }
           }
         }
         block_partials<NV>(loc, a.partials + (size_t)blockIdx.x * NV, sm);
@@ -223,6 +335,7 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgs a) {
         for (int j = 0; j < NR; ++j) {
           if (!s_active[j]) continue;
           const double g_new = sc[j], dl = sc[NR + j], rr = sc[2 * NR + j];
+          s_rr[j] = rr;
           if (rr <= s_thr[j]) {
             s_active[j] = 0;
             continue;
@@ -239,14 +352,21 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgs a) {
         }
       }
       __syncthreads();
+      if constexpr (COARSE) {  // sigma <- Phi^T w + beta sigma
+        for (int e = threadIdx.x; e < NC; e += blockDim.x) {
+          const int j = e % NR;
+          if (s_active[j]) s_sig[e] = sc[3 * NR + e] + s_beta[j] * s_sig[e];
+        }
+      }
       all_done = true;
       for (int j = 0; j < NR; ++j) all_done = all_done && (s_active[j] == 0);
+      __syncthreads();
       if (all_done) break;
       for (int64_t v = r0 + threadIdx.x; v < r1; v += blockDim.x) {
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
           if (!s_active[j]) continue;
-          const double be = s_beta[j];
+          const T be = (T)s_beta[j];
           p[v * NR + j] = u[v * NR + j] + be * p[v * NR + j];
           s[v * NR + j] = w[v * NR + j] + be * s[v * NR + j];
         }
@@ -256,6 +376,9 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgs a) {
       if (a.iters_out) atomicAdd(a.iters_out, it);
       if (a.fail_out && !all_done) atomicExch(a.fail_out, 1);
       if (a.last_iters) *a.last_iters = it;
+      if (a.relres_out) {
+        for (int j = 0; j < NR; ++j) a.relres_out[j] = s_bb[j] > 0.0 ? sqrt(s_rr[j] / s_bb[j]) : 0.0;
+      }
     }
   }
   return;
@@ -263,10 +386,11 @@ timeout:
   if (threadIdx.x == 0 && a.timeout_out) atomicExch(a.timeout_out, 1);
 }
 
-template <int NR> static cudaError_t launch_pcg_impl(const PcgArgs& args, int grid, cudaStream_t st) {
-  PcgArgs a = args;
+template <int NR, typename T, bool COARSE>
+static cudaError_t launch_pcg_impl(const PcgArgsT<T>& args, int grid, cudaStream_t st) {
+  PcgArgsT<T> a = args;
   void* params[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel((const void*)pcg_kernel<NR>, dim3(grid), dim3(256), params, 0, st);
+  return cudaLaunchCooperativeKernel((const void*)pcg_kernel<NR, T, COARSE>, dim3(grid), dim3(256), params, 0, st);
 }
 
 int pcg_max_grid(int nrhs, int64_t n) {
@@ -274,10 +398,10 @@ int pcg_max_grid(int nrhs, int64_t n) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (nrhs == 3)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel<3>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel<3, double, true>, 256, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel<16>, 256, 0);
-  if (occ < 1) occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel<16, double, false>, 256, 0);
+  if (occ < 1) return 1;  // cooperative launch needs co-residency; one block always fits
   // One block per SM at most: the barrier and the partial sums cost grow with
   // the block count, and 256 threads per SM already cover ~500 rows each.
   int64_t want = (n + 511) / 512;
@@ -286,12 +410,69 @@ int pcg_max_grid(int nrhs, int64_t n) {
   return (int)(g < 1 ? 1 : g);
 }
 
-cudaError_t launch_pcg(int nrhs, const PcgArgs& args, int grid, cudaStream_t st) {
+template <typename T> cudaError_t launch_pcg(int nrhs, const PcgArgsT<T>& args, int grid, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(args.bar, 0, sizeof(GridBarrier), st);
   if (e != cudaSuccess) return e;
-  if (nrhs == 3) return launch_pcg_impl<3>(args, grid, st);
-  if (nrhs == 16) return launch_pcg_impl<16>(args, grid, st);
+  if (nrhs == 3) {
+    if (args.phi && args.Einv) return launch_pcg_impl<3, T, true>(args, grid, st);
+    return launch_pcg_impl<3, T, false>(args, grid, st);
+  }
+  if (nrhs == 16) return launch_pcg_impl<16, T, false>(args, grid, st);
   return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_pcg<double>(int, const PcgArgsT<double>&, int, cudaStream_t);
+template cudaError_t launch_pcg<float>(int, const PcgArgsT<float>&, int, cudaStream_t);
+
+// ----------------------------------------------------- FP64 refinement ----
+// r = b - K x in FP64 for the first n rows, with a float copy for the inner
+// solve and per-block partial sums of |r|^2 and |b|^2 (3 columns each).
+__global__ void __launch_bounds__(256) k_residual64(int64_t n, const int32_t* __restrict__ rowptr,
+                                                    const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                    const double* __restrict__ b, const double* __restrict__ x,
+                                                    float* __restrict__ r32, double* __restrict__ partials) {
+  __shared__ double sm[8 * 6];
+  double loc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    double acc[3];
+    spmv_row<3, double>(rowptr, col, val, x, v, acc);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double bv = b[3 * v + j];
+      const double rv = bv - acc[j];
+      r32[3 * v + j] = (float)rv;
+      loc[j] += rv * rv;
+      loc[3 + j] += bv * bv;
+    }
+  }
+  block_partials<6>(loc, partials + (size_t)blockIdx.x * 6, sm);
+}
+
+__global__ void k_sum_partials6(const double* partials, int nblk, double* out) {
+  if (threadIdx.x < 6) {
+    double x = 0.0;
+    for (int b = 0; b < nblk; ++b) x += partials[(size_t)b * 6 + threadIdx.x];
+    out[threadIdx.x] = x;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_axpy_f2d(int64_t n3, const float* __restrict__ e, double* __restrict__ x) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x)
+    x[k] += (double)e[k];
+}
+
+cudaError_t launch_residual64(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* b,
+                              const double* x, float* r32, double* partials, int grid, double* out6, cudaStream_t st) {
+  k_residual64<<<grid, 256, 0, st>>>(n, rowptr, col, val, b, x, r32, partials);
+  k_sum_partials6<<<1, 32, 0, st>>>(partials, grid, out6);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_f2d(int64_t n3, const float* e, double* x, cudaStream_t st) {
+  int grid = (int)((n3 + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_axpy_f2d<<<grid, 256, 0, st>>>(n3, e, x);
+  return cudaGetLastError();
 }
 
 }  // namespace emu

@@ -14,15 +14,21 @@ struct GridBarrier {
 };
 
 // Vectors are vertex-major with nrhs values per vertex (x[v * nrhs + j]).
-struct PcgArgs {
-  Laplacian L;
-  const double* b;
-  double* x;  // in: warm start, out: solution
-  double* r;
-  double* u;
-  double* w;
-  double* p;
-  double* s;
+// T is the arithmetic of the iteration (double, or float for the inner
+// solves of the mixed path); reductions are always accumulated in FP64.
+template <typename T> struct PcgArgsT {
+  int64_t n;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const T* val;
+  const T* dinv;
+  const T* b;
+  T* x;  // in: warm start, out: solution
+  T* r;
+  T* u;
+  T* w;
+  T* p;
+  T* s;
   double* partials;  // grid * 4 * nrhs
   GridBarrier* bar;
   double tol;        // stop when ||r_j|| <= tol ||b_j|| for every column j
@@ -31,9 +37,19 @@ struct PcgArgs {
   int* fail_out;     // set to 1 when max_iter is reached (may be null)
   int* timeout_out;  // set to 1 when a grid barrier gave up (may be null)
   int* last_iters;   // iterations of this solve (may be null)
+  double* relres_out;  // final ||r_j|| / ||b_j|| per column (may be null)
+  const T* phi;        // n x 16 coarse basis (null: Jacobi only; 3 columns only)
+  const double* Einv;  // 16 x 16 (pseudo-)inverse of Phi^T L Phi
 };
 
 int pcg_max_grid(int nrhs, int64_t n);
-cudaError_t launch_pcg(int nrhs, const PcgArgs& args, int grid, cudaStream_t st);
+template <typename T> cudaError_t launch_pcg(int nrhs, const PcgArgsT<T>& args, int grid, cudaStream_t st);
+
+// FP64 residual r = b - K x (3 columns) with a float copy; out6 receives
+// sum |r_j|^2 (j < 3) and sum |b_j|^2 (3 + j).
+cudaError_t launch_residual64(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* b,
+                              const double* x, float* r32, double* partials, int grid, double* out6, cudaStream_t st);
+// x += e (float correction into the FP64 iterate), 3n values.
+cudaError_t launch_axpy_f2d(int64_t n3, const float* e, double* x, cudaStream_t st);
 
 }  // namespace emu

@@ -156,6 +156,21 @@ def test_mixed_path_matches_oracle_at_1e6(emu):
     assert st.rel_residual <= 1e-6
     err = np.abs(s.positions() - r.q).max() / _diag(mesh)
     assert err <= 1e-4, err
+    R, sv, F = s.element_state()
+    np.testing.assert_allclose(np.einsum("nji,njk->nik", R, R), np.broadcast_to(np.eye(3), R.shape), atol=2e-6)
+    np.testing.assert_allclose(np.linalg.det(R), 1.0, atol=2e-6)
+
+
+def test_mixed_muscle_tendon_unit_matches_oracle(emu):
+    # stiff tendon (E = 1e8 vs 6e5): the FP32 state keeps S - I, so the
+    # tendon's tiny strains keep their relative precision
+    mesh = muscle_tendon_unit(4, 4, 14, h=0.01, radius_cells=1.9, frames=1, a_max=0.6)
+    a = mesh.activations[0]
+    o, r = _oracle(mesh, a, tol=1e-10)
+    s, st = _solve_gpu(emu, mesh, a, precision=1, tol=1e-6)
+    assert st.rel_residual <= 1e-6
+    err = np.abs(s.positions() - r.q).max() / _diag(mesh)
+    assert err <= 1e-4, (err, st.newton_iters)
 
 
 def test_warm_started_frames_match_oracle(emu):
