@@ -84,6 +84,10 @@ struct emu_handle {
   float* phi32 = nullptr;
   double* Einv = nullptr;
   bool coarse_ready = false;
+  // register-resident FP32 CG: exchange buffer, partial sums, launch shape
+  float4* ug32 = nullptr;
+  float* part32 = nullptr;
+  int grid32 = 0, rpt32 = 0;
   double q_tol = 1e-8;
   double *part_grad = nullptr, *part_dir = nullptr, *part_ls = nullptr, *part_pcg = nullptr, *cpart = nullptr;
   double* z = nullptr;
@@ -425,6 +429,14 @@ int validate_params(const emu_params* p) {
 
 int read_scalars(emu_handle* h);
 
+// FP32 CG of the mixed path: the register-resident kernel when the mesh fits
+// its launch shape, the generic kernel otherwise.
+cudaError_t run_pcg32(emu_handle* h, const float* rhs, float* x, double tol) {
+  PcgArgsT<float> a = h->pcg32(rhs, x, tol);
+  if (h->rpt32 > 0) return launch_pcg32(a, h->ug32, h->part32, h->grid32, h->rpt32, h->st);
+  return launch_pcg<float>(3, a, h->grid_pcg3, h->st);
+}
+
 // Exact coupling solve q = q*(F) of Eq. 4 from the current F, warm-started
 // from the current q, to relative residual ``tol``. FP64 path: FP64 CG.
 // Mixed path: iterative refinement, the residual b - K q in FP64 and the
@@ -466,7 +478,7 @@ int refresh_q(emu_handle* h, double tol) {
     if (done) break;
     EMU_CK(cudaMemsetAsync(h->e32, 0, 12 * h->n, h->st));
     h->ph_begin();
-    EMU_CK(launch_pcg<float>(3, h->pcg32(h->r32, h->e32, 1e-5), h->grid_pcg3, h->st));
+    EMU_CK(run_pcg32(h, h->r32, h->e32, 1e-5));
     EMU_CK(launch_axpy_f2d(3 * h->n, h->e32, h->q, h->st));
     h->ph_end(EMU_PHASE_PCG, 2);
   }
@@ -491,7 +503,7 @@ int solve_dq(emu_handle* h) {
   h->ph_end(EMU_PHASE_ASSEMBLE, 1);
   EMU_CK(cudaGetLastError());
   h->ph_begin();
-  EMU_CK(launch_pcg<float>(3, h->pcg32(h->b32, h->dq32, tol), h->grid_pcg3, h->st));
+  EMU_CK(run_pcg32(h, h->b32, h->dq32, tol));
   h->ph_end(EMU_PHASE_PCG, 1);
   return EMU_OK;
 }
@@ -884,7 +896,10 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     ok = ok && h->get(h->gam64, 48 * m) && h->get(h->y64, 9 * m) && h->get(h->d64, 9 * m) && h->get(h->Uw64, 54 * m);
   ok = ok && h->get(h->pr, 16 * n) && h->get(h->pu, 16 * n) && h->get(h->pw, 16 * n) && h->get(h->pp, 16 * n) &&
        h->get(h->ps, 16 * n) && h->get(h->scratch16, 32 * n) && h->get(h->phi64, 16 * n) && h->get(h->Einv, 256);
-  if (h->mixed) ok = ok && h->get(h->phi32, 16 * n);
+  if (h->mixed) {
+    ok = ok && h->get(h->phi32, 16 * n) && h->get(h->ug32, n) && h->get(h->part32, 64 * (int64_t)h->sms);
+    if (!pcg32_shape(n, h->sms, &h->grid32, &h->rpt32)) h->rpt32 = 0;
+  }
   h->grid_tet = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 127) / 128), 8 * (int64_t)h->sms);
   h->grid_syrk = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 23) / 24), 2 * (int64_t)h->sms);
   h->grid_pcg3 = pcg_max_grid(3, n);

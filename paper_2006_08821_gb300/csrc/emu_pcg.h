@@ -45,6 +45,12 @@ template <typename T> struct PcgArgsT {
 int pcg_max_grid(int nrhs, int64_t n);
 template <typename T> cudaError_t launch_pcg(int nrhs, const PcgArgsT<T>& args, int grid, cudaStream_t st);
 
+// Register-resident FP32 CG (3 columns): shape for n rows on ``sms`` SMs
+// (false when n needs more than 8 rows per thread), and its launch. ``ug``
+// is an n-entry float4 exchange buffer, ``part`` holds grid * 64 floats.
+bool pcg32_shape(int64_t n, int sms, int* grid, int* rpt);
+cudaError_t launch_pcg32(const PcgArgsT<float>& args, float4* ug, float* part, int grid, int rpt, cudaStream_t st);
+
 // FP64 residual r = b - K x (3 columns) with a float copy; out6 receives
 // sum |r_j|^2 (j < 3) and sum |b_j|^2 (3 + j).
 cudaError_t launch_residual64(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* b,
