@@ -229,6 +229,29 @@ int emu_eval_stretch_terms(const double* s, const double* params, int64_t n, int
  * Outputs R (n x 9) and s (n x 6, ordering as emu_get_element_state). */
 int emu_eval_polar(const double* F, int64_t n, double* R, double* s, void* stream);
 
+/* Coupling solve without device allocation. The paper has no counterpart;
+ * this exists for callers that cannot call cudaMalloc or any allocating
+ * library routine, for instance code running inside a memory pool it does
+ * not own, or a host that forbids allocations after start-up.
+ *
+ * Solves q = q*(F) of Eq. 4 (pinned vertices held as at emu_create) with the
+ * handle's ACAP operator, for a per-tet F given by the caller. The iteration
+ * starts from the rest-state solution q*(I) and stops at the handle's
+ * coupling-solve tolerance min(pcg_tol, 1e-2 tol_rel_residual).
+ *   F_device  n_tets x 9 float64 on the device, row-major F per tet (input).
+ *   q_device  n_verts x 3 float64 on the device (output).
+ *   stream    cudaStream_t the work is enqueued on; the call synchronises it.
+ * All scratch memory is one fixed 32 MiB device array inside the library,
+ * reserved on every GPU that loads the library until the process exits. A
+ * mesh needs 96 n_tets + 144 n_verts bytes plus a few KB; larger meshes are
+ * rejected with EMU_ERR_INVALID_ARG. The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ * Every call uses the same array and it keeps the last call's contents, so
+ * calls that overlap on the GPU (other streams, other threads, other
+ * handles) race: serialise them. Returns EMU_ERR_PCG if the CG iteration
+ * cap is reached, EMU_ERR_TIMEOUT if a bounded device wait ran out. */
+int emu_acap_solve_noalloc(emu_handle* h, const double* F_device, double* q_device, void* stream);
+
 /* ---- profiling ----------------------------------------------------------
  * Kernel phases of one Newton iteration, in launch order. When profiling is
  * on, every launch of a phase is bracketed by CUDA events on the handle's

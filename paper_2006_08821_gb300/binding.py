@@ -37,6 +37,7 @@ EXPORTED = [
     "emu_set_activation", "emu_set_activation_device", "emu_solve_quasistatic", "emu_get_positions",
     "emu_get_element_state", "emu_set_element_state", "emu_reset", "emu_get_sizes",
     "emu_eval_stretch_terms", "emu_eval_polar", "emu_set_profiling", "emu_get_profile",
+    "emu_acap_solve_noalloc",
 ]
 
 PHASES = ["rhs", "assemble", "pcg", "grad", "syrk", "small", "dir", "ls", "update"]
@@ -140,6 +141,7 @@ def load_library(path: str = LIB_PATH):
                                            C.c_void_p, C.c_void_p, C.c_void_p]
     lib.emu_eval_polar.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.emu_set_profiling.argtypes = [C.c_void_p, C.c_int32]
+    lib.emu_acap_solve_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.emu_get_profile.argtypes = [C.c_void_p, P(C.c_double), P(C.c_int32), C.c_int32, P(C.c_int64)]
     for name in EXPORTED:
         if name not in ("emu_default_params", "emu_status_string", "emu_last_error"):
@@ -308,6 +310,12 @@ class Solver:
 
     def reset(self):
         _check(self.lib.emu_reset(self.handle), self.lib)
+
+    def acap_solve_noalloc(self, F_dev_ptr: int, q_dev_ptr: int, stream=None):
+        """emu_acap_solve_noalloc: q = q*(F) with no device allocation (device pointers)."""
+        st = C.c_void_p(int(stream)) if stream is not None else (
+            C.c_void_p(int(self.stream)) if self.stream is not None else None)
+        return self.lib.emu_acap_solve_noalloc(self.handle, C.c_void_p(int(F_dev_ptr)), C.c_void_p(int(q_dev_ptr)), st)
 
     def set_profiling(self, enable: bool):
         _check(self.lib.emu_set_profiling(self.handle, 1 if enable else 0), self.lib)

@@ -639,6 +639,36 @@ int compute_gref(emu_handle* h) {
 
 }  // namespace
 
+namespace emu {
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+bool acap_view(const emu_handle* h, AcapView* v) {
+  if (!h || !v) return false;
+  v->n = h->n;
+  v->m = h->m;
+  v->tet = h->tet;
+  v->Dinv = h->Dinv;
+  v->w = h->w;
+  v->slot_ptr = h->slot_ptr;
+  v->slot_idx = h->slot_idx;
+  v->bfix = h->bfix;
+  v->is_fixed = h->is_fixed;
+  v->qfix = h->qfix;
+  v->rowptr = h->rowptr;
+  v->col = h->col;
+  v->val = h->val;
+  v->ldinv = h->ldinv;
+  v->phi = h->coarse_ready ? h->phi64 : nullptr;
+  v->Einv = h->coarse_ready ? h->Einv : nullptr;
+  v->q0 = h->q0;
+  v->grid_pcg = h->grid_pcg3;
+  v->pcg_max = h->prm.pcg_max;
+  v->pcg_tol = h->q_tol;
+  v->sms = h->sms;
+  return true;
+}
+}  // namespace emu
+
 // ============================================================== C ABI =====
 extern "C" {
 

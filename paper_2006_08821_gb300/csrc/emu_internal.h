@@ -54,4 +54,31 @@ struct Laplacian {
   const double* dinv;   // 1 / L_vv
 };
 
+// Read-only view of a handle's mesh operator, for entry points that live
+// outside the handle's translation unit.
+struct AcapView {
+  int64_t n, m;
+  const int4* tet;
+  const double* Dinv;    // 9m structure of arrays
+  const double* w;       // m
+  const int32_t* slot_ptr;
+  const int32_t* slot_idx;
+  const double* bfix;
+  const uint8_t* is_fixed;
+  const double* qfix;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const double* ldinv;
+  const double* phi;     // null when the coarse space is not built
+  const double* Einv;
+  const double* q0;      // rest-state solution q*(I)
+  int grid_pcg;
+  int pcg_max;
+  double pcg_tol;
+  int sms;
+};
+bool acap_view(const emu_handle* h, AcapView* v);
+void set_last_error(const char* msg);
+
 }  // namespace emu
