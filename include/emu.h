@@ -125,10 +125,12 @@ typedef struct {
  *   dq_tol          relative residual of the per-iteration solve for the
  *                   change of q along the search direction (q*(F + s d) =
  *                   q + s dq, q* being affine); q itself is then updated by
- *                   linearity (default 1e-4).
+ *                   linearity (default 3e-2). After a line search fails,
+ *                   q is re-solved and dq is solved to the exact-solve
+ *                   tolerance for the rest of the call.
  *   q_refresh       every q_refresh iterations, and before convergence is
  *                   declared, q is re-solved exactly from the current F
- *                   (default 16). */
+ *                   (default 32). */
 typedef struct {
   double alpha_rel;
   int32_t weight_mode;

@@ -179,8 +179,8 @@ class Params:
     precision: int = PRECISION_FP64
     mode_iters: int = 4
     seed: int = 12345
-    dq_tol: float = 1e-4
-    q_refresh: int = 16
+    dq_tol: float = 3e-2
+    q_refresh: int = 32
 
     def to_c(self) -> emu_params:
         p = emu_params()

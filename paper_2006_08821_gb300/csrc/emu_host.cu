@@ -85,10 +85,12 @@ struct emu_handle {
   double* Einv = nullptr;
   bool coarse_ready = false;
   // register-resident FP32 CG: exchange buffer, partial sums, launch shape
-  float4* ug32 = nullptr;
+  float4* ug32 = nullptr;                // 2 n exchange entries of the FP32 CG
+  unsigned* sync32 = nullptr;             // its barrier words
   float* part32 = nullptr;
   int grid32 = 0, rpt32 = 0;
   double q_tol = 1e-8;
+  double dq_tol_now = 3e-2;  // dq tolerance of the current solve call
   double *part_grad = nullptr, *part_dir = nullptr, *part_ls = nullptr, *part_pcg = nullptr, *cpart = nullptr;
   double* z = nullptr;
   double* cfull = nullptr;  // summed capacitance entries
@@ -433,7 +435,13 @@ int read_scalars(emu_handle* h);
 // its launch shape, the generic kernel otherwise.
 cudaError_t run_pcg32(emu_handle* h, const float* rhs, float* x, double tol) {
   PcgArgsT<float> a = h->pcg32(rhs, x, tol);
-  if (h->rpt32 > 0) return launch_pcg32(a, h->ug32, h->part32, h->grid32, h->rpt32, h->st);
+  if (h->rpt32 > 0) {
+    Pcg32Work w;
+    w.ug = h->ug32;
+    w.part = h->part32;
+    w.sync = h->sync32;
+    return launch_pcg32(a, w, h->grid32, h->rpt32, h->st);
+  }
   return launch_pcg<float>(3, a, h->grid_pcg3, h->st);
 }
 
@@ -485,9 +493,10 @@ int refresh_q(emu_handle* h, double tol) {
   return EMU_OK;
 }
 
-// dq: the linear change of q* along the direction d, to dq_tol (loose).
+// dq: the linear change of q* along the direction d, to dq_tol (loose), or
+// to the exact-solve tolerance once a line search has failed in this call.
 int solve_dq(emu_handle* h) {
-  const double tol = h->prm.dq_tol;
+  const double tol = h->dq_tol_now;
   if (!h->mixed) {
     h->ph_begin();
     launch_assemble(h->n, h->slot_ptr, h->slot_idx, h->contrib, h->bfix, h->is_fixed, h->qfix, 1, h->b, h->st);
@@ -689,8 +698,8 @@ void emu_default_params(emu_params* p) {
   p->pcg_max = 5000;
   p->precision = EMU_PRECISION_FP64;
   p->mode_iters = 4;
-  p->dq_tol = 1e-4;
-  p->q_refresh = 16;
+  p->dq_tol = 3e-2;
+  p->q_refresh = 32;
   p->seed = 12345;
 }
 
@@ -927,7 +936,8 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
   ok = ok && h->get(h->pr, 16 * n) && h->get(h->pu, 16 * n) && h->get(h->pw, 16 * n) && h->get(h->pp, 16 * n) &&
        h->get(h->ps, 16 * n) && h->get(h->scratch16, 32 * n) && h->get(h->phi64, 16 * n) && h->get(h->Einv, 256);
   if (h->mixed) {
-    ok = ok && h->get(h->phi32, 16 * n) && h->get(h->ug32, n) && h->get(h->part32, 64 * (int64_t)h->sms);
+    ok = ok && h->get(h->phi32, 16 * n) && h->get(h->ug32, 2 * n) && h->get(h->part32, 64 * (int64_t)h->sms) &&
+         h->get(h->sync32, 96);
     if (!pcg32_shape(n, h->sms, &h->grid32, &h->rpt32)) h->rpt32 = 0;
   }
   h->grid_tet = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 127) / 128), 8 * (int64_t)h->sms);
@@ -953,6 +963,12 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     h->release();
     delete h;
     return fail(EMU_ERR_OOM, "pinned host allocation failed");
+  }
+  // barrier words of the FP32 CG start at zero (every launch leaves them so)
+  if (h->sync32 && cudaMemsetAsync(h->sync32, 0, 96 * sizeof(unsigned), h->st) != cudaSuccess) {
+    h->release();
+    delete h;
+    return fail(EMU_ERR_CUDA, "cudaMemsetAsync failed");
   }
 
   auto up = [&](void* dst, const void* src, size_t bytes) {
@@ -1063,7 +1079,9 @@ int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats) {
   TetArgs<double> a64 = h->args<double>();
   MixArgs am = h->margs();
   int since = h->prm.q_refresh;  // iterations since q was last solved exactly
+  h->dq_tol_now = h->prm.dq_tol;
   bool first_eval = true;
+  bool ls_retried = false;  // q was re-solved after the current run of rejected steps
   for (;;) {
     // q = q*(F) exactly every q_refresh iterations; in between q follows
     // q*(F + s d) = q + s dq (Eq. 4 is affine in F).
@@ -1104,7 +1122,23 @@ int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats) {
       }
       break;
     }
+    if (hs.sigma > 0.0) ls_retried = false;  // the last pass accepted a step
     if (hs.ls_fail * kLsTrials >= h->prm.ls_max_trials) {
+      if (since > 0 && !ls_retried) {
+        // q has drifted from q*(F) by the loose dq solves, so the slope the
+        // Armijo test uses no longer matches the energy (a loose residual
+        // can leave a large error in the K-norm): re-solve q exactly, solve
+        // dq tightly from now on and restart the line search
+        const int32_t zero = 0;
+        const double s0 = h->prm.ls_sigma0;
+        EMU_CK(cudaMemcpyAsync(&h->sc->ls_fail, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->st));
+        EMU_CK(cudaMemcpyAsync(&h->sc->sigma_start, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st));
+        EMU_CK(cudaStreamSynchronize(h->st));
+        since = h->prm.q_refresh;
+        h->dq_tol_now = h->q_tol;  // and keep q exact along the steps from here on
+        ls_retried = true;
+        continue;
+      }
       status = fail(EMU_ERR_LINESEARCH, "no Armijo step");
       break;
     }
@@ -1114,13 +1148,16 @@ int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats) {
     }
     // Woodbury direction (Eqs. 9-12)
     h->ph_begin();
-    if (h->mixed)
-      launch_syrk_mixed(am, h->grid_syrk, h->cpart, h->st);
-    else
+    int syrk_blocks = h->grid_syrk;
+    if (h->mixed) {
+      syrk_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (h->m + 31) / 32), 2 * (int64_t)h->sms);
+      launch_syrk_tc(am, syrk_blocks, h->cpart, h->st);
+    } else {
       launch_syrk<double>(a64, h->grid_syrk, h->cpart, h->st);
+    }
     h->ph_end(EMU_PHASE_SYRK, 1);
     h->ph_begin();
-    launch_cap_solve(h->cpart, h->grid_syrk, h->cfull, h->z, h->sc, h->st);
+    launch_cap_solve(h->cpart, syrk_blocks, h->cfull, h->z, h->sc, h->mixed, h->st);
     h->ph_end(EMU_PHASE_SMALL, 2);
     h->ph_begin();
     if (h->mixed) {

@@ -318,78 +318,99 @@ __global__ void __launch_bounds__(256) k_reduce_cpart(const double* __restrict__
   if (lane == 0) cfull[e] = x;
 }
 
-// Factor C = L L^T in FP64 (C symmetrised) and solve z = C^-1 (B y).
+// Factor C = L L^T (C symmetrised) and solve z = C^-1 (B y), in T arithmetic
+// (FP64; FP32 for the mixed path, whose C comes from TF32 products).
+// Right-looking Cholesky with all 256 threads and one barrier per column:
+// the column below the diagonal is left unscaled (L_ij = C_ij / sqrt(d_j),
+// d_j the pivot), so each column is a single rank-1 update of the trailing
+// lower triangle, C_ik -= C_ij C_kj / d_j, on a fixed 16 x 16 thread grid.
+// The two triangular solves run in one warp with the right-hand side in
+// registers. In FP64 the pivots' reciprocals and square roots on GB300's
+// narrow FP64 path set its latency.
+template <typename T>
 __global__ void __launch_bounds__(256) k_cap_solve(const double* __restrict__ cfull, double* z, DevScalars* sc) {
-  __shared__ double C[kK][kK + 1];
-  __shared__ double by[kK];
+  __shared__ T C[kK][kK + 1];
+  __shared__ T rinv[kK];  // 1 / sqrt(d_j)
   __shared__ int s_ok;
   const int tid = threadIdx.x;
-  for (int e = tid; e < kCapEntries + kK; e += blockDim.x) {
-    const double x = cfull[e];
-    if (e < kCapEntries)
-      C[e / kK][e % kK] = x;
-    else
-      by[e - kCapEntries] = x;
-  }
+  const int ti = tid >> 4, tk = tid & 15;
+  for (int e = tid; e < kCapEntries; e += blockDim.x) C[e / kK][e % kK] = (T)cfull[e];
   if (tid == 0) s_ok = 1;
   __syncthreads();
   // unused modes (k_modes < 48) have zero rows: make them identity rows
-  if (tid < kK && C[tid][tid] == 0.0) {
-    C[tid][tid] = 1.0;
-    by[tid] = 0.0;
-  }
-  __syncthreads();
-  // symmetrise
+  if (tid < kK && cfull[tid * kK + tid] == 0.0) C[tid][tid] = T(1);
+  // symmetrise into the lower triangle
   for (int e = tid; e < kCapEntries; e += blockDim.x) {
     const int i = e / kK, j = e % kK;
-    if (j > i) {
-      const double v = 0.5 * (C[i][j] + C[j][i]);
-      C[i][j] = v;
-      C[j][i] = v;
-    }
+    if (j < i) C[i][j] = T(0.5) * (C[i][j] + C[j][i]);
   }
   __syncthreads();
   for (int j = 0; j < kK; ++j) {
-    if (tid == 0) {
-      double d = C[j][j];
-      for (int k = 0; k < j; ++k) d -= C[j][k] * C[j][k];
-      if (!(d > 0.0)) {
-        s_ok = 0;
-        d = 1.0;
+    T d = C[j][j];
+    if (!(d > T(0))) d = T(1);  // failure is recorded below
+    const T rho = T(1) / d;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int i = j + 1 + ti + 16 * a;
+      if (i >= kK) break;
+      const T cij = C[i][j] * rho;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int k = j + 1 + tk + 16 * b;
+        if (k <= i) C[i][k] -= cij * C[k][j];
       }
-      C[j][j] = sqrt(d);
-    }
-    __syncthreads();
-    for (int i = j + 1 + tid; i < kK; i += blockDim.x) {
-      double v = C[i][j];
-      for (int k = 0; k < j; ++k) v -= C[i][k] * C[j][k];
-      C[i][j] = v / C[j][j];
     }
     __syncthreads();
   }
-  if (tid == 0) {
-    double x[kK];
-    for (int i = 0; i < kK; ++i) {
-      double v = by[i];
-      for (int k = 0; k < i; ++k) v -= C[i][k] * x[k];
-      x[i] = v / C[i][i];
+  if (tid < kK) {
+    const T d = C[tid][tid];
+    if (!(d > T(0))) atomicExch(&s_ok, 0);
+    rinv[tid] = d > T(0) ? T(1) / sqrt(d) : T(1);
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int lane = tid;
+    const bool has1 = lane + 32 < kK;
+    T x0 = (T)cfull[kCapEntries + lane];
+    T x1 = has1 ? (T)cfull[kCapEntries + lane + 32] : T(0);
+    if (cfull[lane * kK + lane] == 0.0) x0 = T(0);  // unused mode: identity row, zero right-hand side
+    if (has1 && cfull[(lane + 32) * kK + lane + 32] == 0.0) x1 = T(0);
+    // L y = b: y_j = x_j / L_jj, then x_i -= L_ij y_j for i > j
+    for (int j = 0; j < kK; ++j) {
+      const T xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31);
+      const T yj = xj * rinv[j];
+      const T f = rinv[j] * yj;  // L_ij y_j = C_ij f
+      if (lane == (j & 31)) {
+        if (j < 32) x0 = yj; else x1 = yj;
+      }
+      if (lane > j) x0 -= C[lane][j] * f;
+      if (has1 && lane + 32 > j) x1 -= C[lane + 32][j] * f;
     }
-    for (int i = kK - 1; i >= 0; --i) {
-      double v = x[i];
-      for (int k = i + 1; k < kK; ++k) v -= C[k][i] * x[k];
-      x[i] = v / C[i][i];
+    // L^T z = y: z_j = x_j / L_jj, then x_i -= L_ji z_j for i < j
+    for (int j = kK - 1; j >= 0; --j) {
+      const T xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31);
+      const T zj = xj * rinv[j];
+      if (lane == (j & 31)) {
+        if (j < 32) x0 = zj; else x1 = zj;
+      }
+      if (lane < j) x0 -= C[j][lane] * rinv[lane] * zj;
+      if (has1 && lane + 32 < j) x1 -= C[j][lane + 32] * rinv[lane + 32] * zj;
     }
-    const bool ok = s_ok != 0;
-    for (int i = 0; i < kK; ++i) z[i] = ok ? x[i] : 0.0;
-    sc->cap_ok = ok ? 1.0 : 0.0;
+    const int ok = s_ok;
+    z[lane] = ok ? (double)x0 : 0.0;
+    if (has1) z[lane + 32] = ok ? (double)x1 : 0.0;
+    if (lane == 0) sc->cap_ok = ok ? 1.0 : 0.0;
   }
 }
 
 void launch_cap_solve(const double* cpart, int nblk, const double* cfull_scratch, double* z, DevScalars* sc,
-                      cudaStream_t st) {
+                      bool fp32_factor, cudaStream_t st) {
   double* cfull = const_cast<double*>(cfull_scratch);
   k_reduce_cpart<<<(kCapEntries + kK + 7) / 8, 256, 0, st>>>(cpart, nblk, cfull);
-  k_cap_solve<<<1, 256, 0, st>>>(cfull, z, sc);
+  if (fp32_factor)
+    k_cap_solve<float><<<1, 256, 0, st>>>(cfull, z, sc);
+  else
+    k_cap_solve<double><<<1, 256, 0, st>>>(cfull, z, sc);
 }
 
 // ------------------------------------------------------------ direction ---

@@ -53,9 +53,9 @@ void launch_update_verts(int64_t n, const DevScalars* sc, const double* dq, doub
 void launch_reduce_grad(const double* partials, int nblk, DevScalars* sc, double* By, double* gsum,
                         cudaStream_t st);
 // cpart: entry-major partials (kCapEntries + kK entries x nblk blocks);
-// cfull_scratch receives their sums.
+// cfull_scratch receives their sums. fp32_factor: factor and solve in FP32.
 void launch_cap_solve(const double* cpart, int nblk, const double* cfull_scratch, double* z, DevScalars* sc,
-                      cudaStream_t st);
+                      bool fp32_factor, cudaStream_t st);
 void launch_ls_select(const double* dir_partials, int nblk_dir, const double* ls_partials, int nblk_ls,
                       DevScalars* sc, double sigma0, double rho, double c_armijo, cudaStream_t st);
 

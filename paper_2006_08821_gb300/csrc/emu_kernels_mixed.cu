@@ -255,6 +255,202 @@ void launch_syrk_mixed(const MixArgs& a, int grid, double* cpart, cudaStream_t s
   k_syrk_m<<<grid, 256, 0, st>>>(a, cpart);
 }
 
+// Tensor-core form of the same contraction: C += Yh^T Yh on TF32 tensor
+// cores (mma.sync m16n8k8, FP32 accumulate). Yh is rounded to TF32 once,
+// before the product, so C is still the exact Gram matrix of the rounded
+// rows and stays positive semi-definite.
+//
+// The kernel streams U, gamma, y and w (about 450 bytes per tet) and is
+// meant to run at HBM speed, so the loads are decoupled from the math: the
+// raw inputs of the next 32-tet chunk are copied into shared memory with
+// cp.async while the current chunk is formed and multiplied (two buffers).
+// Each warp owns a contiguous K-range of every chunk and the 12 output tiles
+// (16 x 8) that touch the upper triangle; the warps' tiles are summed in
+// shared memory and the lower triangle mirrored at the end.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const float* g, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(saddr), "l"(g), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+constexpr int kTcCH = 32;              // tets per chunk
+constexpr int kTcKR = kTcCH * 6;       // 192 rows of Yh per chunk: 24 k-steps of 8, 3 per warp
+constexpr int kTcLD = kK + 4;          // padded row of Yh (TF32 bits)
+constexpr int kTcRawRows = 54 + 48 + 9 + 1;  // U, gamma, y, w of a chunk
+constexpr int kTcRL = kTcCH + 1;             // padded raw row
+constexpr size_t kTcYBytes = sizeof(uint32_t) * kTcKR * kTcLD;
+constexpr size_t kTcRawBytes = sizeof(float) * kTcRawRows * kTcRL;
+constexpr size_t kTcSmem = kTcYBytes + 2 * kTcRawBytes;
+
+__global__ void __launch_bounds__(256) k_syrk_tc(MixArgs a, double* __restrict__ cpart) {
+  constexpr int CH = kTcCH, LD = kTcLD, RL = kTcRL;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t* sY = reinterpret_cast<uint32_t*>(smem_raw);
+  float* sRaw = reinterpret_cast<float*>(smem_raw + kTcYBytes);
+  float* sC = reinterpret_cast<float*>(sY);  // reused for the final sum of the warps' tiles
+  float* sBy = sC + kK * kK;                  // and for the final sum of B y
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int64_t m = a.m;
+  const int64_t nch = (m + CH - 1) / CH;
+
+  // cp.async of one chunk's raw rows: element e = row * 32 + tet
+  auto issue = [&](int64_t ch, int buf) {
+    const int64_t base = ch * CH;
+    float* dst = sRaw + buf * (kTcRawRows * RL);
+    for (int e = tid; e < kTcRawRows * CH; e += 256) {
+      const int row = e >> 5, tt = e & 31;
+      const int64_t i = base + tt;
+      const bool ok = i < m;
+      const int64_t ic = ok ? i : 0;
+      const float* src;
+      if (row < 54)
+        src = a.Uw + (int64_t)row * m + ic;
+      else if (row < 102)
+        src = a.gam + (int64_t)(row - 54) * m + ic;
+      else if (row < 111)
+        src = a.y + (int64_t)(row - 102) * m + ic;
+      else
+        src = a.w + ic;
+      cp_async4((uint32_t)__cvta_generic_to_shared(dst + row * RL + tt), src, ok);
+    }
+  };
+
+  // staging role: threads 0..191 own (tet slot stt = tid / 6, row k = tid % 6)
+  const int stt = tid / 6, sk = tid % 6;
+  float acc[12][4];
+#pragma unroll
+  for (int t = 0; t < 12; ++t)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[t][c] = 0.f;
+  // B y entries 8 sk .. 8 sk + 7 (r = sk / 2, j = 8 (sk % 2) + t) of the
+  // staging thread's tet slot, summed over the block's chunks
+  float by8[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) by8[t] = 0.f;
+  const int br = sk >> 1, bh = sk & 1;
+
+  if (blockIdx.x < nch) issue(blockIdx.x, 0);
+  cp_async_commit();
+  int it = 0;
+  for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x, ++it) {
+    const int64_t nxt = ch + gridDim.x;
+    if (nxt < nch) issue(nxt, (it + 1) & 1);
+    cp_async_commit();
+    cp_async_wait1();  // this thread's copies of chunk ch have landed
+    __syncthreads();   // and everyone else's
+    if (tid < 6 * CH) {
+      // Yh[tt*6 + k][16 r + j] = sqrt(w) sum_b U[k][3r+b] gam_j[b]
+      const float* raw = sRaw + (it & 1) * (kTcRawRows * RL) + stt;
+      float u9[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) u9[c] = raw[(9 * sk + c) * RL];
+      const float wi = raw[111 * RL];
+      const float sw = sqrtf(wi);
+      const float y0 = wi * raw[(102 + 3 * br) * RL];
+      const float y1 = wi * raw[(102 + 3 * br + 1) * RL];
+      const float y2 = wi * raw[(102 + 3 * br + 2) * RL];
+      uint32_t* row = sY + (stt * 6 + sk) * LD;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float g0 = raw[(54 + 3 * j) * RL];
+        const float g1 = raw[(54 + 3 * j + 1) * RL];
+        const float g2 = raw[(54 + 3 * j + 2) * RL];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) row[16 * r + j] = to_tf32(sw * (u9[3 * r] * g0 + u9[3 * r + 1] * g1 + u9[3 * r + 2] * g2));
+        const float byj = y0 * g0 + y1 * g1 + y2 * g2;
+        by8[j & 7] += ((j >> 3) == bh) ? byj : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < 3; ++ks) {
+      const int k0 = (warp * 3 + ks) * 8;
+      uint32_t af[3][4], bf[6][2];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int m0 = 16 * i;
+        af[i][0] = sY[(k0 + tig) * LD + m0 + gid];
+        af[i][1] = sY[(k0 + tig) * LD + m0 + gid + 8];
+        af[i][2] = sY[(k0 + tig + 4) * LD + m0 + gid];
+        af[i][3] = sY[(k0 + tig + 4) * LD + m0 + gid + 8];
+      }
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const int n0 = 8 * j;
+        bf[j][0] = sY[(k0 + tig) * LD + n0 + gid];
+        bf[j][1] = sY[(k0 + tig + 4) * LD + n0 + gid];
+      }
+      int t = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 2 * i; j < 6; ++j) mma_tf32(acc[t++], af[i], bf[j]);
+    }
+    __syncthreads();
+  }
+  // sum the warps' tiles in shared memory (warp order fixed)
+  for (int e = tid; e < kK * kK; e += 256) sC[e] = 0.f;
+  __syncthreads();
+  for (int w = 0; w < 8; ++w) {
+    if (warp == w) {
+      int t = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 2 * i; j < 6; ++j, ++t) {
+          const int r0 = 16 * i + gid, c0 = 8 * j + 2 * tig;
+          sC[r0 * kK + c0] += acc[t][0];
+          sC[r0 * kK + c0 + 1] += acc[t][1];
+          sC[(r0 + 8) * kK + c0] += acc[t][2];
+          sC[(r0 + 8) * kK + c0 + 1] += acc[t][3];
+        }
+    }
+    __syncthreads();
+  }
+  if (tid < 6 * CH)
+#pragma unroll
+    for (int t = 0; t < 8; ++t) sBy[stt * kK + 8 * sk + t] = by8[t];
+  __syncthreads();
+  const size_t nb = gridDim.x;
+  for (int e = tid; e < kK * kK; e += 256) {
+    const int r = e / kK, c = e % kK;
+    const bool computed = (c >> 3) >= 2 * (r >> 4);  // tile (r / 16, c / 8) was multiplied
+    cpart[(size_t)e * nb + blockIdx.x] = (double)(computed ? sC[e] : sC[c * kK + r]);
+  }
+  if (tid < kK) {
+    double by = 0.0;
+    for (int tt = 0; tt < CH; ++tt) by += (double)sBy[tt * kK + tid];
+    cpart[(size_t)(kCapEntries + tid) * nb + blockIdx.x] = by;
+  }
+}
+
+void launch_syrk_tc(const MixArgs& a, int grid, double* cpart, cudaStream_t st) {
+  // the opt-in shared-memory size is a per-device property of the kernel
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    attr_set[dev] = true;
+  }
+  k_syrk_tc<<<grid, 256, kTcSmem, st>>>(a, cpart);
+}
+
 // ------------------------------------------------------------ direction ---
 __global__ void __launch_bounds__(128) k_dir_m(MixArgs a) {
   __shared__ float sz[kK];

@@ -45,11 +45,19 @@ template <typename T> struct PcgArgsT {
 int pcg_max_grid(int nrhs, int64_t n);
 template <typename T> cudaError_t launch_pcg(int nrhs, const PcgArgsT<T>& args, int grid, cudaStream_t st);
 
+// Work space of the register-resident FP32 CG.
+struct Pcg32Work {
+  float4* ug;      // 2 n exchange entries (x, then u, per vertex)
+  float* part;     // 64 * grid block partial sums, value-major
+  unsigned* sync;  // 96 words of barrier state, zero before the first launch
+                   // (each launch leaves them zero)
+};
+
 // Register-resident FP32 CG (3 columns): shape for n rows on ``sms`` SMs
-// (false when n needs more than 8 rows per thread), and its launch. ``ug``
-// is an n-entry float4 exchange buffer, ``part`` holds grid * 64 floats.
+// (false when n needs more than 8 rows per thread), and its launch (at most
+// 256 blocks). args.bar, args.r .. args.s and args.partials are unused.
 bool pcg32_shape(int64_t n, int sms, int* grid, int* rpt);
-cudaError_t launch_pcg32(const PcgArgsT<float>& args, float4* ug, float* part, int grid, int rpt, cudaStream_t st);
+cudaError_t launch_pcg32(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, int rpt, cudaStream_t st);
 
 // FP64 residual r = b - K x (3 columns) with a float copy; out6 receives
 // sum |r_j|^2 (j < 3) and sum |b_j|^2 (3 + j).

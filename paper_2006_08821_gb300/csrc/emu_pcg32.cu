@@ -8,8 +8,10 @@
 //   * every vector of the rows a thread owns lives in registers for the
 //     whole solve; only u (needed by neighbouring rows) goes through global
 //     memory, as one float4 per vertex;
-//   * every reduction is FP32 with a fixed shuffle/shared-memory tree, so all
-//     blocks hold bit-identical scalars and the result is deterministic;
+//   * every reduction is FP32 with a fixed shuffle/shared-memory tree
+//     (transposed butterflies: a warp moves each value through the shuffle
+//     unit about once), so all blocks hold bit-identical scalars and the
+//     result is deterministic;
 //   * the matrix, D^-1 and Phi are read-only for the whole launch (__ldg).
 // Two grid-wide barriers per iteration (after u, after the partial sums).
 #include <cuda_runtime.h>
@@ -25,47 +27,124 @@ namespace {
 constexpr int NT = 256;  // threads per block
 constexpr int NR = 3;    // right-hand sides (x, y, z)
 constexpr unsigned long long kSpinLimit32 = 1ull << 25;
+constexpr int kGather = 16;  // entries of a matrix row gathered at once
+constexpr int kMaxGridStrides = 8;  // grid_sum_f handles up to 256 blocks
+// words of Pcg32Work::sync, one 128-byte line apart
+constexpr int kSyncCount = 0, kSyncDone = 32, kSyncErr = 64;
 
-__device__ __forceinline__ bool gsync(GridBarrier* bar, unsigned& epoch, int* s_flag) {
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier: every block adds 1 to an arrival counter with a release
+// reduction (its writes become visible first), and one thread per block
+// polls the counter with acquire loads until all blocks of this barrier
+// have arrived. The counter is never reset inside a launch (barrier e waits
+// for e * gridDim.x arrivals); the last block to leave the kernel zeroes it
+// for the next launch. The wait is bounded: on timeout the block raises the
+// error word, every other waiter sees it, and all blocks leave.
+__device__ __forceinline__ bool gbar(const Pcg32Work& wk, unsigned& epoch, int* s_flag) {
   __syncthreads();
+  epoch += 1u;
   if (threadIdx.x == 0) {
-    epoch += 1u;
-    __threadfence();
-    const unsigned prev = atomicAdd(&bar->count, 1u);
-    if (prev + 1u == gridDim.x * epoch) {
-      __threadfence();
-      atomicExch(&bar->gen, epoch);
-    } else {
-      unsigned long long spins = 0;
-      while (true) {
-        const unsigned g = *((volatile unsigned*)&bar->gen);
-        if (g >= epoch) break;
-        if (*((volatile int*)&bar->err)) break;
-        if (++spins > kSpinLimit32) {
-          atomicExch(&bar->err, 1);
-          break;
-        }
-        __nanosleep(32);
+    red_release_add(wk.sync + kSyncCount, 1u);
+    const unsigned target = gridDim.x * epoch;
+    int bad = 0;
+    unsigned long long spins = 0;
+    while (ld_acquire_u32(wk.sync + kSyncCount) < target) {
+      ++spins;
+      if ((spins & 63u) == 0u && *((volatile unsigned*)(wk.sync + kSyncErr))) {
+        bad = 1;
+        break;
+      }
+      if (spins > kSpinLimit32) {
+        bad = 1;
+        atomicExch(wk.sync + kSyncErr, 1u);
+        break;
       }
     }
-    __threadfence();
-    *s_flag = *((volatile int*)&bar->err);
+    *s_flag = bad;
   }
   __syncthreads();
   return *s_flag == 0;
 }
 
+// Kernel exit of every block: the last one out zeroes the barrier words.
+__device__ __forceinline__ void gbar_exit(const Pcg32Work& wk) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(wk.sync + kSyncDone, 1u);
+    if (prev + 1u == gridDim.x) {
+      atomicExch(wk.sync + kSyncCount, 0u);
+      atomicExch(wk.sync + kSyncErr, 0u);
+      atomicExch(wk.sync + kSyncDone, 0u);
+    }
+  }
+}
+
+// Transposed (reduce-scatter) butterfly over one warp. On entry every lane
+// holds C values; at each step with partner offset O a lane sends half of
+// its values to the partner and adds the partner's half to the half it
+// keeps, so after five steps the warp has moved about C values through the
+// shuffle unit instead of 5 C. With C < 32 the last steps are plain
+// butterflies on one value. The order of every addition is fixed.
+template <int C, int O>
+__device__ __forceinline__ void warp_rs(float* v, int lane) {
+  if constexpr (C >= 2) {
+    constexpr int H = C / 2;
+    const bool hi = (lane & O) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      const float send = hi ? v[i] : v[H + i];
+      const float keep = hi ? v[H + i] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+    if constexpr (O > 1) warp_rs<H, O / 2>(v, lane);
+  } else {
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
+    if constexpr (O > 1) warp_rs<1, O / 2>(v, lane);
+  }
+}
+
+// Index of the first of the max(C / 32, 1) sums lane holds after warp_rs<C, 16>.
+template <int C>
+__device__ __forceinline__ int warp_rs_first(int lane) {
+  int idx = 0, c = C;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1)
+    if (c >= 2) {
+      c >>= 1;
+      if (lane & o) idx += c;
+    }
+  return idx;
+}
+
+__host__ __device__ constexpr int pow2_at_least(int x) {
+  int p = 1;
+  while (p < x) p *= 2;
+  return p;
+}
+
 // Block-wide FP32 sum of v[0..NV) into out[0..NV) (shared), fixed order.
 template <int NV>
 __device__ __forceinline__ void block_sum_f(float (&v)[NV], float* out, float* sm) {
+  constexpr int P = pow2_at_least(NV);
+  constexpr int HOLD = P >= 32 ? P / 32 : 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float t[P];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    float x = v[k];
+  for (int k = 0; k < P; ++k) t[k] = k < NV ? v[k] : 0.f;
+  warp_rs<P, 16>(t, lane);
+  const int first = warp_rs_first<P>(lane);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) sm[warp * NV + k] = x;
-  }
+  for (int h = 0; h < HOLD; ++h)
+    if (first + h < NV) sm[warp * NV + first + h] = t[h];  // equal copies when P < 32
   __syncthreads();
   for (int k = threadIdx.x; k < NV; k += NT) {
     float x = 0.f;
@@ -76,10 +155,41 @@ __device__ __forceinline__ void block_sum_f(float (&v)[NV], float* out, float* s
   __syncthreads();
 }
 
+// Grid-wide sums of the first nv of NV block partials, stored value-major
+// (part[k * G + b]): warp w sums the values k = w, w + 8, ... with its lanes
+// striding over the blocks, then one transposed butterfly per warp.
+template <int NV>
+__device__ __forceinline__ void grid_sum_f(const float* __restrict__ part, int nv, float* out) {
+  constexpr int VPW = (NV + NT / 32 - 1) / (NT / 32);
+  constexpr int P = pow2_at_least(VPW);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = gridDim.x;
+  float t[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) t[j] = 0.f;
+#pragma unroll
+  for (int s = 0; s < kMaxGridStrides; ++s) {
+    const int b = lane + 32 * s;
+    if (b < G) {
+#pragma unroll
+      for (int j = 0; j < VPW; ++j) {
+        const int k = warp + (NT / 32) * j;
+        if (k < nv) t[j] += __ldcg(part + (size_t)k * G + b);
+      }
+    }
+  }
+  warp_rs<P, 16>(t, lane);
+  const int first = warp_rs_first<P>(lane);  // P <= 8 here: one sum per lane
+  {
+    const int k = warp + (NT / 32) * first;
+    if (first < VPW && k < nv) out[k] = t[0];
+  }
+  __syncthreads();
+}
 }  // namespace
 
 template <int RPT, bool COARSE>
-__global__ void __launch_bounds__(NT) pcg32_kernel(PcgArgsT<float> a, float4* __restrict__ ug, float* __restrict__ part) {
+__global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Work wk) {
   constexpr int NC = COARSE ? kModes * NR : 0;
   constexpr int NV0 = 4 * NR + NC;  // gamma, delta, rr, bb, Phi^T w
   constexpr int NV = 3 * NR + NC;   // gamma, delta, rr, Phi^T w
@@ -90,8 +200,14 @@ __global__ void __launch_bounds__(NT) pcg32_kernel(PcgArgsT<float> a, float4* __
   __shared__ float s_rho[NC > 0 ? NC : 1], s_sig[NC > 0 ? NC : 1], s_cc[NC > 0 ? NC : 1];
   __shared__ float s_Einv[COARSE ? kModes * kModes : 1];
   __shared__ int s_flag;
+  // the coarse basis rows of this thread, float4 q of row k at
+  // sPhi[(q * RPT + k) * NT + tid] (consecutive threads, consecutive 16 bytes)
+  extern __shared__ float4 sPhi[];
   unsigned epoch = 0;
   const int64_t n = a.n;
+  float4* __restrict__ ugx = wk.ug;      // x of the first residual
+  float4* __restrict__ ugu = wk.ug + n;  // preconditioned residual u
+  float* __restrict__ part = wk.part;
   const int64_t stride = (int64_t)gridDim.x * NT;
   const int64_t g0 = (int64_t)blockIdx.x * NT + threadIdx.x;
   const int32_t* __restrict__ rowptr = a.rowptr;
@@ -111,9 +227,18 @@ __global__ void __launch_bounds__(NT) pcg32_kernel(PcgArgsT<float> a, float4* __
     di[k] = own[k] ? __ldg(a.dinv + v) : 0.f;
 #pragma unroll
     for (int j = 0; j < NR; ++j) x[k][j] = own[k] ? a.x[v * NR + j] : 0.f;
+    if constexpr (COARSE) {
+      const float4* ph = reinterpret_cast<const float4*>(a.phi + v * kModes);
+#pragma unroll
+      for (int q = 0; q < kModes / 4; ++q)
+        sPhi[(q * RPT + k) * NT + threadIdx.x] = own[k] ? __ldg(ph + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
 
-  // y = A z for the owned rows, z read as float4 per vertex (neighbours' values)
+  // y = A z for the owned rows, z read as float4 per vertex (neighbours' values).
+  // The first kGather entries of a row are gathered at once, so a row costs
+  // one L2 round trip (a vertex of a tetrahedral grid has at most 14
+  // neighbours); longer rows finish in a plain loop.
   auto spmv = [&](const float4* __restrict__ z, float (&y)[RPT][NR]) {
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
@@ -121,26 +246,25 @@ __global__ void __launch_bounds__(NT) pcg32_kernel(PcgArgsT<float> a, float4* __
       if (!own[k]) continue;
       const int64_t v = g0 + k * stride;
       const int32_t e0 = __ldg(rowptr + v), e1 = __ldg(rowptr + v + 1);
-      int32_t e = e0;
-      for (; e + 4 <= e1; e += 4) {
-        int32_t c4[4];
-        float a4[4];
-        float4 z4[4];
+      const int cnt = e1 - e0;
+      float4 z4[kGather];
+      float a4[kGather];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          c4[t] = __ldg(col + e + t);
-          a4[t] = __ldg(val + e + t);
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) z4[t] = __ldcg(z + c4[t]);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          y[k][0] += a4[t] * z4[t].x;
-          y[k][1] += a4[t] * z4[t].y;
-          y[k][2] += a4[t] * z4[t].z;
+      for (int t = 0; t < kGather; ++t) {
+        a4[t] = 0.f;
+        z4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < cnt) {
+          a4[t] = __ldg(val + e0 + t);
+          z4[t] = __ldcg(z + __ldg(col + e0 + t));
         }
       }
-      for (; e < e1; ++e) {
+#pragma unroll
+      for (int t = 0; t < kGather; ++t) {
+        y[k][0] += a4[t] * z4[t].x;
+        y[k][1] += a4[t] * z4[t].y;
+        y[k][2] += a4[t] * z4[t].z;
+      }
+      for (int32_t e = e0 + kGather; e < e1; ++e) {
         const float av = __ldg(val + e);
         const float4 zz = __ldcg(z + __ldg(col + e));
         y[k][0] += av * zz.x;
@@ -159,13 +283,15 @@ __global__ void __launch_bounds__(NT) pcg32_kernel(PcgArgsT<float> a, float4* __
       for (int j = 0; j < NR; ++j) u[k][j] = di[k] * r[k][j];
       if constexpr (COARSE) {
 #pragma unroll
-        for (int m = 0; m < kModes; ++m) {
-          const float ph = __ldg(a.phi + v * kModes + m);
+        for (int q = 0; q < kModes / 4; ++q) {
+          const float4 ph = sPhi[(q * RPT + k) * NT + threadIdx.x];
 #pragma unroll
-          for (int j = 0; j < NR; ++j) u[k][j] += ph * s_cc[m * NR + j];
+          for (int j = 0; j < NR; ++j)
+            u[k][j] += ph.x * s_cc[(4 * q) * NR + j] + ph.y * s_cc[(4 * q + 1) * NR + j] +
+                       ph.z * s_cc[(4 * q + 2) * NR + j] + ph.w * s_cc[(4 * q + 3) * NR + j];
         }
       }
-      ug[v] = make_float4(u[k][0], u[k][1], u[k][2], 0.f);
+      ugu[v] = make_float4(u[k][0], u[k][1], u[k][2], 0.f);
     }
   };
   auto coarse_cc = [&]() {  // s_cc = E^-1 rho
@@ -181,26 +307,37 @@ __global__ void __launch_bounds__(NT) pcg32_kernel(PcgArgsT<float> a, float4* __
     }
   };
   // global sums: every block sums all block partials in the same fixed order
-  auto global_sum = [&](int nv) {
-    float v[NV0];
+  auto global_sum = [&](int nv) { grid_sum_f<NV0>(part, nv, ssum); };
+  // loc[off + m NR + j] += Phi[v][m] y[k][j] over the owned rows
+  auto phi_t = [&](const float (&y)[RPT][NR], float* loc) {
+    if constexpr (COARSE) {
 #pragma unroll
-    for (int k = 0; k < NV0; ++k) v[k] = 0.f;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += NT) {
+      for (int k = 0; k < RPT; ++k) {
+        if (!own[k]) continue;
 #pragma unroll
-      for (int k = 0; k < NV0; ++k)
-        if (k < nv) v[k] += __ldcg(part + (size_t)b * NV0 + k);
+        for (int q = 0; q < kModes / 4; ++q) {
+          const float4 ph = sPhi[(q * RPT + k) * NT + threadIdx.x];
+#pragma unroll
+          for (int j = 0; j < NR; ++j) {
+            loc[(4 * q) * NR + j] += ph.x * y[k][j];
+            loc[(4 * q + 1) * NR + j] += ph.y * y[k][j];
+            loc[(4 * q + 2) * NR + j] += ph.z * y[k][j];
+            loc[(4 * q + 3) * NR + j] += ph.w * y[k][j];
+          }
+        }
+      }
     }
-    block_sum_f<NV0>(v, ssum, sm);
   };
+  const int G = gridDim.x;
 
   // ---- r = b - A x ------------------------------------------------------
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
     const int64_t v = g0 + k * stride;
-    if (own[k]) ug[v] = make_float4(x[k][0], x[k][1], x[k][2], 0.f);
+    if (own[k]) ugx[v] = make_float4(x[k][0], x[k][1], x[k][2], 0.f);
   }
-  if (!gsync(a.bar, epoch, &s_flag)) goto timeout;
-  spmv(ug, w);
+  if (!gbar(wk, epoch, &s_flag)) goto timeout;
+  spmv(ugx, w);
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
     const int64_t v = g0 + k * stride;
@@ -211,30 +348,19 @@ __global__ void __launch_bounds__(NT) pcg32_kernel(PcgArgsT<float> a, float4* __
     float loc[NV0];
 #pragma unroll
     for (int k = 0; k < NV0; ++k) loc[k] = 0.f;
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-      if (!own[k]) continue;
-      const int64_t v = g0 + k * stride;
-#pragma unroll
-      for (int m = 0; m < kModes; ++m) {
-        const float ph = __ldg(a.phi + v * kModes + m);
-#pragma unroll
-        for (int j = 0; j < NR; ++j) loc[m * NR + j] += ph * r[k][j];
-      }
-    }
+    phi_t(r, loc);
     block_sum_f<NV0>(loc, ssum, sm);
-    for (int k = threadIdx.x; k < NC; k += NT) part[(size_t)blockIdx.x * NV0 + k] = ssum[k];
-    if (!gsync(a.bar, epoch, &s_flag)) goto timeout;
+    for (int k = threadIdx.x; k < NC; k += NT) part[(size_t)k * G + blockIdx.x] = ssum[k];
+    if (!gbar(wk, epoch, &s_flag)) goto timeout;
     global_sum(NC);
     for (int k = threadIdx.x; k < NC; k += NT) s_rho[k] = ssum[k];
     __syncthreads();
     coarse_cc();
   }
-  // ug still holds x; every block must have finished reading it
-  if (!gsync(a.bar, epoch, &s_flag)) goto timeout;
+  // u goes to its own buffer, so no block can overwrite x while it is read
   precond();
-  if (!gsync(a.bar, epoch, &s_flag)) goto timeout;
-  spmv(ug, w);
+  if (!gbar(wk, epoch, &s_flag)) goto timeout;
+  spmv(ugu, w);
   {
     float loc[NV0];
 #pragma unroll
@@ -251,19 +377,12 @@ __global__ void __launch_bounds__(NT) pcg32_kernel(PcgArgsT<float> a, float4* __
         loc[2 * NR + j] += r[k][j] * r[k][j];
         loc[3 * NR + j] += bv * bv;
       }
-      if constexpr (COARSE) {
-#pragma unroll
-        for (int m = 0; m < kModes; ++m) {
-          const float ph = __ldg(a.phi + v * kModes + m);
-#pragma unroll
-          for (int j = 0; j < NR; ++j) loc[4 * NR + m * NR + j] += ph * w[k][j];
-        }
-      }
     }
+    phi_t(w, loc + 4 * NR);
     block_sum_f<NV0>(loc, ssum, sm);
-    for (int k = threadIdx.x; k < NV0; k += NT) part[(size_t)blockIdx.x * NV0 + k] = ssum[k];
+    for (int k = threadIdx.x; k < NV0; k += NT) part[(size_t)k * G + blockIdx.x] = ssum[k];
   }
-  if (!gsync(a.bar, epoch, &s_flag)) goto timeout;
+  if (!gbar(wk, epoch, &s_flag)) goto timeout;
   global_sum(NV0);
   if (threadIdx.x < NR) {
     const int j = threadIdx.x;
@@ -312,8 +431,8 @@ __global__ void __launch_bounds__(NT) pcg32_kernel(PcgArgsT<float> a, float4* __
         coarse_cc();
       }
       precond();
-      if (!gsync(a.bar, epoch, &s_flag)) goto timeout;
-      spmv(ug, w);
+      if (!gbar(wk, epoch, &s_flag)) goto timeout;
+      spmv(ugu, w);
       {
         float loc[NV];
 #pragma unroll
@@ -327,23 +446,15 @@ __global__ void __launch_bounds__(NT) pcg32_kernel(PcgArgsT<float> a, float4* __
             loc[NR + j] += w[k][j] * u[k][j];
             loc[2 * NR + j] += r[k][j] * r[k][j];
           }
-          if constexpr (COARSE) {
-            const int64_t v = g0 + k * stride;
-#pragma unroll
-            for (int m = 0; m < kModes; ++m) {
-              const float ph = __ldg(a.phi + v * kModes + m);
-#pragma unroll
-              for (int j = 0; j < NR; ++j) loc[3 * NR + m * NR + j] += ph * w[k][j];
-            }
-          }
         }
+        phi_t(w, loc + 3 * NR);
         float lfull[NV0];
 #pragma unroll
         for (int k = 0; k < NV0; ++k) lfull[k] = k < NV ? loc[k] : 0.f;
         block_sum_f<NV0>(lfull, ssum, sm);
-        for (int k = threadIdx.x; k < NV; k += NT) part[(size_t)blockIdx.x * NV0 + k] = ssum[k];
+        for (int k = threadIdx.x; k < NV; k += NT) part[(size_t)k * G + blockIdx.x] = ssum[k];
       }
-      if (!gsync(a.bar, epoch, &s_flag)) goto timeout;
+      if (!gbar(wk, epoch, &s_flag)) goto timeout;
       global_sum(NV);
       if (threadIdx.x < NR) {
         const int j = threadIdx.x;
@@ -398,17 +509,34 @@ __global__ void __launch_bounds__(NT) pcg32_kernel(PcgArgsT<float> a, float4* __
         for (int j = 0; j < NR; ++j) a.relres_out[j] = s_bb[j] > 0.f ? sqrt((double)s_rr[j] / s_bb[j]) : 0.0;
     }
   }
+  gbar_exit(wk);
   return;
 timeout:
   if (threadIdx.x == 0 && a.timeout_out) atomicExch(a.timeout_out, 1);
+  gbar_exit(wk);
 }
 
 namespace {
 template <int RPT, bool C>
-cudaError_t launch32(const PcgArgsT<float>& args, float4* ug, float* part, int grid, cudaStream_t st) {
+cudaError_t launch32(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, cudaStream_t st) {
+  // the coarse rows live in dynamic shared memory (RPT x 16 KB); above the
+  // default 48 KB the kernel needs the opt-in, a per-device attribute
+  const size_t smem = C ? sizeof(float4) * (kModes / 4) * RPT * NT : 0;
+  if (smem > 48 * 1024) {
+    static bool set[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !set[dev]) {
+      e = cudaFuncSetAttribute(pcg32_kernel<RPT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      set[dev] = true;
+    }
+  }
   PcgArgsT<float> a = args;
-  void* params[] = {(void*)&a, (void*)&ug, (void*)&part};
-  return cudaLaunchCooperativeKernel((const void*)pcg32_kernel<RPT, C>, dim3(grid), dim3(NT), params, 0, st);
+  Pcg32Work w = work;
+  void* params[] = {(void*)&a, (void*)&w};
+  return cudaLaunchCooperativeKernel((const void*)pcg32_kernel<RPT, C>, dim3(grid), dim3(NT), params, smem, st);
 }
 }  // namespace
 
@@ -416,6 +544,7 @@ cudaError_t launch32(const PcgArgsT<float>& args, float4* ug, float* part, int g
 bool pcg32_shape(int64_t n, int sms, int* grid, int* rpt) {
   int64_t nb = (n + 2 * NT - 1) / (2 * NT);
   if (nb > sms) nb = sms;
+  if (nb > 32 * kMaxGridStrides) nb = 32 * kMaxGridStrides;
   if (nb < 1) nb = 1;
   int r = 1;
   while ((int64_t)nb * NT * r < n) r *= 2;
@@ -425,15 +554,14 @@ bool pcg32_shape(int64_t n, int sms, int* grid, int* rpt) {
   return true;
 }
 
-cudaError_t launch_pcg32(const PcgArgsT<float>& args, float4* ug, float* part, int grid, int rpt, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(args.bar, 0, sizeof(GridBarrier), st);
-  if (e != cudaSuccess) return e;
+cudaError_t launch_pcg32(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, int rpt, cudaStream_t st) {
+  if (grid > 32 * kMaxGridStrides) return cudaErrorInvalidValue;
   const bool c = args.phi && args.Einv;
   switch (rpt) {
-    case 1: return c ? launch32<1, true>(args, ug, part, grid, st) : launch32<1, false>(args, ug, part, grid, st);
-    case 2: return c ? launch32<2, true>(args, ug, part, grid, st) : launch32<2, false>(args, ug, part, grid, st);
-    case 4: return c ? launch32<4, true>(args, ug, part, grid, st) : launch32<4, false>(args, ug, part, grid, st);
-    case 8: return c ? launch32<8, true>(args, ug, part, grid, st) : launch32<8, false>(args, ug, part, grid, st);
+    case 1: return c ? launch32<1, true>(args, work, grid, st) : launch32<1, false>(args, work, grid, st);
+    case 2: return c ? launch32<2, true>(args, work, grid, st) : launch32<2, false>(args, work, grid, st);
+    case 4: return c ? launch32<4, true>(args, work, grid, st) : launch32<4, false>(args, work, grid, st);
+    case 8: return c ? launch32<8, true>(args, work, grid, st) : launch32<8, false>(args, work, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }
