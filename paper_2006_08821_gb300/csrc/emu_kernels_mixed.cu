@@ -105,7 +105,7 @@ __device__ __forceinline__ void corners_f(double* __restrict__ contrib, int64_t 
 }
 
 // ------------------------------------------------------------ gradient ----
-__global__ void __launch_bounds__(128) k_grad_m(MixArgs a) {
+__global__ void __launch_bounds__(128, 4) k_grad_m(MixArgs a) {
   const int64_t m = a.m;
   double acc[1] = {0.0};
   int bad = 0;
@@ -284,6 +284,11 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 __device__ __forceinline__ void cp_async4(uint32_t saddr, const float* g, bool ok) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(saddr), "l"(g), "r"(ok ? 4 : 0) : "memory");
 }
+// 16-byte copy of which the first ``bytes`` (0, 4, 8, 12 or 16) come from
+// global memory and the rest is zero-filled
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const float* g, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
@@ -291,13 +296,15 @@ constexpr int kTcCH = 32;              // tets per chunk
 constexpr int kTcKR = kTcCH * 6;       // 192 rows of Yh per chunk: 24 k-steps of 8, 3 per warp
 constexpr int kTcLD = kK + 4;          // padded row of Yh (TF32 bits)
 constexpr int kTcRawRows = 54 + 48 + 9 + 1;  // U, gamma, y, w of a chunk
-constexpr int kTcRL = kTcCH + 1;             // padded raw row
+constexpr int kTcRL = kTcCH + 8;             // padded raw row (16-byte rows, conflict-free reads)
 constexpr size_t kTcYBytes = sizeof(uint32_t) * kTcKR * kTcLD;
 constexpr size_t kTcRawBytes = sizeof(float) * kTcRawRows * kTcRL;
 constexpr size_t kTcSmem = kTcYBytes + 2 * kTcRawBytes;
 
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_syrk_tc(MixArgs a, double* __restrict__ cpart) {
   constexpr int CH = kTcCH, LD = kTcLD, RL = kTcRL;
+  __shared__ const float* s_src[kTcRawRows];  // first element of each raw row
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint32_t* sY = reinterpret_cast<uint32_t*>(smem_raw);
   float* sRaw = reinterpret_cast<float*>(smem_raw + kTcYBytes);
@@ -307,26 +314,36 @@ __global__ void __launch_bounds__(256) k_syrk_tc(MixArgs a, double* __restrict__
   const int gid = lane >> 2, tig = lane & 3;
   const int64_t m = a.m;
   const int64_t nch = (m + CH - 1) / CH;
+  if (tid < kTcRawRows) {
+    const int row = tid;
+    s_src[row] = row < 54 ? a.Uw + (int64_t)row * m
+                 : row < 102 ? a.gam + (int64_t)(row - 54) * m
+                 : row < 111 ? a.y + (int64_t)(row - 102) * m
+                             : a.w;
+  }
+  __syncthreads();
 
-  // cp.async of one chunk's raw rows: element e = row * 32 + tet
+  // cp.async of one chunk's raw rows. VEC (rows 16-byte aligned, m % 4 == 0):
+  // 8 copies of 16 bytes per row; otherwise 32 copies of 4 bytes.
   auto issue = [&](int64_t ch, int buf) {
     const int64_t base = ch * CH;
     float* dst = sRaw + buf * (kTcRawRows * RL);
-    for (int e = tid; e < kTcRawRows * CH; e += 256) {
-      const int row = e >> 5, tt = e & 31;
-      const int64_t i = base + tt;
-      const bool ok = i < m;
-      const int64_t ic = ok ? i : 0;
-      const float* src;
-      if (row < 54)
-        src = a.Uw + (int64_t)row * m + ic;
-      else if (row < 102)
-        src = a.gam + (int64_t)(row - 54) * m + ic;
-      else if (row < 111)
-        src = a.y + (int64_t)(row - 102) * m + ic;
-      else
-        src = a.w + ic;
-      cp_async4((uint32_t)__cvta_generic_to_shared(dst + row * RL + tt), src, ok);
+    if constexpr (VEC) {
+      for (int e = tid; e < kTcRawRows * 8; e += 256) {
+        const int row = e >> 3, seg = e & 7;
+        const int64_t i = base + 4 * seg;
+        const int64_t left = m - i;
+        const int bytes = left >= 4 ? 16 : left > 0 ? 4 * (int)left : 0;
+        const float* src = s_src[row] + (bytes > 0 ? i : 0);
+        cp_async16((uint32_t)__cvta_generic_to_shared(dst + row * RL + 4 * seg), src, bytes);
+      }
+    } else {
+      for (int e = tid; e < kTcRawRows * CH; e += 256) {
+        const int row = e >> 5, tt = e & 31;
+        const int64_t i = base + tt;
+        const bool ok = i < m;
+        cp_async4((uint32_t)__cvta_generic_to_shared(dst + row * RL + tt), s_src[row] + (ok ? i : 0), ok);
+      }
     }
   };
 
@@ -440,19 +457,23 @@ __global__ void __launch_bounds__(256) k_syrk_tc(MixArgs a, double* __restrict__
 }
 
 void launch_syrk_tc(const MixArgs& a, int grid, double* cpart, cudaStream_t st) {
-  // the opt-in shared-memory size is a per-device property of the kernel
+  // the opt-in shared-memory size is a per-device property of each kernel
   static bool attr_set[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    cudaFuncSetAttribute(k_syrk_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    cudaFuncSetAttribute(k_syrk_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     attr_set[dev] = true;
   }
-  k_syrk_tc<<<grid, 256, kTcSmem, st>>>(a, cpart);
+  if (a.m % 4 == 0)
+    k_syrk_tc<true><<<grid, 256, kTcSmem, st>>>(a, cpart);
+  else
+    k_syrk_tc<false><<<grid, 256, kTcSmem, st>>>(a, cpart);
 }
 
 // ------------------------------------------------------------ direction ---
-__global__ void __launch_bounds__(128) k_dir_m(MixArgs a) {
+__global__ void __launch_bounds__(128, 4) k_dir_m(MixArgs a) {
   __shared__ float sz[kK];
   if (threadIdx.x < kK) sz[threadIdx.x] = (float)a.z[threadIdx.x];
   __syncthreads();

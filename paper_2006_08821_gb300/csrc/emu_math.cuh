@@ -217,22 +217,28 @@ template <typename T> EMU_HD void stretch_gradient(const T* S, const T* Sinv, T 
 // In-place lower Cholesky of an N x N SPD matrix (row-major full storage).
 // Returns false if a pivot is not positive.
 template <typename T, int N> EMU_HD bool chol(T* A) {
+  // every loop has a fixed trip count (bounds as conditions), so full
+  // unrolling folds all indices and A stays in registers
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < N; ++j) {
     T d = A[N * j + j];
 #pragma unroll
-    for (int k = 0; k < j; ++k) d -= A[N * j + k] * A[N * j + k];
-    ok = ok && (d > T(0));
+    for (int k = 0; k < N; ++k)
+      if (k < j) d -= A[N * j + k] * A[N * j + k];
+    ok = ok & (d > T(0));
     d = d > T(0) ? sqrt(d) : T(1);
     A[N * j + j] = d;
     T id = T(1) / d;
 #pragma unroll
-    for (int i = j + 1; i < N; ++i) {
-      T v = A[N * i + j];
+    for (int i = 0; i < N; ++i) {
+      if (i > j) {
+        T v = A[N * i + j];
 #pragma unroll
-      for (int k = 0; k < j; ++k) v -= A[N * i + k] * A[N * j + k];
-      A[N * i + j] = v * id;
+        for (int k = 0; k < N; ++k)
+          if (k < j) v -= A[N * i + k] * A[N * j + k];
+        A[N * i + j] = v * id;
+      }
     }
   }
   return ok;
@@ -277,40 +283,37 @@ template <typename T> EMU_HD void chart_factor(const T* R, const T* S, const T* 
     Km[8] += tr;
     inv3(Km, Kinv);
   }
-  T Zr[6 * 9];
+  // Y = e_a e_b^T has k = 0 when a = b and k = +-e_c otherwise, so w is
+  // +-column c of Kinv; the three [w]x S are formed once (their stretch
+  // coordinates ws[c]) and each column of Zr is s(sym Y) -+ ws[c].
+  T ws[3][6];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
+  for (int c = 0; c < 3; ++c) {
+    const T w0 = Kinv[c], w1 = Kinv[3 + c], w2 = Kinv[6 + c];
+    // [w]x S ; [w]x = [[0,-w2,w1],[w2,0,-w0],[-w1,w0,0]]
+    T Wm[9];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      // Y = e_a e_b^T ; k = (Y21 - Y12, Y02 - Y20, Y10 - Y01)
-      T k[3] = {T(0), T(0), T(0)};
-      if (a == 2 && b == 1) k[0] += T(1);
-      if (a == 1 && b == 2) k[0] -= T(1);
-      if (a == 0 && b == 2) k[1] += T(1);
-      if (a == 2 && b == 0) k[1] -= T(1);
-      if (a == 1 && b == 0) k[2] += T(1);
-      if (a == 0 && b == 1) k[2] -= T(1);
-      T w[3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) w[r] = Kinv[3 * r] * k[0] + Kinv[3 * r + 1] * k[1] + Kinv[3 * r + 2] * k[2];
-      // W = [w]x S ; [w]x = [[0,-w2,w1],[w2,0,-w0],[-w1,w0,0]]
-      T Wm[9];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        Wm[c] = -w[2] * S[3 + c] + w[1] * S[6 + c];
-        Wm[3 + c] = w[2] * S[c] - w[0] * S[6 + c];
-        Wm[6 + c] = -w[1] * S[c] + w[0] * S[3 + c];
-      }
-      // dS = sym(Y) - sym(W)
-      T D[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) D[i] = -Wm[i];
-      D[3 * a + b] += T(1);
-      T sv[6];
-      s_from_mat(D, sv);
-#pragma unroll
-      for (int kk = 0; kk < 6; ++kk) Zr[9 * kk + 3 * a + b] = sv[kk];
+    for (int cc = 0; cc < 3; ++cc) {
+      Wm[cc] = -w2 * S[3 + cc] + w1 * S[6 + cc];
+      Wm[3 + cc] = w2 * S[cc] - w0 * S[6 + cc];
+      Wm[6 + cc] = -w1 * S[cc] + w0 * S[3 + cc];
     }
+    s_from_mat(Wm, ws[c]);
+  }
+  const T h = rsqrt2<T>();
+  T Zr[6 * 9];  // column 3a + b
+#pragma unroll
+  for (int kk = 0; kk < 6; ++kk) {
+    const T z0 = ws[0][kk], z1 = ws[1][kk], z2 = ws[2][kk];
+    Zr[9 * kk + 0] = kk == 0 ? T(1) : T(0);  // (0,0)
+    Zr[9 * kk + 4] = kk == 1 ? T(1) : T(0);  // (1,1)
+    Zr[9 * kk + 8] = kk == 2 ? T(1) : T(0);  // (2,2)
+    Zr[9 * kk + 1] = (kk == 5 ? h : T(0)) + z2;  // (0,1): k = -e_2
+    Zr[9 * kk + 3] = (kk == 5 ? h : T(0)) - z2;  // (1,0): k = +e_2
+    Zr[9 * kk + 2] = (kk == 4 ? h : T(0)) - z1;  // (0,2): k = +e_1
+    Zr[9 * kk + 6] = (kk == 4 ? h : T(0)) + z1;  // (2,0): k = -e_1
+    Zr[9 * kk + 5] = (kk == 3 ? h : T(0)) + z0;  // (1,2): k = -e_0
+    Zr[9 * kk + 7] = (kk == 3 ? h : T(0)) - z0;  // (2,1): k = +e_0
   }
   // L_M = chol(M)
   T LM[36];
