@@ -191,6 +191,79 @@ int emu_set_activation_device(emu_handle* h, const double* a_device, int64_t cou
  * reached; the state is then kept. */
 int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats);
 
+/* Solves ``count`` independent meshes (the c3 batch: Algorithm 1 per mesh,
+ * each from its own resident state and activation). Every handle's work is
+ * enqueued on its own stream; the host interleaves the handles' Newton
+ * loops (each waits for its device results without blocking the others),
+ * so meshes given distinct streams overlap on the device. The result of
+ * each mesh is the one emu_solve_quasistatic would give it.
+ *   hs      ``count`` distinct handles (host array, caller-owned).
+ *   stats   NULL or ``count`` entries, filled per handle (status included).
+ * Returns EMU_OK when every solve succeeded, else the first failing status
+ * in handle order (the others still ran to completion). Not thread-safe
+ * with other calls on the same handles. */
+int emu_batch_solve(emu_handle* const* hs, int32_t count, emu_solve_stats* stats);
+
+/* Upper bound of the device memory (bytes) that emu_create allocates for
+ * this mesh and these parameters (the Laplacian is bounded by 16 entries per
+ * tet). Validates like emu_create; needs a current CUDA device. Used by the
+ * server's admission control. */
+int emu_required_bytes(const emu_mesh_desc* desc, const emu_params* params, size_t* bytes);
+
+/* ---------------------------------------------------------------- serving
+ * A persistent request loop on the current device (the c4 stream): each
+ * request is one mesh and n_frames activation vectors, solved frame by frame
+ * from its own resident state (warm starts). A worker thread admits queued
+ * requests in arrival order while their device memory (emu_required_bytes)
+ * fits in the budget and fewer than 32 are active, builds each on its own
+ * stream, and interleaves the active requests' Newton loops so that their
+ * work overlaps on the device (continuous batching: a request that arrives
+ * while others run is admitted as soon as memory and a slot free up). A
+ * request's memory is released when its last frame is done. The result of a
+ * request does not depend on what else is in flight (every kernel is
+ * deterministic and touches only its own handle's memory).
+ * Submit, poll and result may be called from any thread. */
+typedef struct emu_server emu_server;
+
+typedef struct {
+  uint64_t id;
+  int32_t status;         /* EMU_OK, or the status of the frame that failed */
+  int32_t frames_done;    /* frames solved (all of them when status is OK)  */
+  int32_t newton_iters;   /* summed over frames                            */
+  int32_t pcg_iters;      /* summed over frames                            */
+  double rel_residual;    /* of the last frame solved                      */
+  double queue_ms;        /* submit -> admitted                            */
+  double setup_ms;        /* emu_create of the request                     */
+  double solve_ms;        /* frames, after setup                           */
+  double latency_ms;      /* submit -> last frame done (host clock)        */
+  uint64_t device_bytes;  /* memory reserved against the budget            */
+} emu_request_stats;
+
+/* Starts the worker thread. budget_bytes: device memory the active
+ * requests may hold in total. params: NULL for defaults (copied). alloc:
+ * NULL for cudaMalloc (the worker thread calls it). */
+int emu_server_create(size_t budget_bytes, const emu_params* params, const emu_allocator* alloc,
+                      emu_server** out);
+
+/* Queues a request. The mesh arrays and activations (n_frames x n_tets,
+ * row-major, each finite and >= 0) are copied; request_id must not be in
+ * use. EMU_ERR_OOM if the mesh alone exceeds the budget. */
+int emu_server_submit(emu_server* srv, const emu_mesh_desc* mesh, const double* activations, int32_t n_frames,
+                      uint64_t request_id);
+
+/* Writes up to cap ids of finished requests not reported before. */
+int emu_server_poll(emu_server* srv, uint64_t* done_ids, int32_t cap, int32_t* n_done);
+
+/* Copies a finished request's positions (n_frames x n_verts x 3 float64,
+ * the converged q of every frame; NULL to skip) and stats (NULL to skip),
+ * then forgets the request. EMU_ERR_INVALID_ARG if the id is unknown or
+ * not finished. */
+int emu_server_result(emu_server* srv, uint64_t request_id, double* positions, emu_request_stats* stats);
+
+/* Stops the worker: device work already enqueued is waited for, requests
+ * not finished are dropped, and everything is freed. */
+int emu_server_destroy(emu_server* srv);
+
 /* Copies q (n_verts x 3 float64, row-major) to ``out``: a host pointer when
  * out_is_device == 0, a device pointer otherwise. */
 int emu_get_positions(emu_handle* h, double* out, int32_t out_is_device);

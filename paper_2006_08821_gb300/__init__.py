@@ -9,7 +9,11 @@ from .binding import (  # noqa: F401
     LIB_PATH,
     EmuError,
     Params,
+    Server,
     Solver,
+    batch_solve,
+    mesh_desc,
+    required_bytes,
     TorchAllocator,
     default_params,
     eval_polar,

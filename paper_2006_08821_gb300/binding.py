@@ -37,7 +37,8 @@ EXPORTED = [
     "emu_set_activation", "emu_set_activation_device", "emu_solve_quasistatic", "emu_get_positions",
     "emu_get_element_state", "emu_set_element_state", "emu_reset", "emu_get_sizes",
     "emu_eval_stretch_terms", "emu_eval_polar", "emu_set_profiling", "emu_get_profile",
-    "emu_acap_solve_noalloc",
+    "emu_acap_solve_noalloc", "emu_batch_solve", "emu_required_bytes", "emu_server_create",
+    "emu_server_submit", "emu_server_poll", "emu_server_result", "emu_server_destroy",
 ]
 
 PHASES = ["rhs", "assemble", "pcg", "grad", "syrk", "small", "dir", "ls", "update"]
@@ -108,6 +109,22 @@ class emu_solve_stats(C.Structure):
     ]
 
 
+class emu_request_stats(C.Structure):
+    _fields_ = [
+        ("id", C.c_uint64),
+        ("status", C.c_int32),
+        ("frames_done", C.c_int32),
+        ("newton_iters", C.c_int32),
+        ("pcg_iters", C.c_int32),
+        ("rel_residual", C.c_double),
+        ("queue_ms", C.c_double),
+        ("setup_ms", C.c_double),
+        ("solve_ms", C.c_double),
+        ("latency_ms", C.c_double),
+        ("device_bytes", C.c_uint64),
+    ]
+
+
 _lib = None
 
 
@@ -143,6 +160,13 @@ def load_library(path: str = LIB_PATH):
     lib.emu_set_profiling.argtypes = [C.c_void_p, C.c_int32]
     lib.emu_acap_solve_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.emu_get_profile.argtypes = [C.c_void_p, P(C.c_double), P(C.c_int32), C.c_int32, P(C.c_int64)]
+    lib.emu_batch_solve.argtypes = [P(C.c_void_p), C.c_int32, P(emu_solve_stats)]
+    lib.emu_required_bytes.argtypes = [P(emu_mesh_desc), P(emu_params), P(C.c_size_t)]
+    lib.emu_server_create.argtypes = [C.c_size_t, P(emu_params), P(emu_allocator), P(C.c_void_p)]
+    lib.emu_server_submit.argtypes = [C.c_void_p, P(emu_mesh_desc), P(C.c_double), C.c_int32, C.c_uint64]
+    lib.emu_server_poll.argtypes = [C.c_void_p, P(C.c_uint64), C.c_int32, P(C.c_int32)]
+    lib.emu_server_result.argtypes = [C.c_void_p, C.c_uint64, P(C.c_double), P(emu_request_stats)]
+    lib.emu_server_destroy.argtypes = [C.c_void_p]
     for name in EXPORTED:
         if name not in ("emu_default_params", "emu_status_string", "emu_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -221,35 +245,40 @@ class TorchAllocator:
         self.struct = emu_allocator(None, self._af, self._ff)
 
 
+def mesh_desc(mesh):
+    """emu_mesh_desc of a mesh (emu_inputs.MeshSpec-like) and the arrays it
+    points into (keep them alive while the descriptor is used)."""
+    Q = np.ascontiguousarray(mesh.rest_pos, dtype=np.float64)
+    T = np.ascontiguousarray(mesh.tets, dtype=np.int32)
+    E = np.ascontiguousarray(mesh.youngs, dtype=np.float64)
+    nu = np.ascontiguousarray(mesh.poisson, dtype=np.float64)
+    mid = np.ascontiguousarray(mesh.material_id, dtype=np.uint8)
+    fib = None if mesh.fiber_dir is None else np.ascontiguousarray(mesh.fiber_dir, dtype=np.float64)
+    fx = np.ascontiguousarray(mesh.fixed_verts, dtype=np.int32)
+    fp = None if getattr(mesh, "fixed_pos", None) is None else np.ascontiguousarray(mesh.fixed_pos, dtype=np.float64)
+    d = emu_mesh_desc()
+    d.n_verts = Q.shape[0]
+    d.n_tets = T.shape[0]
+    d.rest_pos = _dptr(Q, C.c_double)
+    d.tets = _dptr(T, C.c_int32)
+    d.n_materials = E.shape[0]
+    d.youngs = _dptr(E, C.c_double)
+    d.poisson = _dptr(nu, C.c_double)
+    d.material_id = _dptr(mid, C.c_uint8)
+    d.fiber_dir = _dptr(fib, C.c_double) if fib is not None else None
+    d.n_fixed = fx.shape[0]
+    d.fixed_verts = _dptr(fx, C.c_int32)
+    d.fixed_pos = _dptr(fp, C.c_double) if fp is not None else None
+    return d, [Q, T, E, nu, mid, fib, fx, fp]
+
+
 class Solver:
     """One mesh resident on the GPU (wraps emu_create ... emu_destroy)."""
 
     def __init__(self, mesh, params: Params | None = None, stream=None, allocator=None):
         self.lib = load_library()
         self.params = params or Params()
-        self._keep = []
-        Q = np.ascontiguousarray(mesh.rest_pos, dtype=np.float64)
-        T = np.ascontiguousarray(mesh.tets, dtype=np.int32)
-        E = np.ascontiguousarray(mesh.youngs, dtype=np.float64)
-        nu = np.ascontiguousarray(mesh.poisson, dtype=np.float64)
-        mid = np.ascontiguousarray(mesh.material_id, dtype=np.uint8)
-        fib = None if mesh.fiber_dir is None else np.ascontiguousarray(mesh.fiber_dir, dtype=np.float64)
-        fx = np.ascontiguousarray(mesh.fixed_verts, dtype=np.int32)
-        fp = None if getattr(mesh, "fixed_pos", None) is None else np.ascontiguousarray(mesh.fixed_pos, dtype=np.float64)
-        self._keep += [Q, T, E, nu, mid, fib, fx, fp]
-        d = emu_mesh_desc()
-        d.n_verts = Q.shape[0]
-        d.n_tets = T.shape[0]
-        d.rest_pos = _dptr(Q, C.c_double)
-        d.tets = _dptr(T, C.c_int32)
-        d.n_materials = E.shape[0]
-        d.youngs = _dptr(E, C.c_double)
-        d.poisson = _dptr(nu, C.c_double)
-        d.material_id = _dptr(mid, C.c_uint8)
-        d.fiber_dir = _dptr(fib, C.c_double) if fib is not None else None
-        d.n_fixed = fx.shape[0]
-        d.fixed_verts = _dptr(fx, C.c_int32)
-        d.fixed_pos = _dptr(fp, C.c_double) if fp is not None else None
+        d, self._keep = mesh_desc(mesh)
         self.n_verts = int(d.n_verts)
         self.n_tets = int(d.n_tets)
         self.stream = stream
@@ -335,6 +364,80 @@ class Solver:
         k = C.c_int32()
         _check(self.lib.emu_get_sizes(self.handle, C.byref(n), C.byref(m), C.byref(k)), self.lib)
         return n.value, m.value, k.value
+
+
+def batch_solve(solvers, raise_on_error=True):
+    """emu_batch_solve over ``solvers`` (distinct Solver objects): one
+    quasi-static solve each, interleaved on their streams. Returns the list
+    of per-solver stats (``status`` set on each)."""
+    solvers = list(solvers)
+    lib = load_library()
+    n = len(solvers)
+    hs = (C.c_void_p * max(n, 1))(*[s.handle for s in solvers])
+    st = (emu_solve_stats * max(n, 1))()
+    rc = lib.emu_batch_solve(hs, n, st)
+    if raise_on_error and rc != EMU_OK:
+        _check(rc, lib)
+    return [st[i] for i in range(n)]
+
+
+def required_bytes(mesh, params: Params | None = None) -> int:
+    """emu_required_bytes: device memory bound of a mesh (needs a GPU)."""
+    lib = load_library()
+    d, keep = mesh_desc(mesh)
+    cp = (params or Params()).to_c()
+    out = C.c_size_t()
+    _check(lib.emu_required_bytes(C.byref(d), C.byref(cp), C.byref(out)), lib)
+    return int(out.value)
+
+
+class Server:
+    """emu_server_*: persistent request loop with a device-memory budget."""
+
+    def __init__(self, budget_bytes: int, params: Params | None = None):
+        self.lib = load_library()
+        self.params = params or Params()
+        cp = self.params.to_c()
+        h = C.c_void_p()
+        _check(self.lib.emu_server_create(C.c_size_t(int(budget_bytes)), C.byref(cp), None, C.byref(h)), self.lib)
+        self.handle = h
+        self._shape = {}
+
+    def submit(self, mesh, activations, request_id: int):
+        """activations: (frames, n_tets) float64 (a 1-D array is one frame)."""
+        d, keep = mesh_desc(mesh)
+        a = np.ascontiguousarray(np.atleast_2d(np.asarray(activations, dtype=np.float64)))
+        if a.shape[1] != d.n_tets:
+            raise ValueError("activations must have n_tets columns")
+        _check(self.lib.emu_server_submit(self.handle, C.byref(d), _dptr(a, C.c_double), a.shape[0],
+                                          C.c_uint64(int(request_id))), self.lib)
+        self._shape[int(request_id)] = (a.shape[0], int(d.n_verts))
+
+    def poll(self, cap: int = 256):
+        ids = (C.c_uint64 * cap)()
+        n = C.c_int32()
+        _check(self.lib.emu_server_poll(self.handle, ids, cap, C.byref(n)), self.lib)
+        return [int(ids[k]) for k in range(n.value)]
+
+    def result(self, request_id: int):
+        """(positions (frames, n_verts, 3), emu_request_stats) of a finished request."""
+        frames, n = self._shape.pop(int(request_id))
+        pos = np.empty((frames, n, 3), dtype=np.float64)
+        st = emu_request_stats()
+        _check(self.lib.emu_server_result(self.handle, C.c_uint64(int(request_id)), _dptr(pos, C.c_double),
+                                          C.byref(st)), self.lib)
+        return pos, st
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.emu_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def eval_stretch_terms(s_dev, params_dev, n, mixed, psi_dev, grad_dev, hess_dev, stream=0):

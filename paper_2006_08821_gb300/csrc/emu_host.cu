@@ -9,6 +9,7 @@
 #include <cmath>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "emu_internal.h"
@@ -98,6 +99,8 @@ struct emu_handle {
   double* small = nullptr;      // 256 doubles of small-matrix exchange
   DevScalars* sc = nullptr;
   DevScalars* sc_host = nullptr;  // pinned
+  double* o6_host = nullptr;       // pinned: residual sums of the refresh rounds
+  cudaEvent_t wait_ev = nullptr;   // marks the work a solve task waits for
   GridBarrier* bar = nullptr;
   // Laplacian and pins
   int32_t *rowptr = nullptr, *col = nullptr;
@@ -161,9 +164,15 @@ struct emu_handle {
     ev_pool.clear();
   }
 
+  bool dry = false;       // count bytes only (memory estimate)
+  size_t dry_bytes = 0;
   void* dalloc(size_t bytes) {
     if (bytes == 0) bytes = 256;
     bytes = (bytes + 255) & ~size_t(255);
+    if (dry) {
+      dry_bytes += bytes;
+      return reinterpret_cast<void*>(uintptr_t(256));
+    }
     void* p = nullptr;
     if (has_alloc) {
       p = alloc.alloc(alloc.ctx, bytes, (void*)st);
@@ -189,6 +198,10 @@ struct emu_handle {
     bufs.clear();
     if (sc_host) cudaFreeHost(sc_host);
     sc_host = nullptr;
+    if (o6_host) cudaFreeHost(o6_host);
+    o6_host = nullptr;
+    if (wait_ev) cudaEventDestroy(wait_ev);
+    wait_ev = nullptr;
   }
 
   template <typename TW> TetArgs<TW> args();
@@ -449,7 +462,14 @@ cudaError_t run_pcg32(emu_handle* h, const float* rhs, float* x, double tol) {
 // from the current q, to relative residual ``tol``. FP64 path: FP64 CG.
 // Mixed path: iterative refinement, the residual b - K q in FP64 and the
 // correction from an FP32 CG, until the FP64 residual meets ``tol``.
-int refresh_q(emu_handle* h, double tol) {
+//
+// The steps are enqueued separately so that a solve can wait for the
+// residual without blocking the host: refresh_begin (FP64 path: the whole
+// solve; mixed: the right-hand side), then rounds of refresh_residual (sums
+// into o6_host), refresh_converged and refresh_correction.
+constexpr int kRefreshRounds = 8;
+
+int refresh_begin(emu_handle* h, double tol) {
   if (!h->mixed) {
     TetArgs<double> a = h->args<double>();
     h->ph_begin();
@@ -472,23 +492,45 @@ int refresh_q(emu_handle* h, double tol) {
   launch_assemble(h->n, h->slot_ptr, h->slot_idx, h->contrib, h->bfix, h->is_fixed, h->qfix, 0, h->b, h->st);
   h->ph_end(EMU_PHASE_ASSEMBLE, 1);
   EMU_CK(cudaGetLastError());
+  return EMU_OK;
+}
+
+int refresh_residual(emu_handle* h) {
   const int rgrid = (int)std::min<int64_t>(std::max<int64_t>(1, (h->n + 255) / 256), 2 * (int64_t)h->sms);
-  for (int round = 0; round < 8; ++round) {
-    h->ph_begin();
-    EMU_CK(launch_residual64(h->n, h->rowptr, h->col, h->val, h->b, h->q, h->r32, h->part_pcg, rgrid, h->small, h->st));
-    h->ph_end(EMU_PHASE_PCG, 2);
-    double o6[6];
-    EMU_CK(cudaMemcpyAsync(o6, h->small, sizeof(o6), cudaMemcpyDeviceToHost, h->st));
-    int rc = read_scalars(h);
+  h->ph_begin();
+  EMU_CK(launch_residual64(h->n, h->rowptr, h->col, h->val, h->b, h->q, h->r32, h->part_pcg, rgrid, h->small, h->st));
+  h->ph_end(EMU_PHASE_PCG, 2);
+  EMU_CK(cudaMemcpyAsync(h->o6_host, h->small, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  return EMU_OK;
+}
+
+// valid once the copy of refresh_residual has completed
+bool refresh_converged(const emu_handle* h, double tol) {
+  bool done = true;
+  for (int j = 0; j < 3; ++j) done = done && (h->o6_host[j] <= tol * tol * h->o6_host[3 + j]);
+  return done;
+}
+
+int refresh_correction(emu_handle* h) {
+  EMU_CK(cudaMemsetAsync(h->e32, 0, 12 * h->n, h->st));
+  h->ph_begin();
+  EMU_CK(run_pcg32(h, h->r32, h->e32, 1e-5));
+  EMU_CK(launch_axpy_f2d(3 * h->n, h->e32, h->q, h->st));
+  h->ph_end(EMU_PHASE_PCG, 2);
+  return EMU_OK;
+}
+
+int refresh_q(emu_handle* h, double tol) {
+  int rc = refresh_begin(h, tol);
+  if (rc || !h->mixed) return rc;
+  for (int round = 0; round < kRefreshRounds; ++round) {
+    rc = refresh_residual(h);
     if (rc) return rc;
-    bool done = true;
-    for (int j = 0; j < 3; ++j) done = done && (o6[j] <= tol * tol * o6[3 + j]);
-    if (done) break;
-    EMU_CK(cudaMemsetAsync(h->e32, 0, 12 * h->n, h->st));
-    h->ph_begin();
-    EMU_CK(run_pcg32(h, h->r32, h->e32, 1e-5));
-    EMU_CK(launch_axpy_f2d(3 * h->n, h->e32, h->q, h->st));
-    h->ph_end(EMU_PHASE_PCG, 2);
+    EMU_CK(cudaStreamSynchronize(h->st));
+    h->prof_flush();
+    if (refresh_converged(h, tol)) break;
+    rc = refresh_correction(h);
+    if (rc) return rc;
   }
   return EMU_OK;
 }
@@ -633,6 +675,49 @@ int build_modes(emu_handle* h) {
   EMU_CK(cudaStreamSynchronize(h->st));
   h->coarse_ready = emax > 0.0;
   return EMU_OK;
+}
+
+// Every device buffer of a handle (n, m, mixed and sms set). In dry mode
+// (h->dry) nothing is allocated and h->dry_bytes receives the total.
+bool alloc_device(emu_handle* h, int64_t nnz) {
+  const int64_t n = h->n, m = h->m;
+  bool ok = true;
+  ok = ok && h->get(h->tet, m) && h->get(h->Dinv, 9 * m) && h->get(h->V, m) && h->get(h->c, m) && h->get(h->w, m) &&
+       h->get(h->mu, m) && h->get(h->lam, m) && h->get(h->u, 3 * m) && h->get(h->ka, m);
+  ok = ok && h->get(h->R, 9 * m) && h->get(h->s, 6 * m) && h->get(h->q, 3 * n) && h->get(h->dq, 3 * n) &&
+       h->get(h->q0, 3 * n) && h->get(h->g, 9 * m) && h->get(h->contrib, 12 * m) && h->get(h->b, 16 * n);
+  if (h->mixed) {
+    ok = ok && h->get(h->gam32, 48 * m) && h->get(h->y32, 9 * m) && h->get(h->d32, 9 * m) && h->get(h->Uw32, 54 * m);
+    ok = ok && h->get(h->Dinv32, 9 * m) && h->get(h->V32, m) && h->get(h->c32, m) && h->get(h->w32, m) &&
+         h->get(h->mu32, m) && h->get(h->lam32, m) && h->get(h->u32, 3 * m) && h->get(h->ka32, m) &&
+         h->get(h->E32, 6 * m) && h->get(h->g32, 9 * m) && h->get(h->quat, m) && h->get(h->dq32, 3 * n) &&
+         h->get(h->b32, 3 * n) && h->get(h->r32, 3 * n) && h->get(h->e32, 3 * n) && h->get(h->fr, 3 * n) &&
+         h->get(h->fu, 3 * n) && h->get(h->fw, 3 * n) && h->get(h->fp, 3 * n) && h->get(h->fs, 3 * n) &&
+         h->get(h->E0, 9 * m) && h->get(h->Qrest, 3 * n);
+  } else
+    ok = ok && h->get(h->gam64, 48 * m) && h->get(h->y64, 9 * m) && h->get(h->d64, 9 * m) && h->get(h->Uw64, 54 * m);
+  ok = ok && h->get(h->pr, 16 * n) && h->get(h->pu, 16 * n) && h->get(h->pw, 16 * n) && h->get(h->pp, 16 * n) &&
+       h->get(h->ps, 16 * n) && h->get(h->scratch16, 32 * n) && h->get(h->phi64, 16 * n) && h->get(h->Einv, 256);
+  if (h->mixed) {
+    ok = ok && h->get(h->phi32, 16 * n) && h->get(h->ug32, 2 * n) && h->get(h->part32, 64 * (int64_t)h->sms) &&
+         h->get(h->sync32, 96);
+    if (!pcg32_shape(n, h->sms, &h->grid32, &h->rpt32)) h->rpt32 = 0;
+  }
+  h->grid_tet = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 127) / 128), 8 * (int64_t)h->sms);
+  h->grid_syrk = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 23) / 24), 2 * (int64_t)h->sms);
+  h->grid_pcg3 = pcg_max_grid(3, n);
+  h->grid_pcg16 = pcg_max_grid(16, n);
+  const int pcg_part = std::max(h->grid_pcg3 * (4 * 3 + 3 * kModes), h->grid_pcg16 * 64);  // per-block partials
+  const int64_t gpart = std::max<int64_t>(h->grid_tet * (int64_t)kLsNV, 256 * (int64_t)(2 * h->sms + 1));
+  ok = ok && h->get(h->part_grad, gpart) && h->get(h->part_dir, h->grid_tet) && h->get(h->part_ls, h->grid_tet * kLsNV) &&
+       h->get(h->part_pcg, std::max<int64_t>(pcg_part, 256 * (int64_t)(2 * h->sms + 1))) &&
+       h->get(h->cpart, (int64_t)h->grid_syrk * (kCapEntries + kK)) && h->get(h->z, kK) && h->get(h->cfull, kCapEntries + kK) && h->get(h->small, 256) &&
+       h->get(h->sc, 1) && h->get(h->bar, 1);
+  if (h->mixed) ok = ok && h->get(h->val32, nnz) && h->get(h->ldinv32, n);
+  ok = ok && h->get(h->rowptr, n + 1) && h->get(h->col, nnz) && h->get(h->val, nnz) && h->get(h->ldinv, n) &&
+       h->get(h->bfix, 3 * n) && h->get(h->qfix, 3 * n) && h->get(h->is_fixed, n) && h->get(h->slot_ptr, n + 1) &&
+       h->get(h->slot_idx, 4 * m);
+  return ok;
 }
 
 int compute_gref(emu_handle* h) {
@@ -917,52 +1002,23 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
   }
 
   // ---- device allocation ----
-  bool ok = true;
   const int64_t nnz = (int64_t)colv.size();
-  ok = ok && h->get(h->tet, m) && h->get(h->Dinv, 9 * m) && h->get(h->V, m) && h->get(h->c, m) && h->get(h->w, m) &&
-       h->get(h->mu, m) && h->get(h->lam, m) && h->get(h->u, 3 * m) && h->get(h->ka, m);
-  ok = ok && h->get(h->R, 9 * m) && h->get(h->s, 6 * m) && h->get(h->q, 3 * n) && h->get(h->dq, 3 * n) &&
-       h->get(h->q0, 3 * n) && h->get(h->g, 9 * m) && h->get(h->contrib, 12 * m) && h->get(h->b, 16 * n);
-  if (h->mixed) {
-    ok = ok && h->get(h->gam32, 48 * m) && h->get(h->y32, 9 * m) && h->get(h->d32, 9 * m) && h->get(h->Uw32, 54 * m);
-    ok = ok && h->get(h->Dinv32, 9 * m) && h->get(h->V32, m) && h->get(h->c32, m) && h->get(h->w32, m) &&
-         h->get(h->mu32, m) && h->get(h->lam32, m) && h->get(h->u32, 3 * m) && h->get(h->ka32, m) &&
-         h->get(h->E32, 6 * m) && h->get(h->g32, 9 * m) && h->get(h->quat, m) && h->get(h->dq32, 3 * n) &&
-         h->get(h->b32, 3 * n) && h->get(h->r32, 3 * n) && h->get(h->e32, 3 * n) && h->get(h->fr, 3 * n) &&
-         h->get(h->fu, 3 * n) && h->get(h->fw, 3 * n) && h->get(h->fp, 3 * n) && h->get(h->fs, 3 * n) &&
-         h->get(h->E0, 9 * m) && h->get(h->Qrest, 3 * n);
-  } else
-    ok = ok && h->get(h->gam64, 48 * m) && h->get(h->y64, 9 * m) && h->get(h->d64, 9 * m) && h->get(h->Uw64, 54 * m);
-  ok = ok && h->get(h->pr, 16 * n) && h->get(h->pu, 16 * n) && h->get(h->pw, 16 * n) && h->get(h->pp, 16 * n) &&
-       h->get(h->ps, 16 * n) && h->get(h->scratch16, 32 * n) && h->get(h->phi64, 16 * n) && h->get(h->Einv, 256);
-  if (h->mixed) {
-    ok = ok && h->get(h->phi32, 16 * n) && h->get(h->ug32, 2 * n) && h->get(h->part32, 64 * (int64_t)h->sms) &&
-         h->get(h->sync32, 96);
-    if (!pcg32_shape(n, h->sms, &h->grid32, &h->rpt32)) h->rpt32 = 0;
-  }
-  h->grid_tet = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 127) / 128), 8 * (int64_t)h->sms);
-  h->grid_syrk = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 23) / 24), 2 * (int64_t)h->sms);
-  h->grid_pcg3 = pcg_max_grid(3, n);
-  h->grid_pcg16 = pcg_max_grid(16, n);
-  const int pcg_part = std::max(h->grid_pcg3 * (4 * 3 + 3 * kModes), h->grid_pcg16 * 64);  // per-block partials
-  const int64_t gpart = std::max<int64_t>(h->grid_tet * (int64_t)kLsNV, 256 * (int64_t)(2 * h->sms + 1));
-  ok = ok && h->get(h->part_grad, gpart) && h->get(h->part_dir, h->grid_tet) && h->get(h->part_ls, h->grid_tet * kLsNV) &&
-       h->get(h->part_pcg, std::max<int64_t>(pcg_part, 256 * (int64_t)(2 * h->sms + 1))) &&
-       h->get(h->cpart, (int64_t)h->grid_syrk * (kCapEntries + kK)) && h->get(h->z, kK) && h->get(h->cfull, kCapEntries + kK) && h->get(h->small, 256) &&
-       h->get(h->sc, 1) && h->get(h->bar, 1);
-  if (h->mixed) ok = ok && h->get(h->val32, nnz) && h->get(h->ldinv32, n);
-  ok = ok && h->get(h->rowptr, n + 1) && h->get(h->col, nnz) && h->get(h->val, nnz) && h->get(h->ldinv, n) &&
-       h->get(h->bfix, 3 * n) && h->get(h->qfix, 3 * n) && h->get(h->is_fixed, n) && h->get(h->slot_ptr, n + 1) &&
-       h->get(h->slot_idx, 4 * m);
+  bool ok = alloc_device(h, nnz);
   if (!ok) {
     h->release();
     delete h;
     return fail(EMU_ERR_OOM, "device allocation failed");
   }
-  if (cudaMallocHost(&h->sc_host, sizeof(DevScalars)) != cudaSuccess) {
+  if (cudaMallocHost(&h->sc_host, sizeof(DevScalars)) != cudaSuccess ||
+      cudaMallocHost(&h->o6_host, 8 * sizeof(double)) != cudaSuccess) {
     h->release();
     delete h;
     return fail(EMU_ERR_OOM, "pinned host allocation failed");
+  }
+  if (cudaEventCreateWithFlags(&h->wait_ev, cudaEventDisableTiming) != cudaSuccess) {
+    h->release();
+    delete h;
+    return fail(EMU_ERR_CUDA, "cudaEventCreate failed");
   }
   // barrier words of the FP32 CG start at zero (every launch leaves them so)
   if (h->sync32 && cudaMemsetAsync(h->sync32, 0, 96 * sizeof(unsigned), h->st) != cudaSuccess) {
@@ -1059,161 +1115,359 @@ int emu_set_activation_device(emu_handle* h, const double* a_device, int64_t cou
   return emu_set_activation(h, a.data(), count);
 }
 
-int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats) {
-  if (!h) return fail(EMU_ERR_INVALID_ARG, "NULL handle");
-  auto t0 = std::chrono::steady_clock::now();
-  int rc = EMU_OK;
-  if (!h->gref_valid) {
-    rc = compute_gref(h);
-    if (rc) return rc;
-  }
-  DevScalars init;
-  memset(&init, 0, sizeof(init));
-  init.sigma_start = h->prm.ls_sigma0;
-  EMU_CK(cudaMemcpyAsync(h->sc, &init, sizeof(init), cudaMemcpyHostToDevice, h->st));
-  double gnorm_ref = h->gref > h->floor ? h->gref : 0.0;
-  int it = 0;
-  double res = 0.0;
+}  // extern "C"
+
+namespace emu {
+
+// One quasi-static solve (Algorithm 1) as a resumable task. step() enqueues
+// work on the handle's stream up to the next point where the host must read
+// a device result (the residual of an exact coupling solve, the gradient
+// norm and line-search state of an iteration), records wait_ev there and
+// returns 1; once that work has finished, the next step() takes the decision
+// and enqueues the following stretch. A single solve steps it with blocking
+// waits; a batch or the server interleaves many handles' tasks on their own
+// streams so their work overlaps on the device.
+struct SolveTask {
+  enum Phase { START, TOP, REF_RES, REF_CHECK, GRAD, DECIDE, FINISH, DONE };
+  emu_handle* h = nullptr;
+  emu_solve_stats* stats = nullptr;
+  Phase phase = START;
+  int it = 0, since = 0, round = 0;
   int status = EMU_OK;
-  const double tol = h->prm.tol_rel_residual;
+  double res = 0.0, gnorm_ref = 0.0;
+  bool first_eval = true;
+  bool ls_refreshed = false;  // q re-solved during the current run of rejected passes
+  bool ls_retried = false;    // and dq tightened after it, too
+  std::chrono::steady_clock::time_point t0;
+};
+
+SolveTask* task_new(emu_handle* h, emu_solve_stats* stats) {
+  SolveTask* t = new (std::nothrow) SolveTask;
+  if (!t) return nullptr;
+  t->h = h;
+  t->stats = stats;
+  return t;
+}
+void task_delete(SolveTask* t) { delete t; }
+int task_status(const SolveTask* t) { return t->status; }
+bool task_done(const SolveTask* t) { return t->phase == SolveTask::DONE; }
+bool task_ready(const SolveTask* t) {
+  // a failed query (not "not ready") is surfaced by the next step's calls
+  return cudaEventQuery(t->h->wait_ev) != cudaErrorNotReady;
+}
+
+namespace {
+// enqueue the gradient and its reduction, then wait for the scalars
+int enqueue_grad(emu_handle* h) {
+  h->ph_begin();
+  if (h->mixed)
+    launch_grad_mixed(h->margs(), h->grid_tet, h->st);
+  else
+    launch_grad<double>(h->args<double>(), h->grid_tet, h->st);
+  h->ph_end(EMU_PHASE_GRAD, 1);
+  h->ph_begin();
+  launch_reduce_grad(h->part_grad, h->grid_tet, h->sc, nullptr, nullptr, h->st);
+  h->ph_end(EMU_PHASE_SMALL, 1);
+  EMU_CK(cudaGetLastError());
+  EMU_CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st));
+  return EMU_OK;
+}
+
+// enqueue the rest of one Newton iteration: direction, dq, line search, update
+int enqueue_step(emu_handle* h) {
   TetArgs<double> a64 = h->args<double>();
   MixArgs am = h->margs();
-  int since = h->prm.q_refresh;  // iterations since q was last solved exactly
-  h->dq_tol_now = h->prm.dq_tol;
-  bool first_eval = true;
-  bool ls_retried = false;  // q was re-solved after the current run of rejected steps
+  // Woodbury direction (Eqs. 9-12)
+  h->ph_begin();
+  int syrk_blocks = h->grid_syrk;
+  if (h->mixed) {
+    syrk_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (h->m + 31) / 32), 2 * (int64_t)h->sms);
+    launch_syrk_tc(am, syrk_blocks, h->cpart, h->st);
+  } else {
+    launch_syrk<double>(a64, h->grid_syrk, h->cpart, h->st);
+  }
+  h->ph_end(EMU_PHASE_SYRK, 1);
+  h->ph_begin();
+  launch_cap_solve(h->cpart, syrk_blocks, h->cfull, h->z, h->sc, h->mixed, h->st);
+  h->ph_end(EMU_PHASE_SMALL, 2);
+  h->ph_begin();
+  if (h->mixed) {
+    MixArgs ad = am;
+    ad.partials = h->part_dir;
+    launch_dir_mixed(ad, h->grid_tet, h->st);
+  } else {
+    TetArgs<double> ad = a64;
+    ad.partials = h->part_dir;
+    launch_dir<double>(ad, h->grid_tet, h->st);
+  }
+  h->ph_end(EMU_PHASE_DIR, 1);
+  EMU_CK(cudaGetLastError());
+  int rc = solve_dq(h);
+  if (rc) return rc;
+  // Armijo line search (Algorithm 1)
+  h->ph_begin();
+  if (h->mixed) {
+    MixArgs al = am;
+    al.partials = h->part_ls;
+    launch_ls_mixed(al, h->grid_tet, h->prm.ls_rho, h->st);
+  } else {
+    TetArgs<double> al = a64;
+    al.partials = h->part_ls;
+    launch_ls<double>(al, h->grid_tet, h->prm.ls_rho, h->st);
+  }
+  h->ph_end(EMU_PHASE_LS, 1);
+  h->ph_begin();
+  launch_ls_select(h->part_dir, h->grid_tet, h->part_ls, h->grid_tet, h->sc, h->prm.ls_sigma0, h->prm.ls_rho,
+                   h->prm.ls_c, h->st);
+  h->ph_end(EMU_PHASE_SMALL, 1);
+  h->ph_begin();
+  if (h->mixed) {
+    launch_update_mixed(am, h->grid_tet, h->st);
+    launch_update_verts_f(h->n, h->sc, h->dq32, h->q, h->st);
+  } else {
+    launch_update_tets<double>(a64, h->grid_tet, h->st);
+    launch_update_verts(h->n, h->sc, h->dq, h->q, h->st);
+  }
+  h->ph_end(EMU_PHASE_UPDATE, 2);
+  EMU_CK(cudaGetLastError());
+  return EMU_OK;
+}
+}  // namespace
+
+int task_step(SolveTask* t) {
+  emu_handle* h = t->h;
+  auto wait = [&]() {
+    if (cudaEventRecord(h->wait_ev, h->st) != cudaSuccess) {
+      t->status = fail(EMU_ERR_CUDA, "cudaEventRecord failed");
+      t->phase = SolveTask::DONE;
+      return 0;
+    }
+    return 1;
+  };
+  auto abort = [&](int rc) {
+    t->status = rc;
+    t->phase = SolveTask::DONE;
+    return 0;
+  };
+  const double tol = h->prm.tol_rel_residual;
   for (;;) {
-    // q = q*(F) exactly every q_refresh iterations; in between q follows
-    // q*(F + s d) = q + s dq (Eq. 4 is affine in F).
-    if (since >= h->prm.q_refresh) {
-      rc = refresh_q(h, h->q_tol);
-      if (rc) return rc;
-      since = 0;
-    }
-    h->ph_begin();
-    if (h->mixed)
-      launch_grad_mixed(am, h->grid_tet, h->st);
-    else
-      launch_grad<double>(a64, h->grid_tet, h->st);
-    h->ph_end(EMU_PHASE_GRAD, 1);
-    h->ph_begin();
-    launch_reduce_grad(h->part_grad, h->grid_tet, h->sc, nullptr, nullptr, h->st);
-    h->ph_end(EMU_PHASE_SMALL, 1);
-    EMU_CK(cudaGetLastError());
-    rc = read_scalars(h);
-    if (rc) return rc;
-    const DevScalars& hs = *h->sc_host;
-    if (hs.barrier_timeout) {
-      status = fail(EMU_ERR_TIMEOUT, "grid barrier timed out");
-      break;
-    }
-    if (hs.nonfinite || !std::isfinite(hs.gnorm2)) {
-      status = fail(EMU_ERR_INVERTED, "non-finite gradient");
-      break;
-    }
-    const double gn = std::sqrt(hs.gnorm2);
-    if (first_eval && gnorm_ref == 0.0) gnorm_ref = gn > h->floor ? gn : 0.0;
-    first_eval = false;
-    res = gnorm_ref > 0.0 ? gn / gnorm_ref : 0.0;
-    if (res <= tol) {
-      if (since > 0) {  // confirm with an exact q before declaring convergence
-        since = h->prm.q_refresh;
-        continue;
+    int rc = EMU_OK;
+    switch (t->phase) {
+      case SolveTask::START: {
+        t->t0 = std::chrono::steady_clock::now();
+        if (!h->gref_valid) {
+          rc = compute_gref(h);
+          if (rc) return abort(rc);
+        }
+        DevScalars init;
+        memset(&init, 0, sizeof(init));
+        init.sigma_start = h->prm.ls_sigma0;
+        if (cudaMemcpyAsync(h->sc, &init, sizeof(init), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+          return abort(fail(EMU_ERR_CUDA, "cudaMemcpyAsync failed"));
+        t->gnorm_ref = h->gref > h->floor ? h->gref : 0.0;
+        t->since = h->prm.q_refresh;  // iterations since q was last solved exactly
+        h->dq_tol_now = h->prm.dq_tol;
+        t->phase = SolveTask::TOP;
+        break;
       }
-      break;
-    }
-    if (hs.sigma > 0.0) ls_retried = false;  // the last pass accepted a step
-    if (hs.ls_fail * kLsTrials >= h->prm.ls_max_trials) {
-      if (since > 0 && !ls_retried) {
-        // q has drifted from q*(F) by the loose dq solves, so the slope the
-        // Armijo test uses no longer matches the energy (a loose residual
-        // can leave a large error in the K-norm): re-solve q exactly, solve
-        // dq tightly from now on and restart the line search
-        const int32_t zero = 0;
-        const double s0 = h->prm.ls_sigma0;
-        EMU_CK(cudaMemcpyAsync(&h->sc->ls_fail, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->st));
-        EMU_CK(cudaMemcpyAsync(&h->sc->sigma_start, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st));
-        EMU_CK(cudaStreamSynchronize(h->st));
-        since = h->prm.q_refresh;
-        h->dq_tol_now = h->q_tol;  // and keep q exact along the steps from here on
-        ls_retried = true;
-        continue;
+      case SolveTask::TOP:
+        // q = q*(F) exactly every q_refresh iterations; in between q follows
+        // q*(F + s d) = q + s dq (Eq. 4 is affine in F).
+        if (t->since >= h->prm.q_refresh) {
+          rc = refresh_begin(h, h->q_tol);
+          if (rc) return abort(rc);
+          if (h->mixed) {
+            t->round = 0;
+            t->phase = SolveTask::REF_RES;
+            break;
+          }
+          t->since = 0;
+        }
+        t->phase = SolveTask::GRAD;
+        break;
+      case SolveTask::REF_RES:
+        rc = refresh_residual(h);
+        if (rc) return abort(rc);
+        t->phase = SolveTask::REF_CHECK;
+        return wait();
+      case SolveTask::REF_CHECK:
+        h->prof_flush();
+        if (refresh_converged(h, h->q_tol) || t->round + 1 >= kRefreshRounds) {
+          t->since = 0;
+          t->phase = SolveTask::GRAD;
+          break;
+        }
+        rc = refresh_correction(h);
+        if (rc) return abort(rc);
+        ++t->round;
+        t->phase = SolveTask::REF_RES;
+        break;
+      case SolveTask::GRAD:
+        rc = enqueue_grad(h);
+        if (rc) return abort(rc);
+        t->phase = SolveTask::DECIDE;
+        return wait();
+      case SolveTask::DECIDE: {
+        h->prof_flush();
+        const DevScalars& hs = *h->sc_host;
+        if (hs.barrier_timeout) {
+          t->status = fail(EMU_ERR_TIMEOUT, "grid barrier timed out");
+          t->phase = SolveTask::FINISH;
+          break;
+        }
+        if (hs.nonfinite || !std::isfinite(hs.gnorm2)) {
+          t->status = fail(EMU_ERR_INVERTED, "non-finite gradient");
+          t->phase = SolveTask::FINISH;
+          break;
+        }
+        const double gn = std::sqrt(hs.gnorm2);
+        if (t->first_eval && t->gnorm_ref == 0.0) t->gnorm_ref = gn > h->floor ? gn : 0.0;
+        t->first_eval = false;
+        t->res = t->gnorm_ref > 0.0 ? gn / t->gnorm_ref : 0.0;
+        if (t->res <= tol) {
+          if (t->since > 0) {  // confirm with an exact q before declaring convergence
+            t->since = h->prm.q_refresh;
+            t->phase = SolveTask::TOP;
+          } else {
+            t->phase = SolveTask::FINISH;
+          }
+          break;
+        }
+        if (hs.sigma > 0.0) t->ls_retried = t->ls_refreshed = false;  // the last pass accepted a step
+        // Rejected passes while q follows F only through the loose dq solves
+        // mean that q has drifted from q*(F): the slope the Armijo test uses
+        // then no longer matches the energy (a loose residual can leave a
+        // large error in the K-norm). Re-solve q exactly after two rejected
+        // passes, and restart the line search.
+        if (hs.ls_fail >= 2 && t->since > 0 && !t->ls_refreshed) {
+          launch_ls_reset(h->sc, h->prm.ls_sigma0, h->st);
+          t->since = h->prm.q_refresh;
+          t->ls_refreshed = true;
+          t->phase = SolveTask::TOP;
+          break;
+        }
+        if (hs.ls_fail * kLsTrials >= h->prm.ls_max_trials) {
+          if (!t->ls_retried) {
+            // still no step with an exact q: solve dq tightly from now on
+            // (q then stays exact along the steps) and give it one more run
+            launch_ls_reset(h->sc, h->prm.ls_sigma0, h->st);
+            if (t->since > 0) t->since = h->prm.q_refresh;
+            h->dq_tol_now = h->q_tol;
+            t->ls_retried = true;
+            t->phase = SolveTask::TOP;
+            break;
+          }
+          t->status = fail(EMU_ERR_LINESEARCH, "no Armijo step");
+          t->phase = SolveTask::FINISH;
+          break;
+        }
+        if (t->it >= h->prm.max_newton) {
+          t->status = fail(EMU_ERR_NOT_CONVERGED, "max_newton reached");
+          t->phase = SolveTask::FINISH;
+          break;
+        }
+        rc = enqueue_step(h);
+        if (rc) return abort(rc);
+        ++t->it;
+        ++t->since;
+        t->phase = SolveTask::TOP;
+        break;
       }
-      status = fail(EMU_ERR_LINESEARCH, "no Armijo step");
-      break;
+      case SolveTask::FINISH: {
+        if (cudaStreamSynchronize(h->st) != cudaSuccess) return abort(fail(EMU_ERR_CUDA, "cudaStreamSynchronize failed"));
+        h->prof_flush();
+        auto t1 = std::chrono::steady_clock::now();
+        if (t->stats) {
+          t->stats->newton_iters = t->it;
+          t->stats->ls_trials = h->sc_host->ls_trials;
+          t->stats->pcg_iters = h->sc_host->pcg_iters;
+          t->stats->status = t->status;
+          t->stats->rel_residual = t->res;
+          t->stats->energy_change = h->sc_host->dE;
+          t->stats->ms = std::chrono::duration<double, std::milli>(t1 - t->t0).count();
+        }
+        t->phase = SolveTask::DONE;
+        return 0;
+      }
+      case SolveTask::DONE:
+        return 0;
     }
-    if (it >= h->prm.max_newton) {
-      status = fail(EMU_ERR_NOT_CONVERGED, "max_newton reached");
-      break;
-    }
-    // Woodbury direction (Eqs. 9-12)
-    h->ph_begin();
-    int syrk_blocks = h->grid_syrk;
-    if (h->mixed) {
-      syrk_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (h->m + 31) / 32), 2 * (int64_t)h->sms);
-      launch_syrk_tc(am, syrk_blocks, h->cpart, h->st);
-    } else {
-      launch_syrk<double>(a64, h->grid_syrk, h->cpart, h->st);
-    }
-    h->ph_end(EMU_PHASE_SYRK, 1);
-    h->ph_begin();
-    launch_cap_solve(h->cpart, syrk_blocks, h->cfull, h->z, h->sc, h->mixed, h->st);
-    h->ph_end(EMU_PHASE_SMALL, 2);
-    h->ph_begin();
-    if (h->mixed) {
-      MixArgs ad = am;
-      ad.partials = h->part_dir;
-      launch_dir_mixed(ad, h->grid_tet, h->st);
-    } else {
-      TetArgs<double> ad = a64;
-      ad.partials = h->part_dir;
-      launch_dir<double>(ad, h->grid_tet, h->st);
-    }
-    h->ph_end(EMU_PHASE_DIR, 1);
-    EMU_CK(cudaGetLastError());
-    rc = solve_dq(h);
-    if (rc) return rc;
-    // Armijo line search (Algorithm 1)
-    h->ph_begin();
-    if (h->mixed) {
-      MixArgs al = am;
-      al.partials = h->part_ls;
-      launch_ls_mixed(al, h->grid_tet, h->prm.ls_rho, h->st);
-    } else {
-      TetArgs<double> al = a64;
-      al.partials = h->part_ls;
-      launch_ls<double>(al, h->grid_tet, h->prm.ls_rho, h->st);
-    }
-    h->ph_end(EMU_PHASE_LS, 1);
-    h->ph_begin();
-    launch_ls_select(h->part_dir, h->grid_tet, h->part_ls, h->grid_tet, h->sc, h->prm.ls_sigma0, h->prm.ls_rho,
-                     h->prm.ls_c, h->st);
-    h->ph_end(EMU_PHASE_SMALL, 1);
-    h->ph_begin();
-    if (h->mixed) {
-      launch_update_mixed(am, h->grid_tet, h->st);
-      launch_update_verts_f(h->n, h->sc, h->dq32, h->q, h->st);
-    } else {
-      launch_update_tets<double>(a64, h->grid_tet, h->st);
-      launch_update_verts(h->n, h->sc, h->dq, h->q, h->st);
-    }
-    h->ph_end(EMU_PHASE_UPDATE, 2);
-    EMU_CK(cudaGetLastError());
-    ++it;
-    ++since;
   }
-  EMU_CK(cudaStreamSynchronize(h->st));
-  h->prof_flush();
-  auto t1 = std::chrono::steady_clock::now();
-  if (stats) {
-    stats->newton_iters = it;
-    stats->ls_trials = h->sc_host->ls_trials;
-    stats->pcg_iters = h->sc_host->pcg_iters;
-    stats->status = status;
-    stats->rel_residual = res;
-    stats->energy_change = h->sc_host->dE;
-    stats->ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+}
+
+}  // namespace emu
+
+extern "C" {
+
+int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats) {
+  if (!h) return fail(EMU_ERR_INVALID_ARG, "NULL handle");
+  SolveTask t;
+  t.h = h;
+  t.stats = stats;
+  while (task_step(&t)) {
+    if (cudaEventSynchronize(h->wait_ev) != cudaSuccess) return fail(EMU_ERR_CUDA, "cudaEventSynchronize failed");
   }
+  return t.status;
+}
+
+int emu_required_bytes(const emu_mesh_desc* desc, const emu_params* params, size_t* bytes) {
+  if (!bytes) return fail(EMU_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = 0;
+  int rc = validate_mesh(desc);
+  if (rc) return rc;
+  emu_params prm;
+  if (params)
+    prm = *params;
+  else
+    emu_default_params(&prm);
+  rc = validate_params(&prm);
+  if (rc) return rc;
+  emu_handle h;
+  h.dry = true;
+  h.n = desc->n_verts;
+  h.m = desc->n_tets;
+  h.mixed = prm.precision == EMU_PRECISION_MIXED;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(EMU_ERR_CUDA, "no CUDA device");
+  if (cudaDeviceGetAttribute(&h.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(EMU_ERR_CUDA, "cudaDeviceGetAttribute failed");
+  // the Laplacian has at most 16 entries per tet plus one per pinned row
+  alloc_device(&h, 16 * h.m + h.n);
+  *bytes = h.dry_bytes;
+  return EMU_OK;
+}
+
+int emu_batch_solve(emu_handle* const* hs, int32_t count, emu_solve_stats* stats) {
+  if (count < 0 || (count > 0 && !hs)) return fail(EMU_ERR_INVALID_ARG, "emu_batch_solve: bad handle array");
+  for (int32_t i = 0; i < count; ++i) {
+    if (!hs[i]) return fail(EMU_ERR_INVALID_ARG, "emu_batch_solve: NULL handle");
+    for (int32_t j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(EMU_ERR_INVALID_ARG, "emu_batch_solve: a handle appears twice");
+  }
+  std::vector<SolveTask> ts(count);
+  std::vector<char> waiting(count, 0);
+  int32_t live = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    ts[i].h = hs[i];
+    ts[i].stats = stats ? stats + i : nullptr;
+    waiting[i] = (char)task_step(&ts[i]);
+    live += waiting[i];
+  }
+  while (live > 0) {
+    bool progressed = false;
+    for (int32_t i = 0; i < count; ++i) {
+      if (!waiting[i] || !task_ready(&ts[i])) continue;
+      waiting[i] = (char)task_step(&ts[i]);
+      if (!waiting[i]) --live;
+      progressed = true;
+    }
+    if (!progressed) std::this_thread::yield();
+  }
+  std::string first_err;
+  int status = EMU_OK;
+  for (int32_t i = 0; i < count; ++i)
+    if (ts[i].status != EMU_OK && status == EMU_OK) status = ts[i].status;
+  if (status != EMU_OK) set_last_error("emu_batch_solve: at least one solve failed (see the per-handle stats)");
   return status;
 }
 

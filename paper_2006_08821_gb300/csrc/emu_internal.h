@@ -81,4 +81,16 @@ struct AcapView {
 bool acap_view(const emu_handle* h, AcapView* v);
 void set_last_error(const char* msg);
 
+// Resumable quasi-static solve of one handle (the same steps as
+// emu_solve_quasistatic). task_step enqueues work on the handle's stream up
+// to the next host decision and returns 1 while that work is in flight (poll
+// task_ready), 0 once the solve has finished (task_status is its result).
+struct SolveTask;
+SolveTask* task_new(emu_handle* h, emu_solve_stats* stats);
+int task_step(SolveTask* t);
+bool task_ready(const SolveTask* t);
+bool task_done(const SolveTask* t);
+int task_status(const SolveTask* t);
+void task_delete(SolveTask* t);
+
 }  // namespace emu

@@ -403,6 +403,13 @@ __global__ void __launch_bounds__(256) k_cap_solve(const double* __restrict__ cf
   }
 }
 
+__global__ void k_ls_reset(DevScalars* sc, double sigma0) {
+  sc->ls_fail = 0;
+  sc->sigma_start = sigma0;
+}
+
+void launch_ls_reset(DevScalars* sc, double sigma0, cudaStream_t st) { k_ls_reset<<<1, 1, 0, st>>>(sc, sigma0); }
+
 void launch_cap_solve(const double* cpart, int nblk, const double* cfull_scratch, double* z, DevScalars* sc,
                       bool fp32_factor, cudaStream_t st) {
   double* cfull = const_cast<double*>(cfull_scratch);

@@ -56,6 +56,8 @@ void launch_reduce_grad(const double* partials, int nblk, DevScalars* sc, double
 // cfull_scratch receives their sums. fp32_factor: factor and solve in FP32.
 void launch_cap_solve(const double* cpart, int nblk, const double* cfull_scratch, double* z, DevScalars* sc,
                       bool fp32_factor, cudaStream_t st);
+// Restart the line search: ls_fail = 0, sigma_start = sigma0.
+void launch_ls_reset(DevScalars* sc, double sigma0, cudaStream_t st);
 void launch_ls_select(const double* dir_partials, int nblk_dir, const double* ls_partials, int nblk_ls,
                       DevScalars* sc, double sigma0, double rho, double c_armijo, cudaStream_t st);
 

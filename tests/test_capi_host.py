@@ -91,3 +91,26 @@ def test_create_rejects_invalid_input_before_touching_the_device(lib, mutate, co
     assert rc == code
     assert not h.value
     assert len(lib.emu_last_error()) > 0
+
+
+def test_batch_solve_validates_its_arguments_without_a_device(lib):
+    from paper_2006_08821_gb300 import binding as B
+
+    assert lib.emu_batch_solve(None, 0, None) == B.EMU_OK  # empty batch: nothing to do
+    assert lib.emu_batch_solve(None, 1, None) == B.EMU_ERR_INVALID_ARG
+    hs = (C.c_void_p * 2)(None, None)
+    assert lib.emu_batch_solve(hs, 2, None) == B.EMU_ERR_INVALID_ARG
+    assert lib.emu_batch_solve(hs, -1, None) == B.EMU_ERR_INVALID_ARG
+
+
+def test_server_calls_validate_their_arguments_without_a_device(lib):
+    from paper_2006_08821_gb300 import binding as B
+
+    n = C.c_int32()
+    ids = (C.c_uint64 * 4)()
+    assert lib.emu_server_poll(None, ids, 4, C.byref(n)) == B.EMU_ERR_INVALID_ARG
+    assert lib.emu_server_result(None, 1, None, None) == B.EMU_ERR_INVALID_ARG
+    assert lib.emu_server_submit(None, None, None, 1, 1) == B.EMU_ERR_INVALID_ARG
+    assert lib.emu_server_create(1 << 30, None, None, None) == B.EMU_ERR_INVALID_ARG
+    assert lib.emu_server_destroy(None) == B.EMU_OK
+    assert lib.emu_required_bytes(None, None, None) == B.EMU_ERR_INVALID_ARG
