@@ -40,7 +40,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from emu_inputs import box_beam, muscle_tendon_unit  # noqa: E402
+from emu_inputs import batch_set, box_beam, mtu_for_tet_count, muscle_tendon_unit, request_stream  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -214,13 +214,161 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _finish_line(line, rank, dist):
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_batch(args, emu, torch, rank, world, dist):
+    """Independent box beams of log-uniform size (1k-60k tets, activation
+    U[0, 1]), all solved together by emu_batch_solve, each mesh on its own
+    stream. A step resets every mesh to rest and solves the batch once; the
+    host clock spans the whole batch (synchronized on both sides)."""
+    meshes = batch_set(count=args.meshes, seed=3)
+    mixed = args.precision == "mixed"
+    params = emu.Params(tol_rel_residual=args.tol, precision=emu.PRECISION_MIXED if mixed else emu.PRECISION_FP64)
+    t_setup = time.perf_counter()
+    streams, solvers = [], []
+    for mesh in meshes:
+        st = torch.cuda.Stream()
+        s = emu.Solver(mesh, params, stream=st.cuda_stream)
+        s.set_activation(mesh.activations[0])
+        streams.append(st)
+        solvers.append(s)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    m_each = np.array([mm.n_tets for mm in meshes], dtype=np.float64)
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        for s in solvers:
+            s.reset()
+        for s, mesh in zip(solvers, meshes):
+            s.set_activation(mesh.activations[0])
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats = emu.batch_solve(solvers)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, stats
+
+    for _ in range(args.warmup):
+        step()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    times, tet_iters, iters, resid = [], 0.0, [], []
+    for _ in range(args.steps):
+        dt, stats = step()
+        times.append(dt)
+        its = np.array([st.newton_iters for st in stats], dtype=np.float64)
+        tet_iters += float((m_each * its).sum())
+        iters.append(int(its.sum()))
+        resid.append(max(st.rel_residual for st in stats))
+    clk = clocks.stop()
+    total = float(np.sum(times))
+    if dist:
+        t = torch.tensor([total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t[0])
+    value = tet_iters * world / total
+    line = {
+        "metric": "tet-iters/s", "value": value, "unit": "tet-iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"batch of {len(meshes)} box beams, log-uniform 1k-60k tets "
+                               f"(sum {int(m_each.sum())} tets), activation U[0,1], from rest, rel residual {args.tol:g}, "
+                               "one emu_batch_solve per step, one stream per mesh",
+                   "precision": args.precision, "l2": "inputs larger than L2; flushed between steps",
+                   "tets": int(m_each.sum()), "meshes": len(meshes)},
+        "newton_iters_per_step": iters, "max_rel_residual": float(np.max(resid)), "setup_s": setup_s,
+        "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": value, "unit": "tet-iters/s", "h2d_bytes_per_step": int(8 * m_each.sum()), "d2h_bytes_per_step": 0},
+        "clocks": clk,
+    }
+    for s in solvers:
+        s.close()
+    _finish_line(line, rank, dist)
+
+
+def run_serve(args, emu, torch, rank, world, dist):
+    """Poisson stream of quasi-static requests (muscle-tendon units of 1k to
+    200k tets, 1-30 frames each, tendon fraction U[0, 0.2]) submitted at their
+    arrival times to one emu_server with a device-memory budget; reports the
+    sustained tet-iters/s over the makespan and p50/p99 request latency."""
+    reqs = request_stream(rate_hz=args.rate, seed=4, max_requests=args.requests)
+    built = []
+    for r in reqs:
+        mesh = mtu_for_tet_count(r["tets"], tendon_frac=r["tendon_frac"], seed=r["seed"])
+        muscle = (mesh.material_id == 0).astype(np.float64)
+        fr = r["frames"]
+        acts = np.stack([muscle * r["a_max"] * (f + 1) / fr for f in range(fr)])
+        built.append((r, mesh, acts))
+    mixed = args.precision == "mixed"
+    params = emu.Params(tol_rel_residual=args.tol, precision=emu.PRECISION_MIXED if mixed else emu.PRECISION_FP64)
+    srv = emu.Server(int(args.budget_gb * (1 << 30)), params)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    pending = list(built)
+    results = {}
+    done_at = {}
+    while len(results) < len(built):
+        now = time.perf_counter() - t0
+        while pending and pending[0][0]["arrival_s"] - reqs[0]["arrival_s"] <= now:
+            r, mesh, acts = pending.pop(0)
+            srv.submit(mesh, acts, r["id"])
+        for i in srv.poll():
+            results[i] = srv.result(i)
+            done_at[i] = time.perf_counter() - t0
+        time.sleep(0.0005)
+    makespan = max(done_at.values())
+    clk = clocks.stop()
+    srv.close()
+    tet_iters = 0.0
+    lat, bad = [], 0
+    by_id = {r["id"]: (r, mesh) for r, mesh, _ in built}
+    for i, (q, st) in results.items():
+        r, mesh = by_id[i]
+        tet_iters += float(mesh.n_tets) * st.newton_iters
+        lat.append(st.latency_ms)
+        bad += int(st.status != 0)
+    value = tet_iters * world / makespan
+    line = {
+        "metric": "tet-iters/s", "value": value, "unit": "tet-iters/s", "n_gpus": world, "steps": len(built),
+        "warmup": 0, "ms_per_step": 1e3 * makespan / len(built), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"serving: first {len(built)} requests of a Poisson stream at {args.rate:g}/s, "
+                               "muscle-tendon units log-uniform 1k-200k tets, 1-30 frames, tendon U[0,0.2], "
+                               f"budget {args.budget_gb:g} GB, rel residual {args.tol:g}",
+                   "precision": args.precision, "requests": len(built),
+                   "tets_mean": float(np.mean([mm.n_tets for _, mm, _ in built]))},
+        "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+        "failed_requests": bad, "makespan_s": makespan,
+        "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": value, "unit": "tet-iters/s",
+                "h2d_bytes_per_step": int(np.mean([8 * a.size for _, _, a in built])),
+                "d2h_bytes_per_step": int(np.mean([24 * mm.n_verts * a.shape[0] for _, mm, a in built]))},
+        "clocks": clk,
+    }
+    _finish_line(line, rank, dist)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mtu", choices=["mtu", "box", "mtu_small"])
+    ap.add_argument("--workload", default="mtu", choices=["mtu", "box", "mtu_small", "batch", "serve"])
+    ap.add_argument("--meshes", type=int, default=256, help="batch: number of meshes")
+    ap.add_argument("--requests", type=int, default=24, help="serve: requests taken from the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (1/s)")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: device-memory budget")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -251,6 +399,10 @@ def main():
     b.build()
     import paper_2006_08821_gb300 as emu
 
+    if args.workload == "batch":
+        return run_batch(args, emu, torch, rank, world, dist)
+    if args.workload == "serve":
+        return run_serve(args, emu, torch, rank, world, dist)
     mesh, desc = make_workload(args.workload)
     frames = mesh.activations.shape[0]
     if args.warmup + args.steps > frames - 1:
