@@ -101,6 +101,11 @@ struct emu_handle {
   DevScalars* sc_host = nullptr;  // pinned
   double* o6_host = nullptr;       // pinned: residual sums of the refresh rounds
   cudaEvent_t wait_ev = nullptr;   // marks the work a solve task waits for
+  // one Newton iteration (direction .. update, next gradient) as a CUDA graph
+  cudaGraphExec_t iter_exec = nullptr;
+  double iter_exec_dq = -1.0;      // dq tolerance the graph was captured with
+  bool graphs_ok = true;           // false once a capture failed (direct launches)
+  int64_t iter_graph_kernels = 0;  // kernel launches in one graph launch
   GridBarrier* bar = nullptr;
   // Laplacian and pins
   int32_t *rowptr = nullptr, *col = nullptr;
@@ -202,6 +207,8 @@ struct emu_handle {
     o6_host = nullptr;
     if (wait_ev) cudaEventDestroy(wait_ev);
     wait_ev = nullptr;
+    if (iter_exec) cudaGraphExecDestroy(iter_exec);
+    iter_exec = nullptr;
   }
 
   template <typename TW> TetArgs<TW> args();
@@ -1020,6 +1027,12 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     delete h;
     return fail(EMU_ERR_CUDA, "cudaEventCreate failed");
   }
+  // kernel attributes are set here, outside any stream capture
+  if (h->mixed && (prepare_syrk_tc() != cudaSuccess || prepare_pcg32() != cudaSuccess)) {
+    h->release();
+    delete h;
+    return fail(EMU_ERR_CUDA, "cudaFuncSetAttribute failed");
+  }
   // barrier words of the FP32 CG start at zero (every launch leaves them so)
   if (h->sync32 && cudaMemsetAsync(h->sync32, 0, 96 * sizeof(unsigned), h->st) != cudaSuccess) {
     h->release();
@@ -1232,6 +1245,46 @@ int enqueue_step(emu_handle* h) {
   EMU_CK(cudaGetLastError());
   return EMU_OK;
 }
+// Enqueues enqueue_step + enqueue_grad as one CUDA graph launch (captured
+// on first use and again when the dq tolerance changes). Returns 1 when the
+// graph was launched, 0 when the caller must enqueue directly (profiling
+// on, the legacy default stream, or a capture that failed).
+int launch_iteration_graph(emu_handle* h) {
+  if (!h->graphs_ok || h->prof_on || h->st == nullptr) return 0;
+  if (!h->iter_exec || h->iter_exec_dq != h->dq_tol_now) {
+    if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
+    h->iter_exec = nullptr;
+    if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      h->graphs_ok = false;
+      return 0;
+    }
+    const int64_t launches0 = h->launches;
+    int rc = enqueue_step(h);
+    if (!rc) rc = enqueue_grad(h);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->st, &g);
+    h->iter_graph_kernels = h->launches - launches0;  // kernels of one launch
+    h->launches = launches0;                          // nothing ran yet
+    cudaGraphExec_t ex = nullptr;
+    if (rc || e != cudaSuccess || !g || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      h->graphs_ok = false;
+      return 0;
+    }
+    cudaGraphDestroy(g);
+    h->iter_exec = ex;
+    h->iter_exec_dq = h->dq_tol_now;
+  }
+  if (cudaGraphLaunch(h->iter_exec, h->st) != cudaSuccess) {
+    cudaGetLastError();
+    h->graphs_ok = false;
+    return 0;
+  }
+  h->launches += h->iter_graph_kernels;
+  return 1;
+}
 }  // namespace
 
 int task_step(SolveTask* t) {
@@ -1366,10 +1419,15 @@ int task_step(SolveTask* t) {
           t->phase = SolveTask::FINISH;
           break;
         }
-        rc = enqueue_step(h);
-        if (rc) return abort(rc);
         ++t->it;
         ++t->since;
+        // an iteration with no exact re-solve of q after it runs as one graph
+        if (t->since < h->prm.q_refresh && launch_iteration_graph(h)) {
+          t->phase = SolveTask::DECIDE;
+          return wait();
+        }
+        rc = enqueue_step(h);
+        if (rc) return abort(rc);
         t->phase = SolveTask::TOP;
         break;
       }

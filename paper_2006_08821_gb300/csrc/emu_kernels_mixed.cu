@@ -456,16 +456,23 @@ __global__ void __launch_bounds__(256) k_syrk_tc(MixArgs a, double* __restrict__
   }
 }
 
-void launch_syrk_tc(const MixArgs& a, int grid, double* cpart, cudaStream_t st) {
-  // the opt-in shared-memory size is a per-device property of each kernel
+// Opts the TC SYRK into its dynamic shared memory on the current device
+// (once per device; call outside stream capture).
+cudaError_t prepare_syrk_tc() {
   static bool attr_set[64] = {false};
   int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    cudaFuncSetAttribute(k_syrk_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-    cudaFuncSetAttribute(k_syrk_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-    attr_set[dev] = true;
-  }
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (attr_set[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_syrk_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_syrk_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e == cudaSuccess) attr_set[dev] = true;
+  return e;
+}
+
+void launch_syrk_tc(const MixArgs& a, int grid, double* cpart, cudaStream_t st) {
   if (a.m % 4 == 0)
     k_syrk_tc<true><<<grid, 256, kTcSmem, st>>>(a, cpart);
   else

@@ -48,6 +48,8 @@ void launch_rhs_state_mixed(const MixArgs& a, int grid, cudaStream_t st);
 void launch_syrk_mixed(const MixArgs& a, int grid, double* cpart, cudaStream_t st);
 // Same sums on TF32 tensor cores (mma.sync), grid blocks of 32-tet chunks.
 void launch_syrk_tc(const MixArgs& a, int grid, double* cpart, cudaStream_t st);
+// Per-device kernel attributes of the TC SYRK (before its first launch).
+cudaError_t prepare_syrk_tc();
 void launch_update_verts_f(int64_t n, const DevScalars* sc, const float* dq, double* q, cudaStream_t st);
 void launch_assemble_f(int64_t n, const int32_t* slot_ptr, const int32_t* slot_idx, const double* contrib,
                        const uint8_t* is_fixed, float* b, cudaStream_t st);

@@ -58,6 +58,8 @@ struct Pcg32Work {
 // 256 blocks). args.bar, args.r .. args.s and args.partials are unused.
 bool pcg32_shape(int64_t n, int sms, int* grid, int* rpt);
 cudaError_t launch_pcg32(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, int rpt, cudaStream_t st);
+// Per-device kernel attributes of the FP32 CG (before its first launch).
+cudaError_t prepare_pcg32();
 
 // FP64 residual r = b - K x (3 columns) with a float copy; out6 receives
 // sum |r_j|^2 (j < 3) and sum |b_j|^2 (3 + j).

@@ -518,21 +518,25 @@ timeout:
 
 namespace {
 template <int RPT, bool C>
-cudaError_t launch32(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, cudaStream_t st) {
+cudaError_t prepare32() {
   // the coarse rows live in dynamic shared memory (RPT x 16 KB); above the
   // default 48 KB the kernel needs the opt-in, a per-device attribute
   const size_t smem = C ? sizeof(float4) * (kModes / 4) * RPT * NT : 0;
-  if (smem > 48 * 1024) {
-    static bool set[64] = {false};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64 && !set[dev]) {
-      e = cudaFuncSetAttribute(pcg32_kernel<RPT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      set[dev] = true;
-    }
-  }
+  if (smem <= 48 * 1024) return cudaSuccess;
+  static bool set[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (set[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(pcg32_kernel<RPT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) set[dev] = true;
+  return e;
+}
+
+template <int RPT, bool C>
+cudaError_t launch32(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, cudaStream_t st) {
+  const size_t smem = C ? sizeof(float4) * (kModes / 4) * RPT * NT : 0;
   PcgArgsT<float> a = args;
   Pcg32Work w = work;
   void* params[] = {(void*)&a, (void*)&w};
@@ -552,6 +556,12 @@ bool pcg32_shape(int64_t n, int sms, int* grid, int* rpt) {
   *grid = (int)nb;
   *rpt = r;
   return true;
+}
+
+cudaError_t prepare_pcg32() {
+  cudaError_t e = prepare32<4, true>();
+  if (e == cudaSuccess) e = prepare32<8, true>();
+  return e;
 }
 
 cudaError_t launch_pcg32(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, int rpt, cudaStream_t st) {
