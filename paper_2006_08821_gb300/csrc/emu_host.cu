@@ -68,6 +68,7 @@ struct emu_handle {
   double *y64 = nullptr, *d64 = nullptr, *Uw64 = nullptr;
   float *y32 = nullptr, *d32 = nullptr, *Uw32 = nullptr;
   double* contrib = nullptr;
+  float* contrib32 = nullptr;  // mixed: FP32 corner terms of the direction
   double* b = nullptr;
   double *pr = nullptr, *pu = nullptr, *pw = nullptr, *pp = nullptr, *ps = nullptr;
   // mixed path: FP32 constants and state, FP32 CG work vectors
@@ -292,6 +293,7 @@ struct emu_handle {
     a.d = d32;
     a.Uw = Uw32;
     a.contrib = contrib;
+    a.contrib32 = contrib32;
     a.b32 = b32;
     a.z = z;
     a.sc = sc;
@@ -557,7 +559,7 @@ int solve_dq(emu_handle* h) {
     return EMU_OK;
   }
   h->ph_begin();
-  launch_assemble_f(h->n, h->slot_ptr, h->slot_idx, h->contrib, h->is_fixed, h->b32, h->st);
+  launch_assemble_f(h->n, h->slot_ptr, h->slot_idx, h->contrib32, h->is_fixed, h->b32, h->st);
   h->ph_end(EMU_PHASE_ASSEMBLE, 1);
   EMU_CK(cudaGetLastError());
   h->ph_begin();
@@ -700,7 +702,7 @@ bool alloc_device(emu_handle* h, int64_t nnz) {
          h->get(h->E32, 6 * m) && h->get(h->g32, 9 * m) && h->get(h->quat, m) && h->get(h->dq32, 3 * n) &&
          h->get(h->b32, 3 * n) && h->get(h->r32, 3 * n) && h->get(h->e32, 3 * n) && h->get(h->fr, 3 * n) &&
          h->get(h->fu, 3 * n) && h->get(h->fw, 3 * n) && h->get(h->fp, 3 * n) && h->get(h->fs, 3 * n) &&
-         h->get(h->E0, 9 * m) && h->get(h->Qrest, 3 * n);
+         h->get(h->E0, 9 * m) && h->get(h->Qrest, 3 * n) && h->get(h->contrib32, 12 * m);
   } else
     ok = ok && h->get(h->gam64, 48 * m) && h->get(h->y64, 9 * m) && h->get(h->d64, 9 * m) && h->get(h->Uw64, 54 * m);
   ok = ok && h->get(h->pr, 16 * n) && h->get(h->pu, 16 * n) && h->get(h->pw, 16 * n) && h->get(h->pp, 16 * n) &&

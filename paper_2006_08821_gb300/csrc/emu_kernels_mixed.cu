@@ -83,10 +83,10 @@ __device__ __forceinline__ void load_state(const MixArgs& a, int64_t i, float* R
   for (int k = 0; k < 6; ++k) e6[k] = a.E[k * a.m + i];
 }
 
-template <typename TX>
-__device__ __forceinline__ void corners_f(double* __restrict__ contrib, int64_t i, float w, const TX* X, const float* D) {
+template <typename TO, typename TX>
+__device__ __forceinline__ void corners_f(TO* __restrict__ contrib, int64_t i, float w, const TX* X, const float* D) {
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-  double* out = contrib + 12 * i;
+  TO* out = contrib + 12 * i;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     float v[3];
@@ -153,109 +153,10 @@ __global__ void __launch_bounds__(128, 4) k_grad_m(MixArgs a) {
 void launch_grad_mixed(const MixArgs& a, int grid, cudaStream_t st) { k_grad_m<<<grid, 128, 0, st>>>(a); }
 
 // ------------------------------------------------------------ capacitance --
-// Upper-triangular 3x3 tiles of C = sum_i Yh_i^T Yh_i (FP32 within a block,
-// FP64 across blocks; mirrored into the full 48 x 48 partial), plus B y.
-__global__ void __launch_bounds__(256) k_syrk_m(MixArgs a, double* __restrict__ cpart) {
-  constexpr int CH = 24;  // 24 tets per chunk: 38.7 KB of static shared memory
-  constexpr int KR = CH * 6;
-  __shared__ float sY[KR][kK + 1];
-  __shared__ float sU[CH][54];
-  __shared__ float sg[CH][48];
-  __shared__ float sy[CH][9];
-  __shared__ float sw[CH];
-  const int tid = threadIdx.x;
-  // thread -> upper tile (tr <= tc) of the 16 x 16 grid of 3x3 tiles
-  int tr = -1, tc = -1;
-  if (tid < 136) {
-    int k = tid, r = 0;
-    while (k >= 16 - r) {
-      k -= 16 - r;
-      ++r;
-    }
-    tr = r;
-    tc = r + k;
-  }
-  float acc[3][3];
-#pragma unroll
-  for (int p = 0; p < 3; ++p)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) acc[p][q] = 0.f;
-  double by = 0.0;
-  const int bidx = tid - 136;  // 0..47 for the B y threads
-  const int64_t m = a.m;
-  const int64_t nch = (m + CH - 1) / CH;
-  for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
-    const int64_t base = ch * CH;
-    for (int e = tid; e < CH * 54; e += 256) {
-      const int k = e / CH, tt = e % CH;
-      const int64_t i = base + tt;
-      sU[tt][k] = i < m ? a.Uw[k * m + i] : 0.f;
-    }
-    for (int e = tid; e < CH * 48; e += 256) {
-      const int k = e / CH, tt = e % CH;
-      const int64_t i = base + tt;
-      sg[tt][k] = i < m ? a.gam[k * m + i] : 0.f;
-    }
-    for (int e = tid; e < CH * 9; e += 256) {
-      const int k = e / CH, tt = e % CH;
-      const int64_t i = base + tt;
-      sy[tt][k] = i < m ? a.y[k * m + i] : 0.f;
-    }
-    if (tid < CH) sw[tid] = (base + tid) < m ? a.w[base + tid] : 0.f;
-    __syncthreads();
-    for (int e = tid; e < CH * 6 * kK; e += 256) {
-      const int tt = e / (6 * kK), rem = e % (6 * kK);
-      const int k = rem / kK, col = rem % kK;
-      const int r = col >> 4, j = col & 15;
-      const float v = sU[tt][9 * k + 3 * r] * sg[tt][3 * j] + sU[tt][9 * k + 3 * r + 1] * sg[tt][3 * j + 1] +
-                      sU[tt][9 * k + 3 * r + 2] * sg[tt][3 * j + 2];
-      sY[tt * 6 + k][col] = v * sqrtf(sw[tt]);
-    }
-    __syncthreads();
-    if (tr >= 0) {
-#pragma unroll 4
-      for (int kr = 0; kr < KR; ++kr) {
-        const float a0 = sY[kr][3 * tr], a1 = sY[kr][3 * tr + 1], a2 = sY[kr][3 * tr + 2];
-        const float b0 = sY[kr][3 * tc], b1 = sY[kr][3 * tc + 1], b2 = sY[kr][3 * tc + 2];
-        acc[0][0] += a0 * b0;
-        acc[0][1] += a0 * b1;
-        acc[0][2] += a0 * b2;
-        acc[1][0] += a1 * b0;
-        acc[1][1] += a1 * b1;
-        acc[1][2] += a1 * b2;
-        acc[2][0] += a2 * b0;
-        acc[2][1] += a2 * b1;
-        acc[2][2] += a2 * b2;
-      }
-    } else if (bidx >= 0 && bidx < kK) {
-      const int r = bidx >> 4, j = bidx & 15;
-      float loc = 0.f;
-      for (int tt = 0; tt < CH; ++tt)
-        loc += sw[tt] * (sy[tt][3 * r] * sg[tt][3 * j] + sy[tt][3 * r + 1] * sg[tt][3 * j + 1] + sy[tt][3 * r + 2] * sg[tt][3 * j + 2]);
-      by += (double)loc;
-    }
-    __syncthreads();
-  }
-  // entry-major partials: cpart[e * gridDim.x + block]
-  const size_t nb = gridDim.x;
-  if (tr >= 0) {
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        cpart[(size_t)((3 * tr + p) * kK + 3 * tc + q) * nb + blockIdx.x] = (double)acc[p][q];
-        if (tr != tc) cpart[(size_t)((3 * tc + q) * kK + 3 * tr + p) * nb + blockIdx.x] = (double)acc[p][q];
-      }
-  } else if (bidx >= 0 && bidx < kK) {
-    cpart[(size_t)(kCapEntries + bidx) * nb + blockIdx.x] = by;
-  }
-}
-
-void launch_syrk_mixed(const MixArgs& a, int grid, double* cpart, cudaStream_t st) {
-  k_syrk_m<<<grid, 256, 0, st>>>(a, cpart);
-}
-
-// Tensor-core form of the same contraction: C += Yh^T Yh on TF32 tensor
+// C = sum_i Yh_i^T Yh_i with Yh_i = sqrt(w_i) U_i (G_i Phi^T) (6 x 48 per
+// tet; the Gram form of Eq. 12's capacitance, see emu_math.cuh) and the
+// Woodbury right-hand side B y = sum_i w_i (G_i Phi^T)^T y_i.
+// The contraction C += Yh^T Yh runs on TF32 tensor
 // cores (mma.sync m16n8k8, FP32 accumulate). Yh is rounded to TF32 once,
 // before the product, so C is still the exact Gram matrix of the rounded
 // rows and stays positive semi-definite.
@@ -480,19 +381,24 @@ void launch_syrk_tc(const MixArgs& a, int grid, double* cpart, cudaStream_t st) 
 }
 
 // ------------------------------------------------------------ direction ---
-__global__ void __launch_bounds__(128, 4) k_dir_m(MixArgs a) {
+// U is read twice (t = U v, then v - U^T t) instead of being held in 54
+// registers, so more tets are in flight per SM; the second pass is served
+// mostly by L1.
+__global__ void __launch_bounds__(128, 8) k_dir_m(MixArgs a) {
   __shared__ float sz[kK];
   if (threadIdx.x < kK) sz[threadIdx.x] = (float)a.z[threadIdx.x];
   __syncthreads();
   const int64_t m = a.m;
   double acc[1] = {0.0};
+  const float* __restrict__ Uw = a.Uw;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     float v[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) v[k] = 0.f;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      const float g0 = a.gam[(3 * j) * m + i], g1 = a.gam[(3 * j + 1) * m + i], g2 = a.gam[(3 * j + 2) * m + i];
+      const float g0 = __ldg(a.gam + (3 * j) * m + i), g1 = __ldg(a.gam + (3 * j + 1) * m + i),
+                  g2 = __ldg(a.gam + (3 * j + 2) * m + i);
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         const float zr = sz[16 * r + j];
@@ -501,10 +407,22 @@ __global__ void __launch_bounds__(128, 4) k_dir_m(MixArgs a) {
         v[3 * r + 2] += zr * g2;
       }
     }
-    float U[54];
+    // (I - N) v with N = U^T U
+    float t[6];
 #pragma unroll
-    for (int k = 0; k < 54; ++k) U[k] = a.Uw[k * m + i];
-    apply_I_minus_N(U, v);
+    for (int k = 0; k < 6; ++k) {
+      float acc_k = 0.f;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) acc_k += __ldg(Uw + (9 * k + c) * m + i) * v[c];
+      t[k] = acc_k;
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      float acc_c = 0.f;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc_c += __ldg(Uw + (9 * k + c) * m + i) * t[k];
+      v[c] -= acc_c;
+    }
     float dv[9];
     double gtd = 0.0;
 #pragma unroll
@@ -516,7 +434,7 @@ __global__ void __launch_bounds__(128, 4) k_dir_m(MixArgs a) {
     acc[0] += gtd;
     float D[9];
     load9f(a.Dinv, m, i, D);
-    corners_f(a.contrib, i, a.w[i], dv, D);
+    corners_f(a.contrib32, i, a.w[i], dv, D);
   }
   block_reduce_write<1>(acc, a.partials + blockIdx.x);
 }
@@ -698,10 +616,10 @@ void launch_rhs_state_mixed(const MixArgs& a, int grid, cudaStream_t st) { k_rhs
 
 __global__ void __launch_bounds__(256) k_assemble_f(int64_t n, const int32_t* __restrict__ slot_ptr,
                                                     const int32_t* __restrict__ slot_idx,
-                                                    const double* __restrict__ contrib,
+                                                    const float* __restrict__ contrib,
                                                     const uint8_t* __restrict__ is_fixed, float* __restrict__ b) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    double s0 = 0, s1 = 0, s2 = 0;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
     if (!is_fixed[v]) {
       const int32_t e0 = slot_ptr[v], e1 = slot_ptr[v + 1];
       for (int32_t e = e0; e < e1; ++e) {
@@ -711,13 +629,13 @@ __global__ void __launch_bounds__(256) k_assemble_f(int64_t n, const int32_t* __
         s2 += contrib[3 * sl + 2];
       }
     }
-    b[3 * v] = (float)s0;
-    b[3 * v + 1] = (float)s1;
-    b[3 * v + 2] = (float)s2;
+    b[3 * v] = s0;
+    b[3 * v + 1] = s1;
+    b[3 * v + 2] = s2;
   }
 }
 
-void launch_assemble_f(int64_t n, const int32_t* slot_ptr, const int32_t* slot_idx, const double* contrib,
+void launch_assemble_f(int64_t n, const int32_t* slot_ptr, const int32_t* slot_idx, const float* contrib,
                        const uint8_t* is_fixed, float* b, cudaStream_t st) {
   int grid = (int)((n + 255) / 256);
   if (grid < 1) grid = 1;

@@ -33,7 +33,8 @@ struct MixArgs {
   float* y;            // 9m
   float* d;            // 9m
   float* Uw;           // 54m
-  double* contrib;     // 12m corner terms
+  double* contrib;     // 12m corner terms (FP64: exact re-solves of q)
+  float* contrib32;    // 12m corner terms of the direction (FP32: dq solve)
   float* b32;          // 3n float RHS (unused by the tet kernels)
   const double* z;     // 48
   DevScalars* sc;
@@ -45,13 +46,13 @@ void launch_dir_mixed(const MixArgs& a, int grid, cudaStream_t st);
 void launch_ls_mixed(const MixArgs& a, int grid, double rho, cudaStream_t st);
 void launch_update_mixed(const MixArgs& a, int grid, cudaStream_t st);
 void launch_rhs_state_mixed(const MixArgs& a, int grid, cudaStream_t st);
-void launch_syrk_mixed(const MixArgs& a, int grid, double* cpart, cudaStream_t st);
-// Same sums on TF32 tensor cores (mma.sync), grid blocks of 32-tet chunks.
+// Capacitance partials C and B y on TF32 tensor cores (mma.sync), grid
+// blocks striding over 32-tet chunks; cpart is entry-major (entry * grid + block).
 void launch_syrk_tc(const MixArgs& a, int grid, double* cpart, cudaStream_t st);
 // Per-device kernel attributes of the TC SYRK (before its first launch).
 cudaError_t prepare_syrk_tc();
 void launch_update_verts_f(int64_t n, const DevScalars* sc, const float* dq, double* q, cudaStream_t st);
-void launch_assemble_f(int64_t n, const int32_t* slot_ptr, const int32_t* slot_idx, const double* contrib,
+void launch_assemble_f(int64_t n, const int32_t* slot_ptr, const int32_t* slot_idx, const float* contrib32,
                        const uint8_t* is_fixed, float* b, cudaStream_t st);
 // state conversion: (quat, E) <-> (R 9m, s 6m) FP64 structure of arrays
 void launch_mixed_to_Rs(int64_t m, const float4* quat, const float* E, double* R, double* s, cudaStream_t st);
