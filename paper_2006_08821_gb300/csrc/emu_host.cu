@@ -1180,9 +1180,11 @@ int enqueue_grad(emu_handle* h) {
   else
     launch_grad<double>(h->args<double>(), h->grid_tet, h->st);
   h->ph_end(EMU_PHASE_GRAD, 1);
-  h->ph_begin();
-  launch_reduce_grad(h->part_grad, h->grid_tet, h->sc, nullptr, nullptr, h->st);
-  h->ph_end(EMU_PHASE_SMALL, 1);
+  if (!h->mixed) {  // the mixed gradient kernel reduces ||g||^2 in its last block
+    h->ph_begin();
+    launch_reduce_grad(h->part_grad, h->grid_tet, h->sc, nullptr, nullptr, h->st);
+    h->ph_end(EMU_PHASE_SMALL, 1);
+  }
   EMU_CK(cudaGetLastError());
   EMU_CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st));
   return EMU_OK;
@@ -1224,17 +1226,24 @@ int enqueue_step(emu_handle* h) {
   if (h->mixed) {
     MixArgs al = am;
     al.partials = h->part_ls;
-    launch_ls_mixed(al, h->grid_tet, h->prm.ls_rho, h->st);
+    LsSelect sel;  // the line-search kernel's last block selects the step
+    sel.dir_partials = h->part_dir;
+    sel.nblk_dir = h->grid_tet;
+    sel.sigma0 = h->prm.ls_sigma0;
+    sel.rho = h->prm.ls_rho;
+    sel.c_armijo = h->prm.ls_c;
+    launch_ls_mixed(al, h->grid_tet, sel, h->st);
+    h->ph_end(EMU_PHASE_LS, 1);
   } else {
     TetArgs<double> al = a64;
     al.partials = h->part_ls;
     launch_ls<double>(al, h->grid_tet, h->prm.ls_rho, h->st);
+    h->ph_end(EMU_PHASE_LS, 1);
+    h->ph_begin();
+    launch_ls_select(h->part_dir, h->grid_tet, h->part_ls, h->grid_tet, h->sc, h->prm.ls_sigma0, h->prm.ls_rho,
+                     h->prm.ls_c, h->st);
+    h->ph_end(EMU_PHASE_SMALL, 1);
   }
-  h->ph_end(EMU_PHASE_LS, 1);
-  h->ph_begin();
-  launch_ls_select(h->part_dir, h->grid_tet, h->part_ls, h->grid_tet, h->sc, h->prm.ls_sigma0, h->prm.ls_rho,
-                   h->prm.ls_c, h->st);
-  h->ph_end(EMU_PHASE_SMALL, 1);
   h->ph_begin();
   if (h->mixed) {
     launch_update_mixed(am, h->grid_tet, h->st);

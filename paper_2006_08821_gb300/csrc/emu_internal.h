@@ -26,8 +26,9 @@ struct DevScalars {
   int32_t pcg_fail;     // a CG solve hit pcg_max
   int32_t barrier_timeout;
   int32_t nonfinite;    // a non-finite value was produced
-  int32_t pad[2];
+  uint32_t ticket[2];   // blocks done in the current gradient / line-search launch
 };
+constexpr int kTicketGrad = 0, kTicketLs = 1;
 
 // Mesh constants on the device (structure of arrays, index i = tet).
 template <typename T> struct MeshArrays {

@@ -555,42 +555,7 @@ template <typename TW> void launch_ls(const TetArgs<TW>& a, int grid, double rho
 
 __global__ void __launch_bounds__(256) k_ls_select(const double* dir_partials, int nblk_dir, const double* ls_partials,
                                                     int nblk_ls, DevScalars* sc, double sigma0, double rho, double c_armijo) {
-  __shared__ double s_gtd[1], s_v[kLsNV];
-  block_sum_partials<1>(dir_partials, nblk_dir, s_gtd);
-  block_sum_partials<kLsNV>(ls_partials, nblk_ls, s_v);
-  if (threadIdx.x != 0) return;
-  const double gtd = s_gtd[0];
-  double v[kLsNV];
-  for (int k = 0; k < kLsNV; ++k) v[k] = s_v[k];
-  sc->gtd = gtd;
-  double sig = sc->sigma_start;
-  int accepted = -1;
-  double dE = 0.0;
-  if (gtd < 0.0) {
-    for (int j = 0; j < kLsTrials; ++j) {
-      const double dEj = v[j] + sig * v[kLsTrials] + 0.5 * sig * sig * v[kLsTrials + 1];
-      if (dEj <= c_armijo * sig * gtd) {
-        accepted = j;
-        dE = dEj;
-        break;
-      }
-      sig *= rho;
-    }
-  }
-  if (accepted >= 0) {
-    sc->sigma = sig;
-    sc->sigma_start = sigma0;
-    sc->dE += dE;
-    sc->ls_trials += accepted + 1;
-    sc->ls_fail = 0;
-  } else {
-    sc->sigma = 0.0;
-    double st = sc->sigma_start;
-    for (int j = 0; j < kLsTrials; ++j) st *= rho;
-    sc->sigma_start = st;
-    sc->ls_trials += kLsTrials;
-    sc->ls_fail += 1;
-  }
+  ls_select_block(dir_partials, nblk_dir, ls_partials, nblk_ls, sc, sigma0, rho, c_armijo);
 }
 
 void launch_ls_select(const double* dir_partials, int nblk_dir, const double* ls_partials, int nblk_ls,

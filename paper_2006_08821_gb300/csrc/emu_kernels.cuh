@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "emu_internal.h"
+#include "emu_reduce.cuh"
 
 namespace emu {
 
@@ -84,6 +85,49 @@ void launch_compose_F(int64_t m, const double* R, const double* s, double* F, cu
 
 constexpr int kGradNV = 1 + kK;        // gnorm2 + By
 constexpr int kLsNV = kLsTrials + 2;   // dPsi per trial + c<D,dD> + c|dD|^2
+
+// Armijo selection among the trial steps of one line-search pass, from the
+// block partials of g.d (direction kernel) and of the trial energies.
+__device__ __forceinline__ void ls_select_block(const double* dir_partials, int nblk_dir, const double* ls_partials, int nblk_ls,
+                                DevScalars* sc, double sigma0, double rho, double c_armijo) {
+  __shared__ double s_gtd[1], s_v[kLsNV];
+  block_sum_partials<1>(dir_partials, nblk_dir, s_gtd);
+  block_sum_partials<kLsNV>(ls_partials, nblk_ls, s_v);
+  if (threadIdx.x != 0) return;
+  const double gtd = s_gtd[0];
+  double v[kLsNV];
+  for (int k = 0; k < kLsNV; ++k) v[k] = s_v[k];
+  sc->gtd = gtd;
+  double sig = sc->sigma_start;
+  int accepted = -1;
+  double dE = 0.0;
+  if (gtd < 0.0) {
+    for (int j = 0; j < kLsTrials; ++j) {
+      const double dEj = v[j] + sig * v[kLsTrials] + 0.5 * sig * sig * v[kLsTrials + 1];
+      if (dEj <= c_armijo * sig * gtd) {
+        accepted = j;
+        dE = dEj;
+        break;
+      }
+      sig *= rho;
+    }
+  }
+  if (accepted >= 0) {
+    sc->sigma = sig;
+    sc->sigma_start = sigma0;
+    sc->dE += dE;
+    sc->ls_trials += accepted + 1;
+    sc->ls_fail = 0;
+  } else {
+    sc->sigma = 0.0;
+    double st = sc->sigma_start;
+    for (int j = 0; j < kLsTrials; ++j) st *= rho;
+    sc->sigma_start = st;
+    sc->ls_trials += kLsTrials;
+    sc->ls_fail += 1;
+  }
+}
+
 constexpr int kCapEntries = kK * kK;   // 48 x 48 partial capacitance
 
 }  // namespace emu

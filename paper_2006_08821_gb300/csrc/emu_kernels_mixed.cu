@@ -148,6 +148,15 @@ __global__ void __launch_bounds__(128, 4) k_grad_m(MixArgs a) {
   }
   block_reduce_write<1>(acc, a.partials + blockIdx.x);
   if (bad) atomicExch(&a.sc->nonfinite, 1);
+  // the last block to finish sums the squared gradient norm
+  if (last_block(&a.sc->ticket[kTicketGrad])) {
+    __shared__ double tot[1];
+    block_sum_partials<1>(a.partials, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      a.sc->gnorm2 = tot[0];
+      a.sc->ticket[kTicketGrad] = 0u;
+    }
+  }
 }
 
 void launch_grad_mixed(const MixArgs& a, int grid, cudaStream_t st) { k_grad_m<<<grid, 128, 0, st>>>(a); }
@@ -447,7 +456,8 @@ void launch_dir_mixed(const MixArgs& a, int grid, cudaStream_t st) { k_dir_m<<<g
 //   mu [ s <F - F^-T, d> + s^2 |d|^2 / 2 - s^2 e2 - s^3 det M + (x - log1p x) ]
 //   + lam/2 log1p(x) (2 ln J + log1p(x)) + ka (2 s (Fu).(du) + s^2 |du|^2),
 // with F - F^-T = R (2E + E^2) S^-1; plus the ACAP coefficients.
-__global__ void __launch_bounds__(128) k_ls_m(MixArgs a, double rho) {
+__global__ void __launch_bounds__(128) k_ls_m(MixArgs a, LsSelect sel) {
+  const double rho = sel.rho;
   const int64_t m = a.m;
   const double s0 = a.sc->sigma_start;
   double acc[kLsNV];
@@ -518,9 +528,16 @@ __global__ void __launch_bounds__(128) k_ls_m(MixArgs a, double rho) {
     }
   }
   block_reduce_write<kLsNV>(acc, a.partials + (size_t)blockIdx.x * kLsNV);
+  // the last block to finish sums every block's partials and selects the step
+  if (last_block(&a.sc->ticket[kTicketLs])) {
+    ls_select_block(sel.dir_partials, sel.nblk_dir, a.partials, gridDim.x, a.sc, sel.sigma0, sel.rho, sel.c_armijo);
+    if (threadIdx.x == 0) a.sc->ticket[kTicketLs] = 0u;
+  }
 }
 
-void launch_ls_mixed(const MixArgs& a, int grid, double rho, cudaStream_t st) { k_ls_m<<<grid, 128, 0, st>>>(a, rho); }
+void launch_ls_mixed(const MixArgs& a, int grid, const LsSelect& sel, cudaStream_t st) {
+  k_ls_m<<<grid, 128, 0, st>>>(a, sel);
+}
 
 // ------------------------------------------------------------ update ------
 // F' = R (S + s R^T d) = R (I + Y), Y = E + s R^T d; I + Y = Rx (I + E'):

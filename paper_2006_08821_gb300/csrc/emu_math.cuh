@@ -216,9 +216,10 @@ template <typename T> EMU_HD void stretch_gradient(const T* S, const T* Sinv, T 
 // ------------------------------------------------------ dense Cholesky ----
 // In-place lower Cholesky of an N x N SPD matrix (row-major full storage).
 // Returns false if a pivot is not positive.
-template <typename T, int N> EMU_HD bool chol(T* A) {
+template <typename T, int N> EMU_HD bool chol(T* A, T* idiag = nullptr) {
   // every loop has a fixed trip count (bounds as conditions), so full
-  // unrolling folds all indices and A stays in registers
+  // unrolling folds all indices and A stays in registers. idiag (optional)
+  // receives 1 / L_jj.
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < N; ++j) {
@@ -230,6 +231,7 @@ template <typename T, int N> EMU_HD bool chol(T* A) {
     d = d > T(0) ? sqrt(d) : T(1);
     A[N * j + j] = d;
     T id = T(1) / d;
+    if (idiag) idiag[j] = id;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       if (i > j) {
@@ -242,6 +244,18 @@ template <typename T, int N> EMU_HD bool chol(T* A) {
     }
   }
   return ok;
+}
+
+// Solve L x = b in place (L lower, row-major N x N, idiag = 1 / diag(L)).
+template <typename T, int N> EMU_HD void fwd_sub_inv(const T* L, const T* idiag, T* x) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T v = x[i];
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      if (k < i) v -= L[N * i + k] * x[k];
+    x[i] = v * idiag[i];
+  }
 }
 
 // Solve L x = b in place (L lower, row-major N x N).
@@ -344,14 +358,15 @@ template <typename T> EMU_HD void chart_factor(const T* R, const T* S, const T* 
       L2[6 * i + j] = acc;
       L2[6 * j + i] = acc;
     }
-  ok = chol<T, 6>(L2) && ok;
+  T id2[6];
+  ok = chol<T, 6>(L2, id2) && ok;
   // U = L2^-1 W (column by column forward substitution)
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
     T col[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) col[i] = Wf[9 * i + j];
-    fwd_sub<T, 6>(L2, col);
+    fwd_sub_inv<T, 6>(L2, id2, col);
 #pragma unroll
     for (int i = 0; i < 6; ++i) Wf[9 * i + j] = col[i];
   }

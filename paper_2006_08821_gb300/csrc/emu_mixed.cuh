@@ -43,7 +43,16 @@ struct MixArgs {
 
 void launch_grad_mixed(const MixArgs& a, int grid, cudaStream_t st);
 void launch_dir_mixed(const MixArgs& a, int grid, cudaStream_t st);
-void launch_ls_mixed(const MixArgs& a, int grid, double rho, cudaStream_t st);
+// Line-search constants and the direction kernel's g.d partials, for the
+// Armijo selection the last block of the line-search kernel performs.
+struct LsSelect {
+  const double* dir_partials;
+  int nblk_dir;
+  double sigma0, rho, c_armijo;
+};
+// Trial energies of one pass and, in its last block, the selected step
+// (k_ls_select's work); the gradient kernel likewise leaves ||g||^2 in sc.
+void launch_ls_mixed(const MixArgs& a, int grid, const LsSelect& sel, cudaStream_t st);
 void launch_update_mixed(const MixArgs& a, int grid, cudaStream_t st);
 void launch_rhs_state_mixed(const MixArgs& a, int grid, cudaStream_t st);
 // Capacitance partials C and B y on TF32 tensor cores (mma.sync), grid

@@ -33,12 +33,41 @@ __device__ __forceinline__ void block_sum_partials(const double* __restrict__ pa
   double v[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+  // eight strides of loads in flight at once, added in a fixed order
+  constexpr int U = 8;
+  const int step = blockDim.x;
+  int b = threadIdx.x;
+  for (; b + (U - 1) * step < nblk; b += U * step) {
+    double t[U][NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] += partials[(size_t)b * NV + k];
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) t[u][k] = __ldcg(partials + (size_t)(b + u * step) * NV + k);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) v[k] += t[u][k];
+  }
+  for (; b < nblk; b += step) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += __ldcg(partials + (size_t)b * NV + k);
   }
   block_reduce_write<NV>(v, out);
   __syncthreads();
+}
+
+// True in the block that finishes last among the grid's blocks (the pattern
+// of a threadfence reduction): each block makes its partial sums visible,
+// then takes a ticket; the block with the last ticket may read every
+// block's partials. The caller resets *ticket to 0 from that block.
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
 }
 
 }  // namespace emu
