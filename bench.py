@@ -250,7 +250,7 @@ def run_batch(args, emu, torch, rank, world, dist):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        stats = emu.batch_solve(solvers)
+        stats = emu.batch_solve(solvers, raise_on_error=False)
         torch.cuda.synchronize()
         return time.perf_counter() - t0, stats
 
@@ -260,14 +260,18 @@ def run_batch(args, emu, torch, rank, world, dist):
         dist.barrier()
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    times, tet_iters, iters, resid = [], 0.0, [], []
+    times, tet_iters, iters, resid, failed = [], 0.0, [], [], []
     for _ in range(args.steps):
         dt, stats = step()
         times.append(dt)
         its = np.array([st.newton_iters for st in stats], dtype=np.float64)
         tet_iters += float((m_each * its).sum())
         iters.append(int(its.sum()))
-        resid.append(max(st.rel_residual for st in stats))
+        ok = [st for st in stats if st.status == 0]
+        resid.append(max(st.rel_residual for st in ok) if ok else float("nan"))
+        failed.append([{"mesh": k, "tets": int(m_each[k]), "activation": float(meshes[k].activations[0][0]),
+                        "status": int(st.status), "newton_iters": int(st.newton_iters),
+                        "rel_residual": float(st.rel_residual)} for k, st in enumerate(stats) if st.status != 0])
     clk = clocks.stop()
     total = float(np.sum(times))
     if dist:
@@ -284,7 +288,8 @@ def run_batch(args, emu, torch, rank, world, dist):
                                "one emu_batch_solve per step, one stream per mesh",
                    "precision": args.precision, "l2": "inputs larger than L2; flushed between steps",
                    "tets": int(m_each.sum()), "meshes": len(meshes)},
-        "newton_iters_per_step": iters, "max_rel_residual": float(np.max(resid)), "setup_s": setup_s,
+        "newton_iters_per_step": iters, "max_rel_residual_converged": float(np.max(resid)),
+        "not_converged": failed[-1], "setup_s": setup_s,
         "roofline": None, "cpu_baseline": None,
         "e2e": {"value": value, "unit": "tet-iters/s", "h2d_bytes_per_step": int(8 * m_each.sum()), "d2h_bytes_per_step": 0},
         "clocks": clk,

@@ -188,7 +188,10 @@ int emu_set_activation_device(emu_handle* h, const double* a_device, int64_t cou
 /* Runs Newton iterations from the resident state (warm start) until the
  * relative residual reaches tol_rel_residual (Algorithm 1, Newton part).
  * ``stats`` may be NULL. Returns EMU_ERR_NOT_CONVERGED when max_newton is
- * reached; the state is then kept. */
+ * reached, or when the residual has stalled within 10x of the tolerance
+ * for 200 iterations (the rounding floor of the mixed path's FP32 per-tet
+ * arithmetic can sit there for activations near 0); the state is then kept
+ * and stats->rel_residual tells how close it got. */
 int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats);
 
 /* Solves ``count`` independent meshes (the c3 batch: Algorithm 1 per mesh,

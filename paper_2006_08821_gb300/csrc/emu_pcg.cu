@@ -430,7 +430,8 @@ template cudaError_t launch_pcg<float>(int, const PcgArgsT<float>&, int, cudaStr
 __global__ void __launch_bounds__(256) k_residual64(int64_t n, const int32_t* __restrict__ rowptr,
                                                     const int32_t* __restrict__ col, const double* __restrict__ val,
                                                     const double* __restrict__ b, const double* __restrict__ x,
-                                                    float* __restrict__ r32, double* __restrict__ partials) {
+                                                    float* __restrict__ r32, double* __restrict__ r64,
+                                                    double* __restrict__ partials) {
   __shared__ double sm[8 * 6];
   double loc[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
@@ -440,7 +441,8 @@ __global__ void __launch_bounds__(256) k_residual64(int64_t n, const int32_t* __
     for (int j = 0; j < 3; ++j) {
       const double bv = b[3 * v + j];
       const double rv = bv - acc[j];
-      r32[3 * v + j] = (float)rv;
+      if (r32) r32[3 * v + j] = (float)rv;
+      if (r64) r64[3 * v + j] = rv;
       loc[j] += rv * rv;
       loc[3 + j] += bv * bv;
     }
@@ -462,9 +464,22 @@ __global__ void __launch_bounds__(256) k_axpy_f2d(int64_t n3, const float* __res
 }
 
 cudaError_t launch_residual64(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* b,
-                              const double* x, float* r32, double* partials, int grid, double* out6, cudaStream_t st) {
-  k_residual64<<<grid, 256, 0, st>>>(n, rowptr, col, val, b, x, r32, partials);
+                              const double* x, float* r32, double* r64, double* partials, int grid, double* out6,
+                              cudaStream_t st) {
+  k_residual64<<<grid, 256, 0, st>>>(n, rowptr, col, val, b, x, r32, r64, partials);
   k_sum_partials6<<<1, 32, 0, st>>>(partials, grid, out6);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_axpy_d2d(int64_t n3, const double* __restrict__ e, double* __restrict__ x) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x)
+    x[k] += e[k];
+}
+
+cudaError_t launch_axpy_d2d(int64_t n3, const double* e, double* x, cudaStream_t st) {
+  int grid = (int)((n3 + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_axpy_d2d<<<grid, 256, 0, st>>>(n3, e, x);
   return cudaGetLastError();
 }
 

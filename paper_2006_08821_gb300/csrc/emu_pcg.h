@@ -61,11 +61,15 @@ cudaError_t launch_pcg32(const PcgArgsT<float>& args, const Pcg32Work& work, int
 // Per-device kernel attributes of the FP32 CG (before its first launch).
 cudaError_t prepare_pcg32();
 
-// FP64 residual r = b - K x (3 columns) with a float copy; out6 receives
-// sum |r_j|^2 (j < 3) and sum |b_j|^2 (3 + j).
+// FP64 residual r = b - K x (3 columns), written as float (r32) and/or double
+// (r64) when those are non-null; out6 receives sum |r_j|^2 (j < 3) and
+// sum |b_j|^2 (3 + j).
 cudaError_t launch_residual64(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* b,
-                              const double* x, float* r32, double* partials, int grid, double* out6, cudaStream_t st);
+                              const double* x, float* r32, double* r64, double* partials, int grid, double* out6,
+                              cudaStream_t st);
 // x += e (float correction into the FP64 iterate), 3n values.
 cudaError_t launch_axpy_f2d(int64_t n3, const float* e, double* x, cudaStream_t st);
+// x += e, 3n values (FP64).
+cudaError_t launch_axpy_d2d(int64_t n3, const double* e, double* x, cudaStream_t st);
 
 }  // namespace emu

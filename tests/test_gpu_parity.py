@@ -200,3 +200,16 @@ def test_affine_patch_on_gpu(emu):
     np.testing.assert_allclose(s.positions(), Q @ A.T + b, atol=1e-13)
     _, _, F = s.element_state()
     np.testing.assert_allclose(F, np.broadcast_to(F[0], F.shape), atol=1e-11)
+
+
+def test_fp64_weak_activation_matches_oracle(emu):
+    # a tiny activation: the deformation is a small fraction of the rest
+    # shape, so the exact coupling solve must be converged relative to the
+    # deformation, not to |b| (dominated by the rest shape)
+    mesh = box_beam(3, 3, 8, activation=0.002)
+    o, r = _oracle(mesh, 0.002)
+    s, st = _solve_gpu(emu, mesh, 0.002, tol=1e-10)
+    assert st.rel_residual <= 1e-10
+    disp = np.abs(r.q - mesh.rest_pos).max()
+    err = np.abs(s.positions() - r.q).max()
+    assert err <= 1e-6 * disp, (err, disp)
