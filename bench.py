@@ -45,6 +45,17 @@ from emu_inputs import batch_set, box_beam, mtu_for_tet_count, muscle_tendon_uni
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
+# DRAM bytes (read + write) per launch of a phase's kernel from one ncu
+# capture of the unchanged kernel (summaries under profiles/); None once the
+# kernel has changed since.
+NCU_TRAFFIC = {
+    "pcg": (15.78e6, "profiles/pcg32_kernel_mtu401920.md"),
+    "syrk": (183.11e6, "profiles/k_syrk_tc_mtu401920.md"),
+    "grad": (127.31e6, "profiles/k_grad_m_mtu401920.md"),
+    "dir": (229.04e6, "profiles/k_dir_m_mtu401920.md"),
+    "ls": (84.83e6, "profiles/k_ls_m_mtu401920.md"),
+}
+
 
 def hbm_peak():
     try:
@@ -493,8 +504,10 @@ def main():
         # bytes are summed over all its CG iterations
         bytes_per_launch = total_bytes / nl if name == "pcg" else total_bytes
         achieved = bytes_per_launch / (ms_tot / nl / 1e3) / 1e9
+        traffic = NCU_TRAFFIC.get(name) if (mixed and args.workload == "mtu") else None
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "frac": achieved / peak, "traffic": traffic[0] if traffic else None,
+                "traffic_source": traffic[1] if traffic else None, "peak_source": peak_kind,
                 "bytes_per_launch": bytes_per_launch, "avg_launch_ms": ms_tot / nl,
                 "share_of_device_time": ms_tot / max(1e-9, sum(v[0] for v in prof.values()))}
     line = {
