@@ -115,6 +115,7 @@ struct emu_handle {
   int32_t *slot_ptr = nullptr, *slot_idx = nullptr;
   // launch shapes
   int grid_tet = 1, grid_syrk = 1, grid_pcg3 = 1, grid_pcg16 = 1;
+  int grid_tet4 = 1;  // one wave of the 4-blocks-per-SM mixed gradient and line-search kernels
 
   // profiling: event pairs per phase, resolved at the next host sync
   struct Pending {
@@ -728,13 +729,14 @@ bool alloc_device(emu_handle* h, int64_t nnz) {
   }
   h->grid_tet = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 127) / 128), 8 * (int64_t)h->sms);
   h->grid_syrk = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 23) / 24), 2 * (int64_t)h->sms);
+  h->grid_tet4 = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 127) / 128), 4 * (int64_t)h->sms);
   h->grid_pcg3 = pcg_max_grid(3, n);
   h->grid_pcg16 = pcg_max_grid(16, n);
   const int pcg_part = std::max(h->grid_pcg3 * (4 * 3 + 3 * kModes), h->grid_pcg16 * 64);  // per-block partials
   const int64_t gpart = std::max<int64_t>(h->grid_tet * (int64_t)kLsNV, 256 * (int64_t)(2 * h->sms + 1));
   ok = ok && h->get(h->part_grad, gpart) && h->get(h->part_dir, h->grid_tet) && h->get(h->part_ls, h->grid_tet * kLsNV) &&
        h->get(h->part_pcg, std::max<int64_t>(pcg_part, 256 * (int64_t)(2 * h->sms + 1))) &&
-       h->get(h->cpart, (int64_t)h->grid_syrk * (kCapEntries + kK)) && h->get(h->z, kK) && h->get(h->cfull, kCapEntries + kK) && h->get(h->small, 256) &&
+       h->get(h->cpart, std::max<int64_t>(h->grid_syrk, kTcBlocksPerSM * (int64_t)h->sms) * (kCapEntries + kK)) && h->get(h->z, kK) && h->get(h->cfull, kCapEntries + kK) && h->get(h->small, 256) &&
        h->get(h->sc, 1) && h->get(h->bar, 1);
   if (h->mixed) ok = ok && h->get(h->val32, nnz) && h->get(h->ldinv32, n);
   ok = ok && h->get(h->rowptr, n + 1) && h->get(h->col, nnz) && h->get(h->val, nnz) && h->get(h->ldinv, n) &&
@@ -1195,7 +1197,7 @@ namespace {
 int enqueue_grad(emu_handle* h) {
   h->ph_begin();
   if (h->mixed)
-    launch_grad_mixed(h->margs(), h->grid_tet, h->st);
+    launch_grad_mixed(h->margs(), h->grid_tet4, h->st);
   else
     launch_grad<double>(h->args<double>(), h->grid_tet, h->st);
   h->ph_end(EMU_PHASE_GRAD, 1);
@@ -1217,7 +1219,7 @@ int enqueue_step(emu_handle* h) {
   h->ph_begin();
   int syrk_blocks = h->grid_syrk;
   if (h->mixed) {
-    syrk_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (h->m + 31) / 32), 2 * (int64_t)h->sms);
+    syrk_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (h->m + 31) / 32), kTcBlocksPerSM * (int64_t)h->sms);
     launch_syrk_tc(am, syrk_blocks, h->cpart, h->st);
   } else {
     launch_syrk<double>(a64, h->grid_syrk, h->cpart, h->st);
@@ -1251,7 +1253,7 @@ int enqueue_step(emu_handle* h) {
     sel.sigma0 = h->prm.ls_sigma0;
     sel.rho = h->prm.ls_rho;
     sel.c_armijo = h->prm.ls_c;
-    launch_ls_mixed(al, h->grid_tet, sel, h->st);
+    launch_ls_mixed(al, h->grid_tet4, sel, h->st);
     h->ph_end(EMU_PHASE_LS, 1);
   } else {
     TetArgs<double> al = a64;

@@ -212,7 +212,7 @@ constexpr size_t kTcRawBytes = sizeof(float) * kTcRawRows * kTcRL;
 constexpr size_t kTcSmem = kTcYBytes + 2 * kTcRawBytes;
 
 template <bool VEC>
-__global__ void __launch_bounds__(256) k_syrk_tc(MixArgs a, double* __restrict__ cpart) {
+__global__ void __launch_bounds__(256, kTcBlocksPerSM) k_syrk_tc(MixArgs a, double* __restrict__ cpart) {
   constexpr int CH = kTcCH, LD = kTcLD, RL = kTcRL;
   __shared__ const float* s_src[kTcRawRows];  // first element of each raw row
   extern __shared__ __align__(16) unsigned char smem_raw[];

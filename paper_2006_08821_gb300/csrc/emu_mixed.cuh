@@ -58,6 +58,8 @@ void launch_rhs_state_mixed(const MixArgs& a, int grid, cudaStream_t st);
 // Capacitance partials C and B y on TF32 tensor cores (mma.sync), grid
 // blocks striding over 32-tet chunks; cpart is entry-major (entry * grid + block).
 void launch_syrk_tc(const MixArgs& a, int grid, double* cpart, cudaStream_t st);
+// Blocks of the TC SYRK resident per SM (its launch bounds; grid = this x SMs).
+constexpr int kTcBlocksPerSM = 2;
 // Per-device kernel attributes of the TC SYRK (before its first launch).
 cudaError_t prepare_syrk_tc();
 void launch_update_verts_f(int64_t n, const DevScalars* sc, const float* dq, double* q, cudaStream_t st);
