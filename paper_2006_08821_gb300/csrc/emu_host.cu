@@ -50,6 +50,7 @@ struct emu_handle {
   int sms = 0;
   int kmodes = 16;
   bool mixed = false;
+  bool escalated = false;  // a mixed handle running the FP64 kernels for the rest of a solve
   std::vector<DevBuf> bufs;
 
   double mu_ref = 0, alpha = 0, kappa = 0;
@@ -484,8 +485,10 @@ cudaError_t run_pcg32(emu_handle* h, const float* rhs, float* x, double tol) {
 // refresh_converged and refresh_correction.
 constexpr int kRefreshRounds = 8;
 // a solve whose best residual is within kStallBand of the tolerance and has
-// not improved by 0.1 % for kStallIters iterations ends as not converged
+// not improved by 0.1 % for kEscalateIters iterations switches from the
+// mixed to the FP64 kernels; after kStallIters it ends as not converged
 constexpr double kStallBand = 10.0;
+constexpr int kEscalateIters = 50;
 constexpr int kStallIters = 200;
 
 int refresh_begin(emu_handle* h, double /*tol*/) {
@@ -1317,6 +1320,42 @@ int launch_iteration_graph(emu_handle* h) {
   h->launches += h->iter_graph_kernels;
   return 1;
 }
+void drop_iteration_graph(emu_handle* h) {
+  if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
+  h->iter_exec = nullptr;
+  h->iter_exec_dq = -1.0;
+}
+
+// Precision escalation of a mixed handle whose residual has stalled at the
+// rounding floor of its FP32 per-tet arithmetic: the state (quaternion, E)
+// is converted to (R, s) and the FP64 kernels take over for the rest of the
+// solve (their per-tet buffers are allocated on first use). Positions q are
+// FP64 on both paths. Returns false when it cannot (allocation failed).
+bool escalate(emu_handle* h) {
+  if (!h->mixed || h->escalated) return false;
+  if (!h->gam64) {
+    const int64_t m = h->m;
+    if (!(h->get(h->gam64, 48 * m) && h->get(h->y64, 9 * m) && h->get(h->d64, 9 * m) && h->get(h->Uw64, 54 * m)))
+      return false;
+    launch_gamma<double>(m, h->tet, h->Dinv, h->phi64, h->gam64, h->st);
+  }
+  launch_mixed_to_Rs(h->m, h->quat, h->E32, h->R, h->s, h->st);
+  if (cudaMemsetAsync(h->dq, 0, 24 * h->n, h->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return false;
+  drop_iteration_graph(h);
+  h->mixed = false;
+  h->escalated = true;
+  return true;
+}
+
+// Back to the mixed kernels at the end of an escalated solve.
+void deescalate(emu_handle* h) {
+  if (!h->escalated) return;
+  launch_Rs_to_mixed(h->m, h->R, h->s, h->quat, h->E32, h->st);
+  cudaMemsetAsync(h->dq32, 0, 12 * h->n, h->st);
+  drop_iteration_graph(h);
+  h->mixed = true;
+  h->escalated = false;
+}
 }  // namespace
 
 int task_step(SolveTask* t) {
@@ -1330,6 +1369,7 @@ int task_step(SolveTask* t) {
     return 1;
   };
   auto abort = [&](int rc) {
+    deescalate(h);
     t->status = rc;
     t->phase = SolveTask::DONE;
     return 0;
@@ -1414,10 +1454,22 @@ int task_step(SolveTask* t) {
         // (the rounding floor of the per-tet arithmetic, relative to a
         // normaliser that vanishes with the activation). Stop with the state
         // kept instead of spending the iteration budget.
-        if (t->res > tol && t->best_res <= kStallBand * tol && t->it - t->best_it >= kStallIters) {
-          t->status = fail(EMU_ERR_NOT_CONVERGED, "residual stalled above the tolerance");
-          t->phase = SolveTask::FINISH;
-          break;
+        if (t->res > tol && t->best_res <= kStallBand * tol) {
+          if (h->mixed && t->it - t->best_it >= kEscalateIters && escalate(h)) {
+            // finish in FP64 from an exact q, with a fresh line search
+            launch_ls_reset(h->sc, h->prm.ls_sigma0, h->st);
+            t->best_it = t->it;
+            t->since = h->prm.q_refresh;
+            t->ls_refreshed = t->ls_retried = false;
+            h->dq_tol_now = h->prm.dq_tol;
+            t->phase = SolveTask::TOP;
+            break;
+          }
+          if (t->it - t->best_it >= kStallIters) {
+            t->status = fail(EMU_ERR_NOT_CONVERGED, "residual stalled above the tolerance");
+            t->phase = SolveTask::FINISH;
+            break;
+          }
         }
         if (t->res <= tol) {
           if (t->since > 0) {  // confirm with an exact q before declaring convergence
@@ -1474,6 +1526,7 @@ int task_step(SolveTask* t) {
         break;
       }
       case SolveTask::FINISH: {
+        deescalate(h);
         if (cudaStreamSynchronize(h->st) != cudaSuccess) return abort(fail(EMU_ERR_CUDA, "cudaStreamSynchronize failed"));
         h->prof_flush();
         auto t1 = std::chrono::steady_clock::now();

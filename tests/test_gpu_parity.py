@@ -213,3 +213,20 @@ def test_fp64_weak_activation_matches_oracle(emu):
     disp = np.abs(r.q - mesh.rest_pos).max()
     err = np.abs(s.positions() - r.q).max()
     assert err <= 1e-6 * disp, (err, disp)
+
+
+def test_mixed_weak_activation_reaches_the_tolerance(emu):
+    # a = 0.0023 on a 38,880-tet beam: the mixed path's FP32 per-tet
+    # arithmetic stalls near 2e-6 relative to the activation-sized
+    # normaliser, so the solve finishes on the FP64 kernels
+    a = 0.002275510334493358
+    mesh = box_beam(12, 12, 45, activation=a)
+    s64, st64 = _solve_gpu(emu, mesh, a, precision=0, tol=1e-8)
+    s32, st32 = _solve_gpu(emu, mesh, a, precision=1, tol=1e-6)
+    assert st32.status == 0 and st32.rel_residual <= 1e-6
+    disp = np.abs(s64.positions() - mesh.rest_pos).max()
+    err = np.abs(s32.positions() - s64.positions()).max()
+    assert err <= 1e-4 * disp, (err, disp)
+    # the handle is back on its mixed state afterwards: a second frame runs
+    s32.set_activation(2 * a)
+    assert s32.solve().status == 0
