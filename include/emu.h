@@ -190,8 +190,10 @@ int emu_set_activation_device(emu_handle* h, const double* a_device, int64_t cou
  * ``stats`` may be NULL. Returns EMU_ERR_NOT_CONVERGED when max_newton is
  * reached, or when the residual has stalled within 10x of the tolerance
  * for 200 iterations (the rounding floor of the mixed path's FP32 per-tet
- * arithmetic can sit there for activations near 0); the state is then kept
- * and stats->rel_residual tells how close it got. */
+ * arithmetic can sit there for activations near 0, which is why a mixed
+ * solve that stalls within 10x of the tolerance first finishes on the FP64
+ * kernels); the state is then kept and stats->rel_residual tells how close
+ * it got. */
 int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats);
 
 /* Solves ``count`` independent meshes (the c3 batch: Algorithm 1 per mesh,
@@ -210,7 +212,9 @@ int emu_batch_solve(emu_handle* const* hs, int32_t count, emu_solve_stats* stats
 /* Upper bound of the device memory (bytes) that emu_create allocates for
  * this mesh and these parameters (the Laplacian is bounded by 16 entries per
  * tet). Validates like emu_create; needs a current CUDA device. Used by the
- * server's admission control. */
+ * server's admission control. A mixed-precision solve that escalates to the
+ * FP64 kernels (see emu_solve_quasistatic) allocates 960 more bytes per tet
+ * on first use. */
 int emu_required_bytes(const emu_mesh_desc* desc, const emu_params* params, size_t* bytes);
 
 /* ---------------------------------------------------------------- serving

@@ -528,11 +528,23 @@ bool refresh_converged(const emu_handle* h, double tol) {
   return done;
 }
 
-int refresh_correction(emu_handle* h) {
+// Relative tolerance of the next correction solve: just enough to bring
+// every column's residual to ``tol`` of its normaliser (with a 5x margin),
+// within what the correction's arithmetic can reach. Valid after the copy
+// of refresh_residual has completed.
+double refresh_round_tol(const emu_handle* h, double tol) {
+  const double* o = h->o6_host;
+  double need = 0.5;
+  for (int j = 0; j < 3; ++j)
+    if (o[j] > 0.0) need = std::min(need, 0.2 * tol * std::sqrt(o[8 + j] / o[j]));
+  return std::max(need, h->mixed ? 1e-6 : 1e-12);
+}
+
+int refresh_correction(emu_handle* h, double round_tol) {
   if (h->mixed) {
     EMU_CK(cudaMemsetAsync(h->e32, 0, 12 * h->n, h->st));
     h->ph_begin();
-    EMU_CK(run_pcg32(h, h->r32, h->e32, 1e-5));
+    EMU_CK(run_pcg32(h, h->r32, h->e32, round_tol));
     EMU_CK(launch_axpy_f2d(3 * h->n, h->e32, h->q, h->st));
     h->ph_end(EMU_PHASE_PCG, 2);
     return EMU_OK;
@@ -541,7 +553,7 @@ int refresh_correction(emu_handle* h) {
   double* e64 = h->b + 6 * h->n;
   EMU_CK(cudaMemsetAsync(e64, 0, 24 * h->n, h->st));
   h->ph_begin();
-  EMU_CK(launch_pcg<double>(3, h->pcg64(r64, e64, 1e-6), h->grid_pcg3, h->st));
+  EMU_CK(launch_pcg<double>(3, h->pcg64(r64, e64, round_tol), h->grid_pcg3, h->st));
   EMU_CK(launch_axpy_d2d(3 * h->n, e64, h->q, h->st));
   h->ph_end(EMU_PHASE_PCG, 2);
   return EMU_OK;
@@ -556,7 +568,7 @@ int refresh_q(emu_handle* h, double tol) {
     EMU_CK(cudaStreamSynchronize(h->st));
     h->prof_flush();
     if (refresh_converged(h, tol)) break;
-    rc = refresh_correction(h);
+    rc = refresh_correction(h, refresh_round_tol(h, tol));
     if (rc) return rc;
   }
   return EMU_OK;
@@ -1419,7 +1431,7 @@ int task_step(SolveTask* t) {
           t->phase = SolveTask::GRAD;
           break;
         }
-        rc = refresh_correction(h);
+        rc = refresh_correction(h, refresh_round_tol(h, h->q_tol));
         if (rc) return abort(rc);
         ++t->round;
         t->phase = SolveTask::REF_RES;
