@@ -256,7 +256,11 @@ class OracleResult:
 class EmuOracle:
     """Setup (Sec. 3.1-3.2.1) for one mesh; ``solve`` runs Algorithm 1."""
 
-    def __init__(self, mesh, params: OracleParams | None = None, modes: str = "eigsh"):
+    def __init__(self, mesh, params: OracleParams | None = None, modes: str = "eigsh", factor: bool = True):
+        """modes: "eigsh" (or a dense eigen-solve on small meshes) builds the
+        Eq. 9 basis, "none" skips it; factor=False skips the sparse LU of
+        Eq. 4. Without both, only the pointwise functions (Eq. 2, 5-7 at a
+        given F and q) are available: enough to check a large GPU result."""
         self.p = params or OracleParams()
         self.mesh = mesh
         Q = np.asarray(mesh.rest_pos, dtype=np.float64)
@@ -299,8 +303,11 @@ class EmuOracle:
         self.G_c = self.G[:, self.fixed_dofs].tocsr()
         self.w9 = np.repeat(self.w, 9)
         self.K = (self.G_f.T @ sp.diags(self.w9) @ self.G_f).tocsc()
-        self._lu = spla.splu(self.K)
+        self._lu = spla.splu(self.K) if factor else None
         self.Gc_qc = self.G_c @ self.q_c
+        if modes == "none":
+            self.k = 0
+            return
 
         # Eq. 9: lowest k eigenpairs of the ACAP matrix
         nf = self.free_dofs.size
