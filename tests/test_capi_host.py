@@ -69,7 +69,8 @@ def _desc(mesh):
 
 
 @pytest.mark.parametrize("mutate,code", [
-    ("bad_index", -1), ("no_pins", -1), ("bad_poisson", -1), ("bad_kmodes", -1),
+    ("bad_index", -1), ("no_pins", -1), ("bad_poisson", -1), ("bad_kmodes", -1), ("empty", -1),
+    ("nan_rest", -1), ("bad_material", -1),
 ])
 def test_create_rejects_invalid_input_before_touching_the_device(lib, mutate, code):
     from paper_2006_08821_gb300 import binding as B
@@ -80,9 +81,17 @@ def test_create_rejects_invalid_input_before_touching_the_device(lib, mutate, co
         mesh.tets[0, 0] = mesh.n_verts + 5
     if mutate == "bad_poisson":
         mesh.poisson = np.array([0.5])
+    if mutate == "nan_rest":
+        mesh.rest_pos = mesh.rest_pos.copy()
+        mesh.rest_pos[3, 1] = np.nan
+    if mutate == "bad_material":
+        mesh.material_id = mesh.material_id.copy()
+        mesh.material_id[0] = 7
     d, keep = _desc(mesh)
     if mutate == "no_pins":
         d.n_fixed = 0
+    if mutate == "empty":
+        d.n_tets = 0
     p = B.Params().to_c()
     if mutate == "bad_kmodes":
         p.k_modes = 50

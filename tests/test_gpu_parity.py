@@ -230,3 +230,50 @@ def test_mixed_weak_activation_reaches_the_tolerance(emu):
     # the handle is back on its mixed state afterwards: a second frame runs
     s32.set_activation(2 * a)
     assert s32.solve().status == 0
+
+
+# ------------------------------------------------------------- edge cases --
+def test_degenerate_tet_is_rejected_and_inverted_tets_are_reoriented(emu):
+    mesh = box_beam(2, 2, 3, activation=0.4)
+    flat = box_beam(2, 2, 3, activation=0.4)
+    flat.tets = flat.tets.copy()
+    t = flat.tets[5]
+    flat.rest_pos = flat.rest_pos.copy()
+    flat.rest_pos[t[3]] = flat.rest_pos[t[0]]  # two corners coincide
+    with pytest.raises(emu.EmuError) as e:
+        emu.Solver(flat, emu.Params())
+    assert e.value.code == -2  # EMU_ERR_DEGENERATE_TET
+    # the same mesh with half of its tets given in the other orientation
+    inv = box_beam(2, 2, 3, activation=0.4)
+    inv.tets = inv.tets.copy()
+    inv.tets[::2] = inv.tets[::2][:, [0, 2, 1, 3]]
+    s1, st1 = _solve_gpu(emu, mesh, 0.4, tol=1e-10)
+    s2, st2 = _solve_gpu(emu, inv, 0.4, tol=1e-10)
+    assert np.abs(s1.positions() - s2.positions()).max() <= 1e-12 * _diag(mesh)
+
+
+def test_invalid_activation_is_rejected_and_the_state_is_kept(emu):
+    mesh = box_beam(2, 2, 3, activation=0.4)
+    s, st = _solve_gpu(emu, mesh, 0.4, tol=1e-10)
+    q = s.positions()
+    for bad in (-0.1, np.nan, np.inf):
+        a = np.full(mesh.n_tets, 0.4)
+        a[3] = bad
+        with pytest.raises(emu.EmuError):
+            s.set_activation(a)
+    assert s.solve().newton_iters == 0  # still converged for a = 0.4
+    np.testing.assert_array_equal(s.positions(), q)
+
+
+def test_a_single_tet_with_one_pinned_face(emu):
+    # the smallest mesh: 4 vertices, 3 pinned; FP64 and mixed both converge
+    from emu_inputs import single_tet
+
+    mesh = single_tet()
+    mesh.fixed_verts = np.array([1, 2, 3], dtype=np.int32)
+    o, r = _oracle(mesh, mesh.activations[0])
+    for prec in (0, 1):
+        s, st = _solve_gpu(emu, mesh, mesh.activations[0], precision=prec, tol=1e-6 if prec else 1e-10)
+        assert st.status == 0
+        err = np.abs(s.positions() - r.q).max() / _diag(mesh)
+        assert err <= (1e-4 if prec else 1e-9), (prec, err)

@@ -60,3 +60,20 @@ def test_noalloc_coupling_solve_matches_solver_positions(emu, mesh_fn):
         outs.append(q)
     np.testing.assert_array_equal(outs[0], outs[1])
     s.close()
+
+
+def test_noalloc_rejects_a_mesh_larger_than_its_fixed_scratch(emu):
+    # 401,920 tets need 96 bytes per tet + 144 per vertex: more than the
+    # fixed 32 MiB array, so the call must refuse before touching memory
+    import torch
+
+    mesh = muscle_tendon_unit(frames=1)
+    s = emu.Solver(mesh, emu.Params(precision=emu.PRECISION_MIXED))
+    dev = torch.device("cuda:0")
+    tF = torch.zeros((mesh.n_tets, 9), dtype=torch.float64, device=dev)
+    tq = torch.zeros((mesh.n_verts, 3), dtype=torch.float64, device=dev)
+    rc = s.acap_solve_noalloc(tF.data_ptr(), tq.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == -1  # EMU_ERR_INVALID_ARG
+    assert b"32 MiB" in s.lib.emu_last_error()
+    assert torch.count_nonzero(tq).item() == 0
+    s.close()
