@@ -123,3 +123,16 @@ def test_server_calls_validate_their_arguments_without_a_device(lib):
     assert lib.emu_server_create(1 << 30, None, None, None) == B.EMU_ERR_INVALID_ARG
     assert lib.emu_server_destroy(None) == B.EMU_OK
     assert lib.emu_required_bytes(None, None, None) == B.EMU_ERR_INVALID_ARG
+
+
+def test_the_binding_fails_loudly_without_the_library(tmp_path):
+    # there is no CPU fallback: a missing library is an error, not a detour
+    from paper_2006_08821_gb300 import binding as B
+
+    saved = B._lib
+    B._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            B.load_library(str(tmp_path / "missing.so"))
+    finally:
+        B._lib = saved
