@@ -202,8 +202,10 @@ __device__ __forceinline__ void cp_async16(uint32_t saddr, const float* g, int b
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-constexpr int kTcCH = 32;              // tets per chunk
-constexpr int kTcKR = kTcCH * 6;       // 192 rows of Yh per chunk: 24 k-steps of 8, 3 per warp
+constexpr int kTcCH = 40;              // tets per chunk: 240 staging threads of 256
+constexpr int kTcKR = 256;             // rows of Yh per chunk (240 + 16 zero rows): 32 k-steps of 8, 4 per warp
+constexpr int kTcKS = kTcKR / 64;      // k-steps per warp
+constexpr int kTcSegs = kTcCH / 4;     // 16-byte segments of a raw row
 constexpr int kTcLD = kK + 4;          // padded row of Yh (TF32 bits)
 constexpr int kTcRawRows = 54 + 48 + 9 + 1;  // U, gamma, y, w of a chunk
 constexpr int kTcRL = kTcCH + 8;             // padded raw row (16-byte rows, conflict-free reads)
@@ -234,13 +236,13 @@ __global__ void __launch_bounds__(256, kTcBlocksPerSM) k_syrk_tc(MixArgs a, doub
   __syncthreads();
 
   // cp.async of one chunk's raw rows. VEC (rows 16-byte aligned, m % 4 == 0):
-  // 8 copies of 16 bytes per row; otherwise 32 copies of 4 bytes.
+  // CH / 4 copies of 16 bytes per row; otherwise CH copies of 4 bytes.
   auto issue = [&](int64_t ch, int buf) {
     const int64_t base = ch * CH;
     float* dst = sRaw + buf * (kTcRawRows * RL);
     if constexpr (VEC) {
-      for (int e = tid; e < kTcRawRows * 8; e += 256) {
-        const int row = e >> 3, seg = e & 7;
+      for (int e = tid; e < kTcRawRows * kTcSegs; e += 256) {
+        const int row = e / kTcSegs, seg = e % kTcSegs;
         const int64_t i = base + 4 * seg;
         const int64_t left = m - i;
         const int bytes = left >= 4 ? 16 : left > 0 ? 4 * (int)left : 0;
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(256, kTcBlocksPerSM) k_syrk_tc(MixArgs a, doub
       }
     } else {
       for (int e = tid; e < kTcRawRows * CH; e += 256) {
-        const int row = e >> 5, tt = e & 31;
+        const int row = e / CH, tt = e % CH;
         const int64_t i = base + tt;
         const bool ok = i < m;
         cp_async4((uint32_t)__cvta_generic_to_shared(dst + row * RL + tt), s_src[row] + (ok ? i : 0), ok);
@@ -257,8 +259,10 @@ __global__ void __launch_bounds__(256, kTcBlocksPerSM) k_syrk_tc(MixArgs a, doub
     }
   };
 
-  // staging role: threads 0..191 own (tet slot stt = tid / 6, row k = tid % 6)
+  // staging role: threads 0..6 CH - 1 own (tet slot stt = tid / 6, row k = tid % 6);
+  // rows 6 CH .. kTcKR - 1 of Yh stay zero
   const int stt = tid / 6, sk = tid % 6;
+  for (int e = 6 * CH * LD + tid; e < kTcKR * LD; e += 256) sY[e] = 0u;
   float acc[12][4];
 #pragma unroll
   for (int t = 0; t < 12; ++t)
@@ -305,8 +309,8 @@ __global__ void __launch_bounds__(256, kTcBlocksPerSM) k_syrk_tc(MixArgs a, doub
     }
     __syncthreads();
 #pragma unroll
-    for (int ks = 0; ks < 3; ++ks) {
-      const int k0 = (warp * 3 + ks) * 8;
+    for (int ks = 0; ks < kTcKS; ++ks) {
+      const int k0 = (warp * kTcKS + ks) * 8;
       uint32_t af[3][4], bf[6][2];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
