@@ -287,24 +287,32 @@ __global__ void __launch_bounds__(256, kTcBlocksPerSM) k_syrk_tc(MixArgs a, doub
     if (tid < 6 * CH) {
       // Yh[tt*6 + k][16 r + j] = sqrt(w) sum_b U[k][3r+b] gam_j[b]
       const float* raw = sRaw + (it & 1) * (kTcRawRows * RL) + stt;
-      float u9[9];
-#pragma unroll
-      for (int c = 0; c < 9; ++c) u9[c] = raw[(9 * sk + c) * RL];
       const float wi = raw[111 * RL];
       const float sw = sqrtf(wi);
+      float u9[9];  // sqrt(w) U[k][:]
+#pragma unroll
+      for (int c = 0; c < 9; ++c) u9[c] = sw * raw[(9 * sk + c) * RL];
       const float y0 = wi * raw[(102 + 3 * br) * RL];
       const float y1 = wi * raw[(102 + 3 * br + 1) * RL];
       const float y2 = wi * raw[(102 + 3 * br + 2) * RL];
-      uint32_t* row = sY + (stt * 6 + sk) * LD;
+      uint32_t* row = sY + (stt * 6 + sk) * LD;  // 16-byte aligned (LD = 52)
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float g0 = raw[(54 + 3 * j) * RL];
-        const float g1 = raw[(54 + 3 * j + 1) * RL];
-        const float g2 = raw[(54 + 3 * j + 2) * RL];
+      for (int jq = 0; jq < 4; ++jq) {  // four j at a time: 16-byte stores
+        uint32_t v[3][4];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) row[16 * r + j] = to_tf32(sw * (u9[3 * r] * g0 + u9[3 * r + 1] * g1 + u9[3 * r + 2] * g2));
-        const float byj = y0 * g0 + y1 * g1 + y2 * g2;
-        by8[j & 7] += ((j >> 3) == bh) ? byj : 0.f;
+        for (int t = 0; t < 4; ++t) {
+          const int j = 4 * jq + t;
+          const float g0 = raw[(54 + 3 * j) * RL];
+          const float g1 = raw[(54 + 3 * j + 1) * RL];
+          const float g2 = raw[(54 + 3 * j + 2) * RL];
+#pragma unroll
+          for (int r = 0; r < 3; ++r) v[r][t] = to_tf32(u9[3 * r] * g0 + u9[3 * r + 1] * g1 + u9[3 * r + 2] * g2);
+          const float byj = y0 * g0 + y1 * g1 + y2 * g2;
+          by8[j & 7] += ((j >> 3) == bh) ? byj : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          *reinterpret_cast<uint4*>(row + 16 * r + 4 * jq) = make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]);
       }
     }
     __syncthreads();
