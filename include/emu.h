@@ -125,7 +125,7 @@ typedef struct {
  *   dq_tol          relative residual of the per-iteration solve for the
  *                   change of q along the search direction (q*(F + s d) =
  *                   q + s dq, q* being affine); q itself is then updated by
- *                   linearity (default 3e-2). After a line search fails,
+ *                   linearity (default 5e-2). After a line search fails,
  *                   q is re-solved and dq is solved to the exact-solve
  *                   tolerance for the rest of the call.
  *   q_refresh       every q_refresh iterations, and before convergence is

@@ -203,7 +203,7 @@ class Params:
     precision: int = PRECISION_FP64
     mode_iters: int = 4
     seed: int = 12345
-    dq_tol: float = 3e-2
+    dq_tol: float = 5e-2
     q_refresh: int = 32
 
     def to_c(self) -> emu_params:

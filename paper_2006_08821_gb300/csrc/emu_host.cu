@@ -93,7 +93,7 @@ struct emu_handle {
   float* part32 = nullptr;
   int grid32 = 0, rpt32 = 0;
   double q_tol = 1e-8;
-  double dq_tol_now = 3e-2;  // dq tolerance of the current solve call
+  double dq_tol_now = 5e-2;  // dq tolerance of the current solve call
   double *part_grad = nullptr, *part_dir = nullptr, *part_ls = nullptr, *part_pcg = nullptr, *cpart = nullptr;
   double* z = nullptr;
   double* cfull = nullptr;  // summed capacitance entries
@@ -823,7 +823,7 @@ void emu_default_params(emu_params* p) {
   p->pcg_max = 5000;
   p->precision = EMU_PRECISION_FP64;
   p->mode_iters = 4;
-  p->dq_tol = 3e-2;
+  p->dq_tol = 5e-2;
   p->q_refresh = 32;
   p->seed = 12345;
 }
