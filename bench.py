@@ -252,6 +252,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def make_params(emu, args, mixed):
+    """Solver parameters of a bench leg: tolerance, precision and the first
+    line-search trial step (``--ls-sigma0``; the batch starts every mesh from
+    rest, where sigma0 = 1 measured faster than the default 2)."""
+    p = emu.Params(tol_rel_residual=args.tol, precision=emu.PRECISION_MIXED if mixed else emu.PRECISION_FP64)
+    if args.ls_sigma0 is not None:
+        p.ls_sigma0 = args.ls_sigma0
+    elif args.workload == "batch":
+        p.ls_sigma0 = 1.0
+    return p
+
+
 def _finish_line(line, rank, dist):
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -266,7 +278,7 @@ def run_batch(args, emu, torch, rank, world, dist):
     host clock spans the whole batch (synchronized on both sides)."""
     meshes = batch_set(count=args.meshes, seed=3)
     mixed = args.precision == "mixed"
-    params = emu.Params(tol_rel_residual=args.tol, precision=emu.PRECISION_MIXED if mixed else emu.PRECISION_FP64)
+    params = make_params(emu, args, mixed)
     t_setup = time.perf_counter()
     streams, solvers = [], []
     for mesh in meshes:
@@ -325,7 +337,7 @@ def run_batch(args, emu, torch, rank, world, dist):
                                f"(sum {int(m_each.sum())} tets), activation U[0,1], from rest, rel residual {args.tol:g}, "
                                "one emu_batch_solve per step, one stream per mesh",
                    "precision": args.precision, "l2": "inputs larger than L2; flushed between steps",
-                   "tets": int(m_each.sum()), "meshes": len(meshes)},
+                   "tets": int(m_each.sum()), "meshes": len(meshes), "ls_sigma0": params.ls_sigma0},
         "newton_iters_per_step": iters, "max_rel_residual_converged": float(np.max(resid)),
         "not_converged": failed[-1], "setup_s": setup_s,
         "roofline": None, "cpu_baseline": None,
@@ -351,7 +363,7 @@ def run_serve(args, emu, torch, rank, world, dist):
         acts = np.stack([muscle * r["a_max"] * (f + 1) / fr for f in range(fr)])
         built.append((r, mesh, acts))
     mixed = args.precision == "mixed"
-    params = emu.Params(tol_rel_residual=args.tol, precision=emu.PRECISION_MIXED if mixed else emu.PRECISION_FP64)
+    params = make_params(emu, args, mixed)
     srv = emu.Server(int(args.budget_gb * (1 << 30)), params)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.synchronize()
@@ -388,7 +400,7 @@ def run_serve(args, emu, torch, rank, world, dist):
         "config": {"workload": f"serving: first {len(built)} requests of a Poisson stream at {args.rate:g}/s, "
                                "muscle-tendon units log-uniform 1k-200k tets, 1-30 frames, tendon U[0,0.2], "
                                f"budget {args.budget_gb:g} GB, rel residual {args.tol:g}",
-                   "precision": args.precision, "requests": len(built),
+                   "precision": args.precision, "requests": len(built), "ls_sigma0": params.ls_sigma0,
                    "tets_mean": float(np.mean([mm.n_tets for _, mm, _ in built]))},
         "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
         "failed_requests": bad, "makespan_s": makespan,
@@ -416,6 +428,9 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
+    ap.add_argument("--ls-sigma0", type=float, default=None,
+                    help="first line-search trial step (default: 1 for the batch, whose meshes start from rest; "
+                         "the library default 2 for warm-started frames)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -453,7 +468,7 @@ def main():
         raise SystemExit(f"workload has {frames} frames; warmup + steps must be <= {frames - 1 - n_prof}")
     mixed = args.precision == "mixed"
     stream = torch.cuda.Stream()
-    params = emu.Params(tol_rel_residual=args.tol, precision=emu.PRECISION_MIXED if mixed else emu.PRECISION_FP64)
+    params = make_params(emu, args, mixed)
     t_setup = time.perf_counter()
     solver = emu.Solver(mesh, params, stream=stream.cuda_stream, allocator=emu.TorchAllocator(local))
     setup_s = time.perf_counter() - t_setup
@@ -542,7 +557,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "l2": f"flushed ({args.flush_mb} MB write) between steps",
-                   "tets": m, "verts": n},
+                   "tets": m, "verts": n, "ls_sigma0": params.ls_sigma0},
         "ms_per_converged_frame_p50": float(np.median(frame_ms)),
         "frame_ms_p99": float(np.percentile(frame_ms, 99)),
         "newton_iters_per_frame": [int(x) for x in iters],

@@ -87,7 +87,10 @@ constexpr int kGradNV = 1 + kK;        // gnorm2 + By
 constexpr int kLsNV = kLsTrials + 2;   // dPsi per trial + c<D,dD> + c|dD|^2
 
 // Armijo selection among the trial steps of one line-search pass, from the
-// block partials of g.d (direction kernel) and of the trial energies.
+// block partials of g.d (direction kernel) and of the trial energies. All
+// kLsTrials steps sigma_start * rho^j are evaluated in the same pass anyway,
+// so of those that satisfy the Armijo condition the one with the largest
+// energy decrease is taken (not merely the first).
 __device__ __forceinline__ void ls_select_block(const double* dir_partials, int nblk_dir, const double* ls_partials, int nblk_ls,
                                 DevScalars* sc, double sigma0, double rho, double c_armijo) {
   __shared__ double s_gtd[1], s_v[kLsNV];
@@ -102,15 +105,17 @@ __device__ __forceinline__ void ls_select_block(const double* dir_partials, int 
   int accepted = -1;
   double dE = 0.0;
   if (gtd < 0.0) {
+    double s_j = sig, best_sig = sig;
     for (int j = 0; j < kLsTrials; ++j) {
-      const double dEj = v[j] + sig * v[kLsTrials] + 0.5 * sig * sig * v[kLsTrials + 1];
-      if (dEj <= c_armijo * sig * gtd) {
+      const double dEj = v[j] + s_j * v[kLsTrials] + 0.5 * s_j * s_j * v[kLsTrials + 1];
+      if (dEj <= c_armijo * s_j * gtd && (accepted < 0 || dEj < dE)) {
         accepted = j;
         dE = dEj;
-        break;
+        best_sig = s_j;
       }
-      sig *= rho;
+      s_j *= rho;
     }
+    sig = best_sig;
   }
   if (accepted >= 0) {
     sc->sigma = sig;
