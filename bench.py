@@ -253,14 +253,11 @@ def run_reference(args, rank, world):
 
 
 def make_params(emu, args, mixed):
-    """Solver parameters of a bench leg: tolerance, precision and the first
-    line-search trial step (``--ls-sigma0``; the batch starts every mesh from
-    rest, where sigma0 = 1 measured faster than the default 2)."""
+    """Solver parameters of a bench leg: tolerance, precision and, with
+    ``--ls-sigma0``, the first line-search trial step (else the library's)."""
     p = emu.Params(tol_rel_residual=args.tol, precision=emu.PRECISION_MIXED if mixed else emu.PRECISION_FP64)
     if args.ls_sigma0 is not None:
         p.ls_sigma0 = args.ls_sigma0
-    elif args.workload == "batch":
-        p.ls_sigma0 = 1.0
     return p
 
 
@@ -429,8 +426,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--ls-sigma0", type=float, default=None,
-                    help="first line-search trial step (default: 1 for the batch, whose meshes start from rest; "
-                         "the library default 2 for warm-started frames)")
+                    help="first line-search trial step (default: the library's, 2)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

@@ -193,11 +193,15 @@ int emu_set_activation_device(emu_handle* h, const double* a_device, int64_t cou
  * relative residual reaches tol_rel_residual (Algorithm 1, Newton part).
  * ``stats`` may be NULL. Returns EMU_ERR_NOT_CONVERGED when max_newton is
  * reached, or when the residual has stalled within 10x of the tolerance
- * for 200 iterations (the rounding floor of the mixed path's FP32 per-tet
- * arithmetic can sit there for activations near 0, which is why a mixed
- * solve that stalls within 10x of the tolerance first finishes on the FP64
- * kernels); the state is then kept and stats->rel_residual tells how close
- * it got. */
+ * for 200 iterations; the state is then kept and stats->rel_residual tells
+ * how close it got. Before that, a solve stalled there for 50 iterations
+ * tries three remedies in turn: the first trial step drops from ls_sigma0
+ * to 1 (longer steps can make the gradient zig-zag), a mixed solve
+ * finishes on the FP64 kernels (the rounding floor of FP32 per-tet
+ * arithmetic can sit above the tolerance for activations near 0), then dq
+ * is solved to 1e-2 * dq_tol (q drifts from q*(F) between exact re-solves
+ * when dq is loose). The first and last hold for every later solve on the
+ * handle until emu_reset. */
 int emu_solve_quasistatic(emu_handle* h, emu_solve_stats* stats);
 
 /* Solves ``count`` independent meshes (the c3 batch: Algorithm 1 per mesh,

@@ -94,6 +94,8 @@ struct emu_handle {
   int grid32 = 0, rpt32 = 0;
   double q_tol = 1e-8;
   double dq_tol_now = 5e-2;  // dq tolerance of the current solve call
+  double dq_tol_base = 0.0;  // tighter dq tolerance a stalled solve settled on (0: params.dq_tol)
+  double sigma0_now = 1.0;   // first line-search trial: params.ls_sigma0, or 1 after a stall
   double *part_grad = nullptr, *part_dir = nullptr, *part_ls = nullptr, *part_pcg = nullptr, *cpart = nullptr;
   double* z = nullptr;
   double* cfull = nullptr;  // summed capacitance entries
@@ -106,6 +108,7 @@ struct emu_handle {
   // one Newton iteration (direction .. update, next gradient) as a CUDA graph
   cudaGraphExec_t iter_exec = nullptr;
   double iter_exec_dq = -1.0;      // dq tolerance the graph was captured with
+  double iter_exec_sigma0 = -1.0;  // and first trial step
   bool graphs_ok = true;           // false once a capture failed (direct launches)
   int64_t iter_graph_kernels = 0;  // kernel launches in one graph launch
   GridBarrier* bar = nullptr;
@@ -485,8 +488,9 @@ cudaError_t run_pcg32(emu_handle* h, const float* rhs, float* x, double tol) {
 // refresh_converged and refresh_correction.
 constexpr int kRefreshRounds = 8;
 // a solve whose best residual is within kStallBand of the tolerance and has
-// not improved by 0.1 % for kEscalateIters iterations switches from the
-// mixed to the FP64 kernels; after kStallIters it ends as not converged
+// not improved by 0.1 % for kEscalateIters iterations shortens its first
+// trial step to 1, or else switches from the mixed to the FP64 kernels, or
+// else tightens dq; after kStallIters with none left it ends as not converged
 constexpr double kStallBand = 10.0;
 constexpr int kEscalateIters = 50;
 constexpr int kStallIters = 200;
@@ -871,6 +875,7 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
   emu_handle* h = new (std::nothrow) emu_handle();
   if (!h) return fail(EMU_ERR_OOM, "host allocation failed");
   h->prm = prm;
+  h->sigma0_now = prm.ls_sigma0;
   h->st = (cudaStream_t)stream;
   if (alloc && alloc->alloc && alloc->free) {
     h->alloc = *alloc;
@@ -1265,7 +1270,7 @@ int enqueue_step(emu_handle* h) {
     LsSelect sel;  // the line-search kernel's last block selects the step
     sel.dir_partials = h->part_dir;
     sel.nblk_dir = h->grid_tet;
-    sel.sigma0 = h->prm.ls_sigma0;
+    sel.sigma0 = h->sigma0_now;
     sel.rho = h->prm.ls_rho;
     sel.c_armijo = h->prm.ls_c;
     launch_ls_mixed(al, h->grid_tet4, sel, h->st);
@@ -1276,7 +1281,7 @@ int enqueue_step(emu_handle* h) {
     launch_ls<double>(al, h->grid_tet, h->prm.ls_rho, h->st);
     h->ph_end(EMU_PHASE_LS, 1);
     h->ph_begin();
-    launch_ls_select(h->part_dir, h->grid_tet, h->part_ls, h->grid_tet, h->sc, h->prm.ls_sigma0, h->prm.ls_rho,
+    launch_ls_select(h->part_dir, h->grid_tet, h->part_ls, h->grid_tet, h->sc, h->sigma0_now, h->prm.ls_rho,
                      h->prm.ls_c, h->st);
     h->ph_end(EMU_PHASE_SMALL, 1);
   }
@@ -1293,12 +1298,12 @@ int enqueue_step(emu_handle* h) {
   return EMU_OK;
 }
 // Enqueues enqueue_step + enqueue_grad as one CUDA graph launch (captured
-// on first use and again when the dq tolerance changes). Returns 1 when the
+// on first use and again when the dq tolerance or first trial step changes). Returns 1 when the
 // graph was launched, 0 when the caller must enqueue directly (profiling
 // on, the legacy default stream, or a capture that failed).
 int launch_iteration_graph(emu_handle* h) {
   if (!h->graphs_ok || h->prof_on || h->st == nullptr) return 0;
-  if (!h->iter_exec || h->iter_exec_dq != h->dq_tol_now) {
+  if (!h->iter_exec || h->iter_exec_dq != h->dq_tol_now || h->iter_exec_sigma0 != h->sigma0_now) {
     if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
     h->iter_exec = nullptr;
     if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -1323,6 +1328,7 @@ int launch_iteration_graph(emu_handle* h) {
     cudaGraphDestroy(g);
     h->iter_exec = ex;
     h->iter_exec_dq = h->dq_tol_now;
+    h->iter_exec_sigma0 = h->sigma0_now;
   }
   if (cudaGraphLaunch(h->iter_exec, h->st) != cudaSuccess) {
     cudaGetLastError();
@@ -1398,12 +1404,12 @@ int task_step(SolveTask* t) {
         }
         DevScalars init;
         memset(&init, 0, sizeof(init));
-        init.sigma_start = h->prm.ls_sigma0;
+        init.sigma_start = h->sigma0_now;
         if (cudaMemcpyAsync(h->sc, &init, sizeof(init), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
           return abort(fail(EMU_ERR_CUDA, "cudaMemcpyAsync failed"));
         t->gnorm_ref = h->gref > h->floor ? h->gref : 0.0;
         t->since = h->prm.q_refresh;  // iterations since q was last solved exactly
-        h->dq_tol_now = h->prm.dq_tol;
+        h->dq_tol_now = h->dq_tol_base > 0.0 ? h->dq_tol_base : h->prm.dq_tol;
         t->phase = SolveTask::TOP;
         break;
       }
@@ -1462,20 +1468,39 @@ int task_step(SolveTask* t) {
           t->best_res = t->res;
           t->best_it = t->it;
         }
-        // Stalled just above the tolerance: the residual has stopped falling
-        // (the rounding floor of the per-tet arithmetic, relative to a
-        // normaliser that vanishes with the activation). Stop with the state
-        // kept instead of spending the iteration budget.
+        // Stalled just above the tolerance: the residual has stopped falling.
+        // Three causes are known, each with a remedy tried in turn before the
+        // solve gives up with the state kept: trial steps longer than the
+        // quasi-Newton step, which the energy test accepts while the gradient
+        // zig-zags (first trial 1 from then on), the rounding floor of the
+        // FP32 per-tet arithmetic relative to a normaliser that vanishes with
+        // the activation (finish on the FP64 kernels), and q drifting from
+        // q*(F) between exact re-solves when dq is solved loosely and the
+        // steps are long (solve dq 100x tighter). The first and last persist
+        // into later solves on the handle.
         if (t->res > tol && t->best_res <= kStallBand * tol) {
-          if (h->mixed && t->it - t->best_it >= kEscalateIters && escalate(h)) {
-            // finish in FP64 from an exact q, with a fresh line search
-            launch_ls_reset(h->sc, h->prm.ls_sigma0, h->st);
-            t->best_it = t->it;
-            t->since = h->prm.q_refresh;
-            t->ls_refreshed = t->ls_retried = false;
-            h->dq_tol_now = h->prm.dq_tol;
-            t->phase = SolveTask::TOP;
-            break;
+          if (t->it - t->best_it >= kEscalateIters) {
+            const double dq_tight = std::max(h->q_tol, 1e-2 * h->prm.dq_tol);
+            bool restart = false;
+            if (h->sigma0_now > 1.0) {
+              h->sigma0_now = 1.0;
+              restart = true;
+            } else if (h->mixed && escalate(h)) {
+              h->dq_tol_now = h->dq_tol_base > 0.0 ? h->dq_tol_base : h->prm.dq_tol;
+              restart = true;
+            } else if (h->dq_tol_now > dq_tight) {
+              // later solves on this handle (the next frames) start tight
+              h->dq_tol_now = h->dq_tol_base = dq_tight;
+              restart = true;
+            }
+            if (restart) {  // from an exact q, with a fresh line search
+              launch_ls_reset(h->sc, h->sigma0_now, h->st);
+              t->best_it = t->it;
+              t->since = h->prm.q_refresh;
+              t->ls_refreshed = t->ls_retried = false;
+              t->phase = SolveTask::TOP;
+              break;
+            }
           }
           if (t->it - t->best_it >= kStallIters) {
             t->status = fail(EMU_ERR_NOT_CONVERGED, "residual stalled above the tolerance");
@@ -1499,7 +1524,7 @@ int task_step(SolveTask* t) {
         // large error in the K-norm). Re-solve q exactly after two rejected
         // passes, and restart the line search.
         if (hs.ls_fail >= 2 && t->since > 0 && !t->ls_refreshed) {
-          launch_ls_reset(h->sc, h->prm.ls_sigma0, h->st);
+          launch_ls_reset(h->sc, h->sigma0_now, h->st);
           t->since = h->prm.q_refresh;
           t->ls_refreshed = true;
           t->phase = SolveTask::TOP;
@@ -1509,7 +1534,7 @@ int task_step(SolveTask* t) {
           if (!t->ls_retried) {
             // still no step with an exact q: solve dq tightly from now on
             // (q then stays exact along the steps) and give it one more run
-            launch_ls_reset(h->sc, h->prm.ls_sigma0, h->st);
+            launch_ls_reset(h->sc, h->sigma0_now, h->st);
             if (t->since > 0) t->since = h->prm.q_refresh;
             h->dq_tol_now = h->q_tol;
             t->ls_retried = true;
@@ -1708,6 +1733,8 @@ int emu_reset(emu_handle* h) {
   if (!h) return fail(EMU_ERR_INVALID_ARG, "NULL handle");
   int rc = set_rest_state(h);
   if (rc) return rc;
+  h->dq_tol_base = 0.0;
+  h->sigma0_now = h->prm.ls_sigma0;
   EMU_CK(cudaMemcpyAsync(h->q, h->q0, 24 * h->n, cudaMemcpyDeviceToDevice, h->st));
   EMU_CK(cudaStreamSynchronize(h->st));
   return EMU_OK;

@@ -12,7 +12,7 @@ stationary point of Eq. 5.
 import numpy as np
 import pytest
 
-from emu_inputs import box_beam, muscle_tendon_unit
+from emu_inputs import box_beam, mtu_for_tet_count, muscle_tendon_unit
 from oracle import EmuOracle, OracleParams, element_terms_s, lame, stretch_from_s
 
 pytestmark = pytest.mark.gpu
@@ -230,6 +230,21 @@ def test_mixed_weak_activation_reaches_the_tolerance(emu):
     # the handle is back on its mixed state afterwards: a second frame runs
     s32.set_activation(2 * a)
     assert s32.solve().status == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_stalled_solve_recovers(emu, precision):
+    # a 1,320-tet muscle-tendon unit (tendon 7.8 %) at a = 0.0328 from rest:
+    # with trial steps from 2 and dq solved to 5e-2 between exact re-solves
+    # the residual stalls near 1e-6 in both precisions (without the stall
+    # remedies this ended as not converged); after the first trial step
+    # drops to 1 the solve reaches the tolerance
+    mesh = mtu_for_tet_count(1767.2392638934577, tendon_frac=0.078437782739324, seed=1882127289)
+    a = (mesh.material_id == 0) * (0.9176424148326532 / 28)
+    s, st = _solve_gpu(emu, mesh, a, precision=precision, tol=1e-6, ls_sigma0=2.0)
+    assert st.status == 0 and st.rel_residual <= 1e-6
+    assert np.all(np.isfinite(s.positions()))
+    s.close()
 
 
 # ------------------------------------------------------------- edge cases --
