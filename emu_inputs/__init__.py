@@ -15,6 +15,7 @@ from .meshes import (  # noqa: F401
     batch_set,
     request_stream,
     single_tet,
+    arm_assembly,
     MUSCLE,
     TENDON,
     BONE,

@@ -55,6 +55,10 @@ class MeshSpec:
     activations: np.ndarray
     fixed_pos: np.ndarray | None = None
     bone_id: np.ndarray | None = None
+    # joints between bones: dicts with "type" ("hinge" or "ball"), "bones"
+    # (b1, b2), "point" (3,) metres, and for a hinge "axis" (3,) unit and
+    # "half_length" (metres; the hinge's two points are point +- half_length axis)
+    joints: list | None = None
     meta: dict = dataclasses.field(default_factory=dict)
 
     @property
@@ -267,3 +271,107 @@ def request_stream(rate_hz=200.0, horizon_s=60.0, seed=4, t_min=1e3, t_max=2e5, 
         if max_requests is not None and len(reqs) >= max_requests:
             break
     return reqs
+
+
+def arm_assembly(bone_w=12, bone_len=58, r0=32.0, gap_x=1, h=2.5e-3, frames=120, a_max=1.0,
+                 youngs_muscle=6e5, youngs_tendon=1e8, youngs_bone=1e10, poisson=0.45,
+                 poisson_bone=0.3, name=None):
+    """Arm-like assembly: two box bones, a hinge between them, and a fusiform
+    muscle spanning them (the setting of Sec. 3.3 of the paper).
+
+    One cube grid of edge h, every size below in cells:
+
+    * bone 1 occupies x in [0, bone_w), y in [y0, y0 + bone_w), z in
+      [0, bone_len); bone 2 the same x, y range and z in [bone_len + 1,
+      2 bone_len + 1): the bones are collinear along z with a one-cell gap,
+      so they share no vertex;
+    * the muscle is a spindle about the line x = bone_w + gap_x + r0,
+      y = ny / 2, from z_a = bone_len / 2 (mid bone 1) to z_b = bone_len +
+      1 + bone_len / 2 (mid bone 2), of radius r(t) = r0 (0.3 + 0.7 sin pi t),
+      t = (z - z_a) / (z_b - z_a), by cell centres; it never touches a bone;
+    * two tendon bars, two cells thick in z around z_a and z_b, join the
+      spindle's ends to the bones' +x faces (shared vertices);
+    * materials: muscle (E = 6e5), tendon (E = 1e8), bone (E = 1e10,
+      nu = 0.3); bone_id 0 / 1 on the bones' tets, -1 elsewhere;
+    * spindle fibers u = normalise(e_z + rho r'(z) / r(z) e_rho) (rho the
+      distance to the spindle's axis, e_rho its direction); e_z elsewhere;
+    * every vertex of bone 1 is pinned;
+    * one hinge at the gap's centre on the bones' axis, along y, with
+      half-length bone_w / 2;
+    * activation a_max sin^2(pi f / frames), f = 0 .. frames - 1, on the
+      spindle's tets (0 on tendon and bone).
+
+    The defaults give about 800k tets with two 50,112-tet bones.
+    """
+    bw, L = int(bone_w), int(bone_len)
+    nyc = max(bw, 2 * int(math.ceil(r0)) + 2)
+    if (nyc - bw) % 2:
+        nyc += 1
+    y0 = (nyc - bw) // 2
+    xc = bw + gap_x + r0
+    yc = 0.5 * nyc
+    nx = int(math.ceil(xc + r0)) + 1
+    nz = 2 * L + 1
+    rest, tets, cen = kuhn_grid(nx, nyc, nz, h)
+    c = cen / h  # centroids in cell units
+    # label each tet by its cell (the six tets of a cell share its centre)
+    cell = np.floor(c).astype(np.int64)
+    cc = cell + 0.5
+    in_y = (cell[:, 1] >= y0) & (cell[:, 1] < y0 + bw)
+    in_x = cell[:, 0] < bw
+    bone1 = in_x & in_y & (cell[:, 2] < L)
+    bone2 = in_x & in_y & (cell[:, 2] >= L + 1) & (cell[:, 2] < 2 * L + 1)
+    za, zb = 0.5 * L, L + 1 + 0.5 * L
+    t = (cc[:, 2] - za) / (zb - za)
+    tt = np.clip(t, 0.0, 1.0)
+    rt = r0 * (0.3 + 0.7 * np.sin(np.pi * tt))
+    rho = np.hypot(cc[:, 0] - xc, cc[:, 1] - yc)
+    spindle = (t >= 0.0) & (t <= 1.0) & (rho <= rt)
+    bar_y = np.abs(cc[:, 1] - yc) <= max(0.3 * r0, 0.5)
+    bar_x = (cc[:, 0] > bw) & (cc[:, 0] <= xc)
+    bar_z = (np.abs(cc[:, 2] - za) <= 1.0) | (np.abs(cc[:, 2] - zb) <= 1.0)
+    bar = bar_x & bar_y & bar_z
+    bone = bone1 | bone2
+    spindle &= ~bone
+    bar &= ~(bone | spindle)
+    keep = bone | spindle | bar
+    rest, tets, _ = _compact(rest, tets, keep)
+    bone1, bone2, spindle, bar = bone1[keep], bone2[keep], spindle[keep], bar[keep]
+    cc, rho, tt = cc[keep], rho[keep], tt[keep]
+    m = tets.shape[0]
+    mat = np.full(m, MUSCLE, dtype=np.uint8)
+    mat[bar] = TENDON
+    mat[bone1 | bone2] = BONE
+    bone_id = np.full(m, -1, dtype=np.int32)
+    bone_id[bone1] = 0
+    bone_id[bone2] = 1
+    # spindle fibers: e_z plus the radial slope of the spindle's surface
+    drdz = r0 * 0.7 * np.pi * np.cos(np.pi * tt) / (zb - za)
+    er = np.stack([cc[:, 0] - xc, cc[:, 1] - yc, np.zeros(m)], axis=1)
+    er /= np.maximum(rho, 1e-12)[:, None]
+    slope = np.where(spindle, rho * drdz / np.maximum(r0 * (0.3 + 0.7 * np.sin(np.pi * tt)), 1e-12), 0.0)
+    fib = np.zeros((m, 3))
+    fib[:, 2] = 1.0
+    fib += slope[:, None] * er
+    fib /= np.linalg.norm(fib, axis=1, keepdims=True)
+    f = np.arange(frames)
+    ramp = a_max * np.sin(np.pi * f / frames) ** 2
+    acts = np.where(spindle[None, :], ramp[:, None], 0.0)
+    fixed = np.unique(tets[bone1]).astype(np.int32)
+    hinge = dict(type="hinge", bones=(0, 1),
+                 point=np.array([0.5 * bw, y0 + 0.5 * bw, L + 0.5]) * h,
+                 axis=np.array([0.0, 1.0, 0.0]), half_length=0.5 * bw * h)
+    return MeshSpec(
+        name=name or f"arm_{bw}x{L}_r{r0:g}",
+        rest_pos=rest,
+        tets=tets,
+        youngs=np.array([youngs_muscle, youngs_tendon, youngs_bone], dtype=np.float64),
+        poisson=np.array([poisson, poisson, poisson_bone], dtype=np.float64),
+        material_id=mat,
+        fiber_dir=fib,
+        fixed_verts=fixed,
+        activations=acts,
+        bone_id=bone_id,
+        joints=[hinge],
+        meta=dict(nx=nx, ny=nyc, nz=nz, h=h, bone_w=bw, bone_len=L, r0=r0, gap_x=gap_x),
+    )

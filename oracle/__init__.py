@@ -4,3 +4,4 @@ from .emu_oracle import (  # noqa: F401
     psd_project, delta_psi, sym_basis, stretch_from_s, s_from_stretch, element_terms_s,
     INVERTED_ENERGY,
 )
+from .bones import BoneOracle, affine_fit_weights  # noqa: F401,E402
