@@ -91,6 +91,8 @@ struct emu_handle {
   float4* ug32 = nullptr;                // 2 n exchange entries of the FP32 CG
   unsigned* sync32 = nullptr;             // its barrier words
   float* part32 = nullptr;
+  float* aphi32 = nullptr;                // rows of L Phi for the pipelined FP32 CG
+  bool aphi_ready = false;
   int grid32 = 0, rpt32 = 0;
   double q_tol = 1e-8;
   double dq_tol_now = 5e-2;  // dq tolerance of the current solve call
@@ -459,7 +461,10 @@ int validate_params(const emu_params* p) {
 int read_scalars(emu_handle* h);
 
 // FP32 CG of the mixed path: the register-resident kernel when the mesh fits
-// its launch shape, the generic kernel otherwise.
+// its launch shape, the generic kernel otherwise. Loose solves (tol >= 1e-3)
+// take the pipelined register-resident kernel (one grid barrier per
+// iteration); its recurrences drift from the true residual near FP32
+// precision, so tighter solves keep the plain one.
 cudaError_t run_pcg32(emu_handle* h, const float* rhs, float* x, double tol) {
   PcgArgsT<float> a = h->pcg32(rhs, x, tol);
   if (h->rpt32 > 0) {
@@ -467,6 +472,10 @@ cudaError_t run_pcg32(emu_handle* h, const float* rhs, float* x, double tol) {
     w.ug = h->ug32;
     w.part = h->part32;
     w.sync = h->sync32;
+    if (tol >= 1e-3 && h->aphi_ready && a.phi && pcg32_pipe_ok(h->rpt32)) {
+      w.aphi = h->aphi32;
+      return launch_pcg32_pipe(a, w, h->grid32, h->rpt32, h->st);
+    }
     return launch_pcg32(a, w, h->grid32, h->rpt32, h->st);
   }
   return launch_pcg<float>(3, a, h->grid_pcg3, h->st);
@@ -715,8 +724,11 @@ int build_modes(emu_handle* h) {
       for (int j = 0; j < 16; ++j) Ei[16 * i + j] += Ev[16 * i + k] * Ev[16 * j + k] / lk;
   }
   EMU_CK(cudaMemcpyAsync(h->Einv, Ei.data(), 256 * 8, cudaMemcpyHostToDevice, h->st));
+  if (h->mixed && h->rpt32 > 0)
+    EMU_CK(launch_aphi32(n, h->rowptr, h->col, h->val32, h->phi32, h->aphi32, h->st));
   EMU_CK(cudaStreamSynchronize(h->st));
   h->coarse_ready = emax > 0.0;
+  h->aphi_ready = h->mixed && h->rpt32 > 0;
   return EMU_OK;
 }
 
@@ -742,8 +754,8 @@ bool alloc_device(emu_handle* h, int64_t nnz) {
   ok = ok && h->get(h->pr, 16 * n) && h->get(h->pu, 16 * n) && h->get(h->pw, 16 * n) && h->get(h->pp, 16 * n) &&
        h->get(h->ps, 16 * n) && h->get(h->scratch16, 32 * n) && h->get(h->phi64, 16 * n) && h->get(h->Einv, 256);
   if (h->mixed) {
-    ok = ok && h->get(h->phi32, 16 * n) && h->get(h->ug32, 2 * n) && h->get(h->part32, 64 * (int64_t)h->sms) &&
-         h->get(h->sync32, 96);
+    ok = ok && h->get(h->phi32, 16 * n) && h->get(h->ug32, 2 * n) && h->get(h->part32, 128 * (int64_t)h->sms) &&
+         h->get(h->sync32, 96) && h->get(h->aphi32, 16 * n);
     if (!pcg32_shape(n, h->sms, &h->grid32, &h->rpt32)) h->rpt32 = 0;
   }
   h->grid_tet = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 127) / 128), 8 * (int64_t)h->sms);

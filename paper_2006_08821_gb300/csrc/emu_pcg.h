@@ -48,9 +48,11 @@ template <typename T> cudaError_t launch_pcg(int nrhs, const PcgArgsT<T>& args, 
 // Work space of the register-resident FP32 CG.
 struct Pcg32Work {
   float4* ug;      // 2 n exchange entries (x, then u, per vertex)
-  float* part;     // 64 * grid block partial sums, value-major
+  float* part;     // 128 * grid block partial sums, value-major (two buffers
+                   // of 64 * grid; the plain kernel uses the first)
   unsigned* sync;  // 96 words of barrier state, zero before the first launch
                    // (each launch leaves them zero)
+  const float* aphi = nullptr;  // n x 16 rows of A Phi (pipelined kernel only)
 };
 
 // Register-resident FP32 CG (3 columns): shape for n rows on ``sms`` SMs
@@ -60,6 +62,16 @@ bool pcg32_shape(int64_t n, int sms, int* grid, int* rpt);
 cudaError_t launch_pcg32(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, int rpt, cudaStream_t st);
 // Per-device kernel attributes of the FP32 CG (before its first launch).
 cudaError_t prepare_pcg32();
+// Pipelined form of the same iteration with one grid barrier per iteration
+// instead of two. It needs the coarse space (args.phi, args.Einv) and
+// work.aphi, and supports rpt <= 4; launch_pcg32_pipe returns
+// cudaErrorInvalidValue otherwise. Its recurrences drift from the true
+// residual near FP32 precision, so it serves the loose inner solves.
+bool pcg32_pipe_ok(int rpt);
+cudaError_t launch_pcg32_pipe(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, int rpt, cudaStream_t st);
+// aphi = A phi for the n x 16 row-major coarse basis (FP32 CSR matrix).
+cudaError_t launch_aphi32(int64_t n, const int32_t* rowptr, const int32_t* col, const float* val, const float* phi,
+                          float* aphi, cudaStream_t st);
 
 // FP64 residual r = b - K x (3 columns), written as float (r32) and/or double
 // (r64) when those are non-null; out6 receives sum |r_j|^2 (j < 3) and

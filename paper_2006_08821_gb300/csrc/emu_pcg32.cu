@@ -13,8 +13,11 @@
 //     unit about once), so all blocks hold bit-identical scalars and the
 //     result is deterministic;
 //   * the matrix, D^-1 and Phi are read-only for the whole launch (__ldg).
-// Two grid-wide barriers per iteration (after u, after the partial sums).
+// Two grid-wide barriers per iteration (after u, after the partial sums);
+// pcg32p_kernel below is the pipelined variant with one.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "emu_internal.h"
@@ -516,6 +519,315 @@ timeout:
   gbar_exit(wk);
 }
 
+
+// Pipelined form of the same Chronopoulos-Gear iteration (after Ghysels and
+// Vanroose), with one grid barrier per iteration instead of two. The
+// preconditioned residual u = M r and w = A u are carried by recurrences,
+// together with q = M s and z = A q, so that the only vector a block needs
+// from its neighbours, v = D^-1 w, is published with the partial sums of the
+// same iteration. The coarse part of M w, Phi E^-1 Phi^T w, needs Phi^T w,
+// a global sum; it is applied after the barrier through the precomputed
+// rows of A Phi: n = A M w = A v + (A Phi) c with c = E^-1 Phi^T w.
+// Exchange vectors and partial sums alternate between two buffers: a block
+// may publish iteration i + 1 while a slower one still reads iteration i.
+template <int RPT>
+__global__ void __launch_bounds__(NT, 1) pcg32p_kernel(PcgArgsT<float> a, Pcg32Work wk) {
+  constexpr int NC = kModes * NR;
+  constexpr int NV0 = 4 * NR + NC;  // gamma, delta, rr, bb, Phi^T w
+  constexpr int PSTRIDE = 64;       // values per partial-sum buffer (x grid)
+  static_assert(NV0 <= PSTRIDE, "partial sums exceed their buffer");
+  __shared__ float sm[(NT / 32) * NV0];
+  __shared__ float ssum[NV0];
+  __shared__ float s_al[NR], s_be[NR], s_ga[NR], s_thr[NR], s_bb[NR], s_rr[NR];
+  __shared__ int s_act[NR];
+  __shared__ float s_rho[NC], s_cc[NC];
+  __shared__ float s_Einv[kModes * kModes];
+  __shared__ int s_flag;
+  // rows of Phi, then rows of A Phi: float4 q of row k at [(q * RPT + k) * NT + tid]
+  extern __shared__ float4 sPhi[];
+  float4* sAPhi = sPhi + (kModes / 4) * RPT * NT;
+  unsigned epoch = 0;
+  const int64_t n = a.n;
+  const int G = gridDim.x;
+  const int64_t stride = (int64_t)G * NT;
+  const int64_t g0 = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int32_t* __restrict__ rowptr = a.rowptr;
+  const int32_t* __restrict__ col = a.col;
+  const float* __restrict__ val = a.val;
+  for (int k = threadIdx.x; k < kModes * kModes; k += NT) s_Einv[k] = (float)a.Einv[k];
+
+  float x[RPT][NR], r[RPT][NR], u[RPT][NR], w[RPT][NR], p[RPT][NR], s[RPT][NR], qv[RPT][NR], z[RPT][NR];
+  float di[RPT];
+  bool own[RPT];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int64_t v = g0 + k * stride;
+    own[k] = v < n;
+    di[k] = own[k] ? __ldg(a.dinv + v) : 0.f;
+    const float4* ph = reinterpret_cast<const float4*>(a.phi + v * kModes);
+    const float4* aph = reinterpret_cast<const float4*>(wk.aphi + v * kModes);
+#pragma unroll
+    for (int q = 0; q < kModes / 4; ++q) {
+      sPhi[(q * RPT + k) * NT + threadIdx.x] = own[k] ? __ldg(ph + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      sAPhi[(q * RPT + k) * NT + threadIdx.x] = own[k] ? __ldg(aph + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      x[k][j] = own[k] ? a.x[v * NR + j] : 0.f;
+      p[k][j] = s[k][j] = qv[k][j] = z[k][j] = 0.f;
+    }
+  }
+
+  // y = A z for the owned rows (neighbours' z as float4 per vertex), one L2
+  // round trip per row for rows of up to kGather entries
+  auto spmv = [&](const float4* __restrict__ zsrc, float (&y)[RPT][NR]) {
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      y[k][0] = y[k][1] = y[k][2] = 0.f;
+      if (!own[k]) continue;
+      const int64_t v = g0 + k * stride;
+      const int32_t e0 = __ldg(rowptr + v), e1 = __ldg(rowptr + v + 1);
+      const int cnt = e1 - e0;
+      float4 z4[kGather];
+      float a4[kGather];
+#pragma unroll
+      for (int t = 0; t < kGather; ++t) {
+        a4[t] = 0.f;
+        z4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < cnt) {
+          a4[t] = __ldg(val + e0 + t);
+          z4[t] = __ldcg(zsrc + __ldg(col + e0 + t));
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kGather; ++t) {
+        y[k][0] += a4[t] * z4[t].x;
+        y[k][1] += a4[t] * z4[t].y;
+        y[k][2] += a4[t] * z4[t].z;
+      }
+      for (int32_t e = e0 + kGather; e < e1; ++e) {
+        const float av = __ldg(val + e);
+        const float4 zz = __ldcg(zsrc + __ldg(col + e));
+        y[k][0] += av * zz.x;
+        y[k][1] += av * zz.y;
+        y[k][2] += av * zz.z;
+      }
+    }
+  };
+  // loc[m NR + j] += Phi[v][m] y[k][j] over the owned rows
+  auto phi_t = [&](const float (&y)[RPT][NR], float* loc) {
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      if (!own[k]) continue;
+#pragma unroll
+      for (int q = 0; q < kModes / 4; ++q) {
+        const float4 ph = sPhi[(q * RPT + k) * NT + threadIdx.x];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          loc[(4 * q) * NR + j] += ph.x * y[k][j];
+          loc[(4 * q + 1) * NR + j] += ph.y * y[k][j];
+          loc[(4 * q + 2) * NR + j] += ph.z * y[k][j];
+          loc[(4 * q + 3) * NR + j] += ph.w * y[k][j];
+        }
+      }
+    }
+  };
+  // s_cc = E^-1 s_rho
+  auto coarse_cc = [&]() {
+    for (int e = threadIdx.x; e < NC; e += NT) {
+      const int m = e / NR, j = e % NR;
+      float acc = 0.f;
+#pragma unroll
+      for (int l = 0; l < kModes; ++l) acc += s_Einv[m * kModes + l] * s_rho[l * NR + j];
+      s_cc[e] = acc;
+    }
+    __syncthreads();
+  };
+  // sum_m rows[v][m] s_cc[m NR + j] for row k (rows: sPhi or sAPhi)
+  auto coarse_row = [&](const float4* rows, int k, int j) {
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < kModes / 4; ++q) {
+      const float4 ph = rows[(q * RPT + k) * NT + threadIdx.x];
+      acc += ph.x * s_cc[(4 * q) * NR + j] + ph.y * s_cc[(4 * q + 1) * NR + j] + ph.z * s_cc[(4 * q + 2) * NR + j] +
+             ph.w * s_cc[(4 * q + 3) * NR + j];
+    }
+    return acc;
+  };
+
+  // ---- r = b - A x ------------------------------------------------------
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int64_t v = g0 + k * stride;
+    if (own[k]) wk.ug[v] = make_float4(x[k][0], x[k][1], x[k][2], 0.f);
+  }
+  if (!gbar(wk, epoch, &s_flag)) goto timeout;
+  spmv(wk.ug, w);
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int64_t v = g0 + k * stride;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) r[k][j] = own[k] ? a.b[v * NR + j] - w[k][j] : 0.f;
+  }
+  {  // u = D^-1 r + Phi E^-1 Phi^T r, published in the second exchange buffer
+    float loc[NV0];
+#pragma unroll
+    for (int k = 0; k < NV0; ++k) loc[k] = 0.f;
+    phi_t(r, loc);
+    block_sum_f<NV0>(loc, ssum, sm);
+    for (int k = threadIdx.x; k < NC; k += NT) wk.part[(size_t)k * G + blockIdx.x] = ssum[k];
+    if (!gbar(wk, epoch, &s_flag)) goto timeout;
+    grid_sum_f<NV0>(wk.part, NC, ssum);
+    for (int k = threadIdx.x; k < NC; k += NT) s_rho[k] = ssum[k];
+    __syncthreads();
+    coarse_cc();
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int64_t v = g0 + k * stride;
+#pragma unroll
+      for (int j = 0; j < NR; ++j) u[k][j] = own[k] ? di[k] * r[k][j] + coarse_row(sPhi, k, j) : 0.f;
+      if (own[k]) wk.ug[n + v] = make_float4(u[k][0], u[k][1], u[k][2], 0.f);
+    }
+  }
+  if (!gbar(wk, epoch, &s_flag)) goto timeout;
+  spmv(wk.ug + n, w);  // w = A u
+
+  {
+    int it = 0, buf = 0;
+    bool first = true, all_done = false;
+    for (;;) {
+      float* __restrict__ pb = wk.part + (size_t)buf * PSTRIDE * G;
+      float4* __restrict__ ub = wk.ug + (size_t)buf * n;
+      {  // partial sums of this iteration and v = D^-1 w for the neighbours
+        float loc[NV0];
+#pragma unroll
+        for (int k = 0; k < NV0; ++k) loc[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+          if (!own[k]) continue;
+          const int64_t v = g0 + k * stride;
+#pragma unroll
+          for (int j = 0; j < NR; ++j) {
+            loc[j] += r[k][j] * u[k][j];
+            loc[NR + j] += w[k][j] * u[k][j];
+            loc[2 * NR + j] += r[k][j] * r[k][j];
+            if (first) {
+              const float bv = a.b[v * NR + j];
+              loc[3 * NR + j] += bv * bv;
+            }
+          }
+          ub[v] = make_float4(di[k] * w[k][0], di[k] * w[k][1], di[k] * w[k][2], 0.f);
+        }
+        phi_t(w, loc + 4 * NR);
+        block_sum_f<NV0>(loc, ssum, sm);
+        for (int k = threadIdx.x; k < NV0; k += NT) pb[(size_t)k * G + blockIdx.x] = ssum[k];
+      }
+      if (!gbar(wk, epoch, &s_flag)) goto timeout;
+      grid_sum_f<NV0>(pb, NV0, ssum);
+      if (threadIdx.x < NR) {
+        const int j = threadIdx.x;
+        if (first) {
+          const float bb = ssum[3 * NR + j];
+          s_bb[j] = bb;
+          s_thr[j] = (float)(a.tol * a.tol) * bb;
+          s_act[j] = 1;
+        }
+        const float rr = ssum[2 * NR + j];
+        s_rr[j] = rr;
+        if (s_act[j]) {
+          const float g_new = ssum[j], dl = ssum[NR + j];
+          if (rr <= s_thr[j]) {
+            s_act[j] = 0;
+          } else {
+            const float be = first ? 0.f : g_new / s_ga[j];
+            const float den = first ? dl : dl - be * g_new / s_al[j];
+            if (!(den > 0.f)) {
+              s_act[j] = 0;
+            } else {
+              s_be[j] = be;
+              s_al[j] = g_new / den;
+              s_ga[j] = g_new;
+            }
+          }
+        }
+      }
+      for (int e = threadIdx.x; e < NC; e += NT) s_rho[e] = ssum[4 * NR + e];
+      __syncthreads();
+      if (first) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+#pragma unroll
+          for (int j = 0; j < NR; ++j)
+            if (s_bb[j] == 0.f) x[k][j] = 0.f;  // zero right-hand side: x = 0 exactly
+      }
+      all_done = !(s_act[0] || s_act[1] || s_act[2]);
+      if (all_done || it >= a.max_iter) break;
+      ++it;
+      coarse_cc();  // c = E^-1 Phi^T w
+      float nv[RPT][NR];
+      spmv(ub, nv);  // A D^-1 w
+#pragma unroll
+      for (int k = 0; k < RPT; ++k)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          if (!s_act[j]) continue;
+          const float be = s_be[j], al = s_al[j];
+          const float mv = di[k] * w[k][j] + coarse_row(sPhi, k, j);   // m = M w
+          const float nn = nv[k][j] + coarse_row(sAPhi, k, j);         // n = A M w
+          z[k][j] = nn + be * z[k][j];
+          qv[k][j] = mv + be * qv[k][j];
+          s[k][j] = w[k][j] + be * s[k][j];
+          p[k][j] = u[k][j] + be * p[k][j];
+          x[k][j] += al * p[k][j];
+          r[k][j] -= al * s[k][j];
+          u[k][j] -= al * qv[k][j];
+          w[k][j] -= al * z[k][j];
+        }
+      first = false;
+      buf ^= 1;
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int64_t v = g0 + k * stride;
+      if (own[k])
+#pragma unroll
+        for (int j = 0; j < NR; ++j) a.x[v * NR + j] = x[k][j];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (a.iters_out) atomicAdd(a.iters_out, it);
+      if (a.fail_out && !all_done) atomicExch(a.fail_out, 1);
+      if (a.last_iters) *a.last_iters = it;
+      if (a.relres_out)
+        for (int j = 0; j < NR; ++j) a.relres_out[j] = s_bb[j] > 0.f ? sqrt((double)s_rr[j] / s_bb[j]) : 0.0;
+    }
+  }
+  gbar_exit(wk);
+  return;
+timeout:
+  if (threadIdx.x == 0 && a.timeout_out) atomicExch(a.timeout_out, 1);
+  gbar_exit(wk);
+}
+
+// aphi = A phi, one thread per (row, four modes)
+__global__ void k_aphi32(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                         const float* __restrict__ val, const float4* __restrict__ phi, float4* __restrict__ aphi) {
+  const int64_t tot = n * (kModes / 4);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / (kModes / 4);
+    const int q = (int)(i % (kModes / 4));
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+      const float av = val[e];
+      const float4 ph = phi[(int64_t)col[e] * (kModes / 4) + q];
+      acc.x += av * ph.x;
+      acc.y += av * ph.y;
+      acc.z += av * ph.z;
+      acc.w += av * ph.w;
+    }
+    aphi[i] = acc;
+  }
+}
+
 namespace {
 template <int RPT, bool C>
 cudaError_t prepare32() {
@@ -558,9 +870,63 @@ bool pcg32_shape(int64_t n, int sms, int* grid, int* rpt) {
   return true;
 }
 
+
+namespace {
+template <int RPT>
+constexpr size_t pipe_smem() {
+  return 2 * sizeof(float4) * (kModes / 4) * RPT * NT;  // rows of Phi and of A Phi
+}
+
+template <int RPT>
+cudaError_t prepare32p() {
+  static bool set[64] = {false};
+  if (pipe_smem<RPT>() <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (set[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(pcg32p_kernel<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipe_smem<RPT>());
+  if (e == cudaSuccess) set[dev] = true;
+  return e;
+}
+
+template <int RPT>
+cudaError_t launch32p(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, cudaStream_t st) {
+  PcgArgsT<float> a = args;
+  Pcg32Work w = work;
+  void* params[] = {(void*)&a, (void*)&w};
+  return cudaLaunchCooperativeKernel((const void*)pcg32p_kernel<RPT>, dim3(grid), dim3(NT), params, pipe_smem<RPT>(),
+                                     st);
+}
+}  // namespace
+
+bool pcg32_pipe_ok(int rpt) { return rpt == 1 || rpt == 2 || rpt == 4; }
+
+cudaError_t launch_pcg32_pipe(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, int rpt, cudaStream_t st) {
+  if (grid > 32 * kMaxGridStrides || !args.phi || !args.Einv || !work.aphi) return cudaErrorInvalidValue;
+  switch (rpt) {
+    case 1: return launch32p<1>(args, work, grid, st);
+    case 2: return launch32p<2>(args, work, grid, st);
+    case 4: return launch32p<4>(args, work, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_aphi32(int64_t n, const int32_t* rowptr, const int32_t* col, const float* val, const float* phi,
+                          float* aphi, cudaStream_t st) {
+  const int64_t tot = n * (kModes / 4);
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(1, (tot + 255) / 256), 4096);
+  k_aphi32<<<grid, 256, 0, st>>>(n, rowptr, col, val, reinterpret_cast<const float4*>(phi),
+                                 reinterpret_cast<float4*>(aphi));
+  return cudaGetLastError();
+}
+
 cudaError_t prepare_pcg32() {
   cudaError_t e = prepare32<4, true>();
   if (e == cudaSuccess) e = prepare32<8, true>();
+  if (e == cudaSuccess) e = prepare32p<2>();
+  if (e == cudaSuccess) e = prepare32p<4>();
   return e;
 }
 
