@@ -49,7 +49,7 @@ FALLBACK_HBM_GBS = 6800.0
 # capture of the unchanged kernel (summaries under profiles/); None once the
 # kernel has changed since.
 NCU_TRAFFIC = {
-    "pcg": (15.78e6, "profiles/pcg32_kernel_mtu401920.md"),
+    "pcg": (20.60e6, "profiles/pcg32p_kernel_mtu401920.md"),
     "grad": (127.31e6, "profiles/k_grad_m_mtu401920.md"),
     "dir": (229.04e6, "profiles/k_dir_m_mtu401920.md"),
     "ls": (84.83e6, "profiles/k_ls_m_mtu401920.md"),
