@@ -461,10 +461,13 @@ int validate_params(const emu_params* p) {
 int read_scalars(emu_handle* h);
 
 // FP32 CG of the mixed path: the register-resident kernel when the mesh fits
-// its launch shape, the generic kernel otherwise. Loose solves (tol >= 1e-3)
-// take the pipelined register-resident kernel (one grid barrier per
+// its launch shape, the generic kernel otherwise. Solves to kPipeMinTol or
+// looser take the pipelined register-resident kernel (one grid barrier per
 // iteration); its recurrences drift from the true residual near FP32
-// precision, so tighter solves keep the plain one.
+// precision, so tighter solves keep the plain one. (The correction rounds of
+// the exact re-solve, at 1e-5 to 1e-3, measured slower on it: 260 instead of
+// 243 us of CG per Newton iteration on the 401,920-tet unit.)
+constexpr double kPipeMinTol = 1e-3;
 cudaError_t run_pcg32(emu_handle* h, const float* rhs, float* x, double tol) {
   PcgArgsT<float> a = h->pcg32(rhs, x, tol);
   if (h->rpt32 > 0) {
@@ -472,7 +475,7 @@ cudaError_t run_pcg32(emu_handle* h, const float* rhs, float* x, double tol) {
     w.ug = h->ug32;
     w.part = h->part32;
     w.sync = h->sync32;
-    if (tol >= 1e-3 && h->aphi_ready && a.phi && pcg32_pipe_ok(h->rpt32)) {
+    if (tol >= kPipeMinTol && h->aphi_ready && a.phi && pcg32_pipe_ok(h->rpt32)) {
       w.aphi = h->aphi32;
       return launch_pcg32_pipe(a, w, h->grid32, h->rpt32, h->st);
     }
