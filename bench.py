@@ -426,7 +426,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--ls-sigma0", type=float, default=None,
-                    help="first line-search trial step (default: the library's, 2)")
+                    help="first line-search trial step (default: the library's, 4)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

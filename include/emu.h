@@ -112,7 +112,7 @@ typedef struct {
  *   tol_rel_residual stop when ||dE/dF||_2 / ||dE/dF at F=I||_2 <= tol.
  *   max_newton      Newton iteration cap per solve.
  *   ls_sigma0, ls_c, ls_rho, ls_max_trials   Armijo backtracking
- *                   (Algorithm 1 uses 10, 1e-4, 0.5; defaults 2, 1e-4,
+ *                   (Algorithm 1 uses 10, 1e-4, 0.5; defaults 4, 1e-4,
  *                   0.5, 40). Each pass evaluates 4 trial steps
  *                   sigma * rho^j together and takes, among those meeting
  *                   the Armijo condition, the one with the largest energy

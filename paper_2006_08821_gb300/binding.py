@@ -194,7 +194,7 @@ class Params:
     fiber_scale: float = 1.0
     tol_rel_residual: float = 1e-6
     max_newton: int = 2000
-    ls_sigma0: float = 2.0
+    ls_sigma0: float = 4.0
     ls_c: float = 1e-4
     ls_rho: float = 0.5
     ls_max_trials: int = 40

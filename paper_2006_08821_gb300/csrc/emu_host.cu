@@ -834,7 +834,7 @@ void emu_default_params(emu_params* p) {
   p->fiber_scale = 1.0;
   p->tol_rel_residual = 1e-6;
   p->max_newton = 2000;
-  p->ls_sigma0 = 2.0;
+  p->ls_sigma0 = 4.0;
   p->ls_c = 1e-4;
   p->ls_rho = 0.5;
   p->ls_max_trials = 40;
