@@ -98,6 +98,20 @@ typedef struct {
   int64_t n_fixed;
   const int32_t* fixed_verts;
   const double* fixed_pos;
+  /* Bones and joints (Sec. 3.3): bone_id (n_tets; -1 = deformable, b >= 0 =
+   * bone b) may be NULL; n_joints joints between bones, each with a type
+   * (0 ball, 1 hinge), two bone ids, a point (metres) and, for a hinge, a
+   * unit axis and the half-length of its two axis points. This version's
+   * GPU path has no bones or joints yet: a mesh with a bone tet or a joint
+   * is rejected with EMU_ERR_NOT_IMPLEMENTED before any device work. All
+   * may be NULL / 0. */
+  const int32_t* bone_id;
+  int32_t n_joints;
+  const int32_t* joint_type;        /* n_joints */
+  const int32_t* joint_bones;       /* n_joints x 2 */
+  const double* joint_point;        /* n_joints x 3 */
+  const double* joint_axis;         /* n_joints x 3 */
+  const double* joint_half_length;  /* n_joints */
 } emu_mesh_desc;
 
 /* Solver parameters. emu_default_params fills the defaults shown.

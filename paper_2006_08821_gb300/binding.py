@@ -72,6 +72,13 @@ class emu_mesh_desc(C.Structure):
         ("n_fixed", C.c_int64),
         ("fixed_verts", C.POINTER(C.c_int32)),
         ("fixed_pos", C.POINTER(C.c_double)),
+        ("bone_id", C.POINTER(C.c_int32)),
+        ("n_joints", C.c_int32),
+        ("joint_type", C.POINTER(C.c_int32)),
+        ("joint_bones", C.POINTER(C.c_int32)),
+        ("joint_point", C.POINTER(C.c_double)),
+        ("joint_axis", C.POINTER(C.c_double)),
+        ("joint_half_length", C.POINTER(C.c_double)),
     ]
 
 
@@ -269,7 +276,23 @@ def mesh_desc(mesh):
     d.n_fixed = fx.shape[0]
     d.fixed_verts = _dptr(fx, C.c_int32)
     d.fixed_pos = _dptr(fp, C.c_double) if fp is not None else None
-    return d, [Q, T, E, nu, mid, fib, fx, fp]
+    bid = getattr(mesh, "bone_id", None)
+    bid = None if bid is None else np.ascontiguousarray(bid, dtype=np.int32)
+    d.bone_id = _dptr(bid, C.c_int32) if bid is not None else None
+    joints = getattr(mesh, "joints", None) or []
+    jt = np.array([1 if j["type"] == "hinge" else 0 for j in joints], dtype=np.int32)
+    jb = np.array([j["bones"] for j in joints], dtype=np.int32).reshape(-1, 2)
+    jp = np.array([j["point"] for j in joints], dtype=np.float64).reshape(-1, 3)
+    ja = np.array([j.get("axis", (0.0, 0.0, 0.0)) for j in joints], dtype=np.float64).reshape(-1, 3)
+    jh = np.array([j.get("half_length", 0.0) for j in joints], dtype=np.float64)
+    d.n_joints = len(joints)
+    if joints:
+        d.joint_type = _dptr(jt, C.c_int32)
+        d.joint_bones = _dptr(jb, C.c_int32)
+        d.joint_point = _dptr(jp, C.c_double)
+        d.joint_axis = _dptr(ja, C.c_double)
+        d.joint_half_length = _dptr(jh, C.c_double)
+    return d, [Q, T, E, nu, mid, fib, fx, fp, bid, jt, jb, jp, ja, jh]
 
 
 class Solver:

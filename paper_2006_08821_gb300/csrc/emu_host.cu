@@ -436,6 +436,11 @@ int validate_mesh(const emu_mesh_desc* d) {
     if (d->fixed_verts[i] < 0 || d->fixed_verts[i] >= d->n_verts) return fail(EMU_ERR_INVALID_ARG, "fixed vertex out of range");
   for (int64_t i = 0; i < 3 * d->n_verts; ++i)
     if (!std::isfinite(d->rest_pos[i])) return fail(EMU_ERR_INVALID_ARG, "non-finite rest position");
+  if (d->n_joints < 0) return fail(EMU_ERR_INVALID_ARG, "n_joints must be >= 0");
+  if (d->n_joints > 0) return fail(EMU_ERR_NOT_IMPLEMENTED, "joints (Sec. 3.3) are not supported by the GPU path yet");
+  if (d->bone_id)
+    for (int64_t i = 0; i < d->n_tets; ++i)
+      if (d->bone_id[i] >= 0) return fail(EMU_ERR_NOT_IMPLEMENTED, "bones (Sec. 3.3) are not supported by the GPU path yet");
   return EMU_OK;
 }
 

@@ -189,6 +189,83 @@ __device__ __forceinline__ void grid_sum_f(const float* __restrict__ part, int n
   }
   __syncthreads();
 }
+
+// y = A z for the rows a thread owns (g0 + k stride, k < RPT), z read as
+// float4 per vertex (the neighbours' values). The first kGather entries of a
+// row are gathered at once, so a row costs one L2 round trip (a vertex of a
+// tetrahedral grid has at most 14 neighbours); longer rows finish in a plain
+// loop.
+template <int RPT>
+__device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                          const float* __restrict__ val, const bool (&own)[RPT], int64_t g0,
+                                          int64_t stride, const float4* __restrict__ z, float (&y)[RPT][NR]) {
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    y[k][0] = y[k][1] = y[k][2] = 0.f;
+    if (!own[k]) continue;
+    const int64_t v = g0 + k * stride;
+    const int32_t e0 = __ldg(rowptr + v), e1 = __ldg(rowptr + v + 1);
+    const int cnt = e1 - e0;
+    float4 z4[kGather];
+    float a4[kGather];
+#pragma unroll
+    for (int t = 0; t < kGather; ++t) {
+      a4[t] = 0.f;
+      z4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (t < cnt) {
+        a4[t] = __ldg(val + e0 + t);
+        z4[t] = __ldcg(z + __ldg(col + e0 + t));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kGather; ++t) {
+      y[k][0] += a4[t] * z4[t].x;
+      y[k][1] += a4[t] * z4[t].y;
+      y[k][2] += a4[t] * z4[t].z;
+    }
+    for (int32_t e = e0 + kGather; e < e1; ++e) {
+      const float av = __ldg(val + e);
+      const float4 zz = __ldcg(z + __ldg(col + e));
+      y[k][0] += av * zz.x;
+      y[k][1] += av * zz.y;
+      y[k][2] += av * zz.z;
+    }
+  }
+}
+
+// loc[m NR + j] += Phi[v][m] y[k][j] over the owned rows; the coarse rows of
+// a thread live in shared memory, float4 q of row k at sPhi[(q RPT + k) NT + tid]
+template <int RPT>
+__device__ __forceinline__ void phi_t_rows(const float4* sPhi, const bool (&own)[RPT], const float (&y)[RPT][NR],
+                                           float* loc) {
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    if (!own[k]) continue;
+#pragma unroll
+    for (int q = 0; q < kModes / 4; ++q) {
+      const float4 ph = sPhi[(q * RPT + k) * NT + threadIdx.x];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        loc[(4 * q) * NR + j] += ph.x * y[k][j];
+        loc[(4 * q + 1) * NR + j] += ph.y * y[k][j];
+        loc[(4 * q + 2) * NR + j] += ph.z * y[k][j];
+        loc[(4 * q + 3) * NR + j] += ph.w * y[k][j];
+      }
+    }
+  }
+}
+
+// cc = E^-1 rho for the 16 x 3 coarse coefficients (block-wide, then a barrier)
+__device__ __forceinline__ void coarse_solve(const float* s_Einv, const float* s_rho, float* s_cc) {
+  for (int e = threadIdx.x; e < kModes * NR; e += NT) {
+    const int m = e / NR, j = e % NR;
+    float acc = 0.f;
+#pragma unroll
+    for (int l = 0; l < kModes; ++l) acc += s_Einv[m * kModes + l] * s_rho[l * NR + j];
+    s_cc[e] = acc;
+  }
+  __syncthreads();
+}
 }  // namespace
 
 template <int RPT, bool COARSE>
@@ -238,43 +315,8 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
     }
   }
 
-  // y = A z for the owned rows, z read as float4 per vertex (neighbours' values).
-  // The first kGather entries of a row are gathered at once, so a row costs
-  // one L2 round trip (a vertex of a tetrahedral grid has at most 14
-  // neighbours); longer rows finish in a plain loop.
   auto spmv = [&](const float4* __restrict__ z, float (&y)[RPT][NR]) {
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-      y[k][0] = y[k][1] = y[k][2] = 0.f;
-      if (!own[k]) continue;
-      const int64_t v = g0 + k * stride;
-      const int32_t e0 = __ldg(rowptr + v), e1 = __ldg(rowptr + v + 1);
-      const int cnt = e1 - e0;
-      float4 z4[kGather];
-      float a4[kGather];
-#pragma unroll
-      for (int t = 0; t < kGather; ++t) {
-        a4[t] = 0.f;
-        z4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (t < cnt) {
-          a4[t] = __ldg(val + e0 + t);
-          z4[t] = __ldcg(z + __ldg(col + e0 + t));
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < kGather; ++t) {
-        y[k][0] += a4[t] * z4[t].x;
-        y[k][1] += a4[t] * z4[t].y;
-        y[k][2] += a4[t] * z4[t].z;
-      }
-      for (int32_t e = e0 + kGather; e < e1; ++e) {
-        const float av = __ldg(val + e);
-        const float4 zz = __ldcg(z + __ldg(col + e));
-        y[k][0] += av * zz.x;
-        y[k][1] += av * zz.y;
-        y[k][2] += av * zz.z;
-      }
-    }
+    spmv_rows<RPT>(rowptr, col, val, own, g0, stride, z, y);
   };
   // u = D^-1 r + Phi cc, stored for the neighbours
   auto precond = [&]() {
@@ -298,38 +340,13 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
     }
   };
   auto coarse_cc = [&]() {  // s_cc = E^-1 rho
-    if constexpr (COARSE) {
-      for (int e = threadIdx.x; e < NC; e += NT) {
-        const int m = e / NR, j = e % NR;
-        float acc = 0.f;
-#pragma unroll
-        for (int l = 0; l < kModes; ++l) acc += s_Einv[m * kModes + l] * s_rho[l * NR + j];
-        s_cc[e] = acc;
-      }
-      __syncthreads();
-    }
+    if constexpr (COARSE) coarse_solve(s_Einv, s_rho, s_cc);
   };
   // global sums: every block sums all block partials in the same fixed order
   auto global_sum = [&](int nv) { grid_sum_f<NV0>(part, nv, ssum); };
   // loc[off + m NR + j] += Phi[v][m] y[k][j] over the owned rows
   auto phi_t = [&](const float (&y)[RPT][NR], float* loc) {
-    if constexpr (COARSE) {
-#pragma unroll
-      for (int k = 0; k < RPT; ++k) {
-        if (!own[k]) continue;
-#pragma unroll
-        for (int q = 0; q < kModes / 4; ++q) {
-          const float4 ph = sPhi[(q * RPT + k) * NT + threadIdx.x];
-#pragma unroll
-          for (int j = 0; j < NR; ++j) {
-            loc[(4 * q) * NR + j] += ph.x * y[k][j];
-            loc[(4 * q + 1) * NR + j] += ph.y * y[k][j];
-            loc[(4 * q + 2) * NR + j] += ph.z * y[k][j];
-            loc[(4 * q + 3) * NR + j] += ph.w * y[k][j];
-          }
-        }
-      }
-    }
+    if constexpr (COARSE) phi_t_rows<RPT>(sPhi, own, y, loc);
   };
   const int G = gridDim.x;
 
@@ -578,71 +595,11 @@ __global__ void __launch_bounds__(NT, 1) pcg32p_kernel(PcgArgsT<float> a, Pcg32W
     }
   }
 
-  // y = A z for the owned rows (neighbours' z as float4 per vertex), one L2
-  // round trip per row for rows of up to kGather entries
   auto spmv = [&](const float4* __restrict__ zsrc, float (&y)[RPT][NR]) {
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-      y[k][0] = y[k][1] = y[k][2] = 0.f;
-      if (!own[k]) continue;
-      const int64_t v = g0 + k * stride;
-      const int32_t e0 = __ldg(rowptr + v), e1 = __ldg(rowptr + v + 1);
-      const int cnt = e1 - e0;
-      float4 z4[kGather];
-      float a4[kGather];
-#pragma unroll
-      for (int t = 0; t < kGather; ++t) {
-        a4[t] = 0.f;
-        z4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (t < cnt) {
-          a4[t] = __ldg(val + e0 + t);
-          z4[t] = __ldcg(zsrc + __ldg(col + e0 + t));
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < kGather; ++t) {
-        y[k][0] += a4[t] * z4[t].x;
-        y[k][1] += a4[t] * z4[t].y;
-        y[k][2] += a4[t] * z4[t].z;
-      }
-      for (int32_t e = e0 + kGather; e < e1; ++e) {
-        const float av = __ldg(val + e);
-        const float4 zz = __ldcg(zsrc + __ldg(col + e));
-        y[k][0] += av * zz.x;
-        y[k][1] += av * zz.y;
-        y[k][2] += av * zz.z;
-      }
-    }
+    spmv_rows<RPT>(rowptr, col, val, own, g0, stride, zsrc, y);
   };
-  // loc[m NR + j] += Phi[v][m] y[k][j] over the owned rows
-  auto phi_t = [&](const float (&y)[RPT][NR], float* loc) {
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-      if (!own[k]) continue;
-#pragma unroll
-      for (int q = 0; q < kModes / 4; ++q) {
-        const float4 ph = sPhi[(q * RPT + k) * NT + threadIdx.x];
-#pragma unroll
-        for (int j = 0; j < NR; ++j) {
-          loc[(4 * q) * NR + j] += ph.x * y[k][j];
-          loc[(4 * q + 1) * NR + j] += ph.y * y[k][j];
-          loc[(4 * q + 2) * NR + j] += ph.z * y[k][j];
-          loc[(4 * q + 3) * NR + j] += ph.w * y[k][j];
-        }
-      }
-    }
-  };
-  // s_cc = E^-1 s_rho
-  auto coarse_cc = [&]() {
-    for (int e = threadIdx.x; e < NC; e += NT) {
-      const int m = e / NR, j = e % NR;
-      float acc = 0.f;
-#pragma unroll
-      for (int l = 0; l < kModes; ++l) acc += s_Einv[m * kModes + l] * s_rho[l * NR + j];
-      s_cc[e] = acc;
-    }
-    __syncthreads();
-  };
+  auto phi_t = [&](const float (&y)[RPT][NR], float* loc) { phi_t_rows<RPT>(sPhi, own, y, loc); };
+  auto coarse_cc = [&]() { coarse_solve(s_Einv, s_rho, s_cc); };  // s_cc = E^-1 s_rho
   // sum_m rows[v][m] s_cc[m NR + j] for row k (rows: sPhi or sAPhi)
   auto coarse_row = [&](const float4* rows, int k, int j) {
     float acc = 0.f;

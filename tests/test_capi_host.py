@@ -70,7 +70,7 @@ def _desc(mesh):
 
 @pytest.mark.parametrize("mutate,code", [
     ("bad_index", -1), ("no_pins", -1), ("bad_poisson", -1), ("bad_kmodes", -1), ("empty", -1),
-    ("nan_rest", -1), ("bad_material", -1),
+    ("nan_rest", -1), ("bad_material", -1), ("bone", -10), ("joint", -10), ("neg_joints", -1),
 ])
 def test_create_rejects_invalid_input_before_touching_the_device(lib, mutate, code):
     from paper_2006_08821_gb300 import binding as B
@@ -92,6 +92,15 @@ def test_create_rejects_invalid_input_before_touching_the_device(lib, mutate, co
         d.n_fixed = 0
     if mutate == "empty":
         d.n_tets = 0
+    if mutate == "bone":  # bones exist in the oracle only: EMU_ERR_NOT_IMPLEMENTED
+        bid = np.full(mesh.n_tets, -1, dtype=np.int32)
+        bid[0] = 0
+        keep.append(bid)
+        d.bone_id = bid.ctypes.data_as(C.POINTER(C.c_int32))
+    if mutate == "joint":
+        d.n_joints = 1
+    if mutate == "neg_joints":
+        d.n_joints = -1
     p = B.Params().to_c()
     if mutate == "bad_kmodes":
         p.k_modes = 50
