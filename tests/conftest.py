@@ -15,7 +15,7 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # GPU tests are skipped with a clear reason when no GPU is visible;
-    # the driver selects them explicitly with -m gpu on a GPU machine.
+    # on a machine with a GB300 they are selected with -m gpu.
     try:
         import torch
         have_gpu = torch.cuda.is_available()
