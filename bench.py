@@ -252,6 +252,21 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def reduce_over_ranks(dist, maxes, sums, device="cuda"):
+    """Whole-job totals of a replica run: the maximum over ranks of each entry
+    of ``maxes`` (times) and the sum over ranks of each entry of ``sums``
+    (units of work). Without a process group the local values come back."""
+    if not dist:
+        return [float(x) for x in maxes], [float(x) for x in sums]
+    import torch
+
+    t = torch.tensor([float(x) for x in maxes], device=device, dtype=torch.float64)
+    u = torch.tensor([float(x) for x in sums], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return t.tolist(), u.tolist()
+
+
 def make_params(emu, args, mixed):
     """Solver parameters of a bench leg: tolerance, precision and, with
     ``--ls-sigma0``, the first line-search trial step (else the library's)."""
@@ -320,12 +335,8 @@ def run_batch(args, emu, torch, rank, world, dist):
                         "status": int(st.status), "newton_iters": int(st.newton_iters),
                         "rel_residual": float(st.rel_residual)} for k, st in enumerate(stats) if st.status != 0])
     clk = clocks.stop()
-    total = float(np.sum(times))
-    if dist:
-        t = torch.tensor([total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t[0])
-    value = tet_iters * world / total
+    (total,), (tet_iters_job,) = reduce_over_ranks(dist, [float(np.sum(times))], [tet_iters])
+    value = tet_iters_job / total
     line = {
         "metric": "tet-iters/s", "value": value, "unit": "tet-iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
@@ -389,7 +400,8 @@ def run_serve(args, emu, torch, rank, world, dist):
         tet_iters += float(mesh.n_tets) * st.newton_iters
         lat.append(st.latency_ms)
         bad += int(st.status != 0)
-    value = tet_iters * world / makespan
+    (makespan,), (tet_iters_job,) = reduce_over_ranks(dist, [makespan], [tet_iters])
+    value = tet_iters_job / makespan
     line = {
         "metric": "tet-iters/s", "value": value, "unit": "tet-iters/s", "n_gpus": world, "steps": len(built),
         "warmup": 0, "ms_per_step": 1e3 * makespan / len(built), "higher_is_better": True, "scaling": "weak",
@@ -519,13 +531,8 @@ def main():
         prof_cg += st.pcg_iters
     torch.cuda.synchronize()
     prof, _ = solver.profile()
-    total_ms = float(np.sum(frame_ms))
-    total_e2e = float(np.sum(e2e_s))
-    if dist:
-        t = torch.tensor([total_ms, total_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, total_e2e = float(t[0]), float(t[1])
-    tet_iters = float(m * np.sum(iters)) * world
+    (total_ms, total_e2e), (tet_iters,) = reduce_over_ranks(
+        dist, [float(np.sum(frame_ms)), float(np.sum(e2e_s))], [float(m * np.sum(iters))])
     value = tet_iters / (total_ms / 1e3)
     e2e_value = tet_iters / total_e2e
 
