@@ -153,3 +153,32 @@ def test_hinge_turns_the_free_bone_rigidly_about_its_axis(arm, arm_solved):
     axis /= np.linalg.norm(axis)
     assert angle > 0.05                         # the muscle flexes the joint
     assert abs(axis @ np.asarray(arm.joints[0]["axis"])) >= 1.0 - 1e-8
+
+
+def test_warm_started_frame_reaches_the_cold_solution(arm):
+    # frames are solved from the previous frame's F (Sec. 4's sequences); the
+    # stationary point must not depend on the start
+    o = BoneOracle(arm, PRM)
+    a1, a2 = arm.activations[1], arm.activations[2]
+    r1 = o.solve(a1, tol=1e-10)
+    warm = o.solve(a2, X0=r1.F, tol=1e-10)
+    cold = o.solve(a2, tol=1e-10)
+    assert np.abs(warm.q - cold.q).max() <= 1e-8 * _diag(arm)
+
+
+def test_ball_joint_holds_its_point_and_lets_the_bone_turn(arm):
+    ball = [dict(type="ball", bones=(0, 1), point=arm.joints[0]["point"])]
+    mesh = dataclasses.replace(arm, joints=ball)
+    o = BoneOracle(mesh, PRM)
+    r = o.solve(mesh.activations[2], tol=1e-10)
+    assert len(o.joint_points) == 1
+    Fb = r.F[o.bone_slot[1]]
+    v2 = o.bone_verts[1]
+    t_b = (r.q[v2] - mesh.rest_pos[v2] @ Fb.T).mean(0)
+    p0 = np.asarray(ball[0]["point"])
+    disp = np.abs(r.q - mesh.rest_pos).max()
+    # the free bone's affine map keeps the joint point (bone 1 is pinned at rest)
+    assert np.linalg.norm(Fb @ p0 + t_b - p0) <= 1e-5 * disp
+    U, S, Vt = np.linalg.svd(Fb)
+    angle = np.arccos(np.clip(0.5 * (np.trace(U @ Vt) - 1.0), -1.0, 1.0))
+    assert angle > 0.05
