@@ -138,6 +138,9 @@ typedef struct {
  *   precision       EMU_PRECISION_FP64 or EMU_PRECISION_MIXED (per-tet
  *                   Hessian/Woodbury work in FP32; state, gradient,
  *                   residual, line-search sums and ACAP solve in FP64).
+ *                   MIXED is for tol_rel_residual >= 1e-6 or so: its FP32
+ *                   rounding floor can lie above a tighter tolerance, and a
+ *                   solve then runs to max_newton; use FP64 there.
  *   mode_iters      subspace iterations used to build the low-rank basis.
  *   seed            seeds the random start of the subspace iteration.
  *   dq_tol          relative residual of the per-iteration solve for the
