@@ -211,6 +211,18 @@ def cpu_baseline(workload_name, budget_s=15.0):
             "sample": f"{sample}; frames 1..{frames} ({tets_iters} tet-iters, {dt:.1f} s)"}
 
 
+def batch_desc(meshes, tol):
+    return (f"batch of {len(meshes)} box beams, log-uniform 1k-60k tets "
+            f"(sum {sum(mm.n_tets for mm in meshes)} tets), activation U[0,1], from rest, rel residual {tol:g}, "
+            "one emu_batch_solve per step, one stream per mesh")
+
+
+def serve_desc(args, n_requests):
+    return (f"serving: first {n_requests} requests of a Poisson stream at {args.rate:g}/s, "
+            "muscle-tendon units log-uniform 1k-200k tets, 1-30 frames, tendon U[0,0.2], "
+            f"budget {args.budget_gb:g} GB, rel residual {args.tol:g}")
+
+
 def run_reference(args, rank, world):
     """The oracle (FP64 CPU) as the reference arm: a step is one warm-started
     frame of a bounded sample of the workload (the same construction at
@@ -219,13 +231,18 @@ def run_reference(args, rank, world):
         return
     from oracle import EmuOracle, OracleParams
 
+    if args.workload == "batch":
+        return run_reference_batch(args)
     if args.workload in ("mtu", "mtu_small", "serve"):
         mesh = muscle_tendon_unit(8, 8, 32, h=0.01, radius_cells=12.9 / 4, frames=60)
         sample = f"muscle-tendon unit 8x8x32 ({mesh.n_tets} tets, same construction), warm-started ramp frames"
     else:
         mesh = box_beam(4, 4, 16, activation=np.linspace(0.0, 0.5, 12))
         sample = "box beam 4x4x16, ramp frames"
-    _, desc = make_workload(args.workload if args.workload in ("mtu", "box", "mtu_small") else "mtu")
+    if args.workload == "serve":
+        desc = serve_desc(args, args.requests)
+    else:
+        _, desc = make_workload(args.workload)
     o = EmuOracle(mesh, OracleParams(alpha_rel=1.0, weight_mode=0))
     nf = mesh.activations.shape[0]
     F = None
@@ -248,6 +265,38 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc}, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "tet-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_batch(args):
+    """Reference arm of the batch: a step is one mesh of the same 256-mesh set
+    (in order, from rest), on the host cores."""
+    from oracle import EmuOracle, OracleParams
+
+    meshes = batch_set(count=args.meshes, seed=3)
+    order = iter(range(len(meshes)))
+    done, tet_iters, dt = 0, 0, 0.0
+    for phase, count in (("warmup", args.warmup), ("timed", args.steps)):
+        for _ in range(count):
+            k = next(order)
+            mesh = meshes[k]
+            t0 = time.perf_counter()
+            r = EmuOracle(mesh, OracleParams(alpha_rel=1.0, weight_mode=0)).solve(
+                mesh.activations[0], tol=args.tol, max_newton=5000)
+            if phase == "timed":
+                dt += time.perf_counter() - t0
+                tet_iters += mesh.n_tets * r.iterations
+                done += 1
+    value = tet_iters / dt if dt > 0 else 0.0
+    cb = {"value": value, "unit": "tet-iters/s", "cores": os.cpu_count(), "kind": "oracle",
+          "sample": f"meshes {args.warmup}..{args.warmup + done - 1} of the batch set, from rest "
+                    f"({tet_iters} tet-iters, {dt:.1f} s; setup and solve timed)"}
+    line = {"impl": "reference", "metric": "tet-iters/s", "value": value, "unit": "tet-iters/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": batch_desc(meshes, args.tol)}, "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "tet-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -341,9 +390,7 @@ def run_batch(args, emu, torch, rank, world, dist):
         "metric": "tet-iters/s", "value": value, "unit": "tet-iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": f"batch of {len(meshes)} box beams, log-uniform 1k-60k tets "
-                               f"(sum {int(m_each.sum())} tets), activation U[0,1], from rest, rel residual {args.tol:g}, "
-                               "one emu_batch_solve per step, one stream per mesh",
+        "config": {"workload": batch_desc(meshes, args.tol),
                    "precision": args.precision, "l2": "inputs larger than L2; flushed between steps",
                    "tets": int(m_each.sum()), "meshes": len(meshes), "ls_sigma0": params.ls_sigma0},
         "newton_iters_per_step": iters, "max_rel_residual_converged": float(np.max(resid)),
@@ -406,9 +453,7 @@ def run_serve(args, emu, torch, rank, world, dist):
         "metric": "tet-iters/s", "value": value, "unit": "tet-iters/s", "n_gpus": world, "steps": len(built),
         "warmup": 0, "ms_per_step": 1e3 * makespan / len(built), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": f"serving: first {len(built)} requests of a Poisson stream at {args.rate:g}/s, "
-                               "muscle-tendon units log-uniform 1k-200k tets, 1-30 frames, tendon U[0,0.2], "
-                               f"budget {args.budget_gb:g} GB, rel residual {args.tol:g}",
+        "config": {"workload": serve_desc(args, len(built)),
                    "precision": args.precision, "requests": len(built), "ls_sigma0": params.ls_sigma0,
                    "tets_mean": float(np.mean([mm.n_tets for _, mm, _ in built]))},
         "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
