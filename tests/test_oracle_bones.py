@@ -182,3 +182,33 @@ def test_ball_joint_holds_its_point_and_lets_the_bone_turn(arm):
     U, S, Vt = np.linalg.svd(Fb)
     angle = np.arccos(np.clip(0.5 * (np.trace(U @ Vt) - 1.0), -1.0, 1.0))
     assert angle > 0.05
+
+
+def test_reduced_capacitance_equals_its_gram_form_with_a_virtual_tet_per_bone(arm):
+    # Eq. 12's capacitance Lambda - alpha B H^-1 B^T over the reduced
+    # variables, assembled another way: every deformable tet as the Gram term
+    # w Gamma^T N Gamma (N = I - alpha w H^-1), pinned-bone tets as
+    # w Gamma^T Gamma, and a free bone as one tet of weight sum w, operator
+    # the weighted mean of its tets' Gamma, plus their weighted variance
+    o = BoneOracle(arm, PRM)
+    a = arm.activations[2]
+    rng = np.random.default_rng(1)
+    X = o.identity() + 0.02 * rng.normal(size=(o.nvar, 3, 3))
+    H = o.hessian_blocks(X, a)
+    al = o.base.alpha
+    Bt = o.B.T.reshape(o.nvar, 9, o.k)
+    C_ref = o.Lhat - al * (o.B @ np.linalg.solve(H, Bt).reshape(9 * o.nvar, o.k))
+    Gam = (o.base.G_f @ o.Phi).reshape(o.m, 9, o.k)
+    w, slot, sb = o.w, o.slot, o.bone_slot[1]
+    C = np.zeros((o.k, o.k))
+    for i in range(o.m):
+        if slot[i] < 0:
+            C += w[i] * Gam[i].T @ Gam[i]
+        elif slot[i] != sb:
+            C += w[i] * Gam[i].T @ (np.eye(9) - al * w[i] * np.linalg.inv(H[slot[i]])) @ Gam[i]
+    tb = np.nonzero(slot == sb)[0]
+    wb = w[tb].sum()
+    Gbar = np.einsum("i,ijk->jk", w[tb], Gam[tb]) / wb
+    C += sum(w[i] * (Gam[i] - Gbar).T @ (Gam[i] - Gbar) for i in tb)
+    C += wb * Gbar.T @ (np.eye(9) - al * wb * np.linalg.inv(H[sb])) @ Gbar
+    assert np.abs(C - C_ref).max() <= 1e-12 * np.abs(C_ref).max()
