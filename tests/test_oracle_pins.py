@@ -5,6 +5,8 @@ finite differences, closed forms, a second independent solver, symmetry or
 a brute-force root. A dropped term, a wrong sign or index, or a transposed
 operand anywhere in the oracle fails at least one of them.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 import scipy.optimize as so
@@ -320,3 +322,40 @@ def test_energy_decreases_monotonically_and_converges():
         E_prev, F = E, r.F
     r = o.solve(a, F0=F, tol=1e-8)
     assert r.rel_residual <= 1e-8
+
+
+def _diag(mesh):
+    return float(np.linalg.norm(mesh.rest_pos.max(0) - mesh.rest_pos.min(0)))
+
+
+def test_converged_result_does_not_depend_on_the_mode_basis():
+    # Eqs. 9-12 only shape the direction; the gradient is exact, so the
+    # stationary point is the same for any number of modes
+    mesh = box_beam(2, 2, 6, activation=0.5)
+    qs = [EmuOracle(mesh, OracleParams(weight_mode=0, k_modes=k)).solve(0.5, tol=1e-11).q for k in (6, 24, 48)]
+    for q in qs[1:]:
+        assert np.abs(q - qs[0]).max() <= 1e-9 * _diag(mesh)
+
+
+def test_converged_result_does_not_depend_on_the_line_search_start():
+    # Algorithm 1's first trial step (10) or the Newton step (1): same point
+    mesh = box_beam(2, 2, 6, activation=0.5)
+    q1 = EmuOracle(mesh, OracleParams(weight_mode=0, ls_sigma0=1.0)).solve(0.5, tol=1e-11).q
+    q10 = EmuOracle(mesh, OracleParams(weight_mode=0, ls_sigma0=10.0)).solve(0.5, tol=1e-11).q
+    assert np.abs(q10 - q1).max() <= 1e-9 * _diag(mesh)
+
+
+def test_rigid_motion_of_the_rest_state_moves_the_solution_with_it():
+    # Eq. 2 uses edge differences and Psi, the fiber term and the ACAP term
+    # are invariant under a rotation of the reference frame: rotating and
+    # translating the rest mesh, its fibers and its pins rotates and
+    # translates the converged positions
+    mesh = box_beam(2, 2, 5, activation=0.6)
+    A = RNG.normal(size=(3, 3))
+    R0, _ = np.linalg.qr(A)
+    R0 *= np.sign(np.linalg.det(R0))
+    t0 = np.array([0.3, -0.2, 0.1])
+    moved = dataclasses.replace(mesh, rest_pos=mesh.rest_pos @ R0.T + t0, fiber_dir=mesh.fiber_dir @ R0.T)
+    q = EmuOracle(mesh, OracleParams(weight_mode=0)).solve(0.6, tol=1e-11).q
+    qm = EmuOracle(moved, OracleParams(weight_mode=0)).solve(0.6, tol=1e-11).q
+    assert np.abs(qm - (q @ R0.T + t0)).max() <= 1e-9 * _diag(mesh)
