@@ -359,3 +359,19 @@ def test_rigid_motion_of_the_rest_state_moves_the_solution_with_it():
     q = EmuOracle(mesh, OracleParams(weight_mode=0)).solve(0.6, tol=1e-11).q
     qm = EmuOracle(moved, OracleParams(weight_mode=0)).solve(0.6, tol=1e-11).q
     assert np.abs(qm - (q @ R0.T + t0)).max() <= 1e-9 * _diag(mesh)
+
+
+def test_scaling_the_mesh_or_the_moduli_leaves_the_shape_unchanged():
+    # E(F) is a sum of V_i times per-volume densities, with w_i = V_i, and
+    # alpha and kappa are multiples of the smallest shear modulus: scaling
+    # every length by s scales every term by s^3, and scaling every Young's
+    # modulus scales every term alike, so the stationary F is unchanged and
+    # the positions scale with the mesh
+    mesh = box_beam(2, 2, 5, activation=0.6)
+    q = EmuOracle(mesh, OracleParams(weight_mode=0)).solve(0.6, tol=1e-11).q
+    big = dataclasses.replace(mesh, rest_pos=2.0 * mesh.rest_pos)
+    qb = EmuOracle(big, OracleParams(weight_mode=0)).solve(0.6, tol=1e-11).q
+    assert np.abs(qb - 2.0 * q).max() <= 1e-9 * _diag(big)
+    stiff = dataclasses.replace(mesh, youngs=37.0 * mesh.youngs)
+    qs = EmuOracle(stiff, OracleParams(weight_mode=0)).solve(0.6, tol=1e-11).q
+    assert np.abs(qs - q).max() <= 1e-9 * _diag(mesh)
