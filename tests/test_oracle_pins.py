@@ -375,3 +375,14 @@ def test_scaling_the_mesh_or_the_moduli_leaves_the_shape_unchanged():
     stiff = dataclasses.replace(mesh, youngs=37.0 * mesh.youngs)
     qs = EmuOracle(stiff, OracleParams(weight_mode=0)).solve(0.6, tol=1e-11).q
     assert np.abs(qs - q).max() <= 1e-9 * _diag(mesh)
+
+
+def test_small_activations_act_linearly():
+    # around the rest state the response is linear in a: doubling a small
+    # activation doubles the displacement up to O(a^2)
+    mesh = box_beam(2, 2, 5)
+    o = EmuOracle(mesh, OracleParams(weight_mode=0))
+    u1 = o.solve(1e-4, tol=1e-10).q - mesh.rest_pos
+    u2 = o.solve(2e-4, tol=1e-10).q - mesh.rest_pos
+    assert np.abs(u2 - 2.0 * u1).max() <= 1e-3 * np.abs(u1).max()
+    assert np.abs(u1).max() > 0.0
