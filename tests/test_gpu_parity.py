@@ -292,3 +292,33 @@ def test_a_single_tet_with_one_pinned_face(emu):
         assert st.status == 0
         err = np.abs(s.positions() - r.q).max() / _diag(mesh)
         assert err <= (1e-4 if prec else 1e-9), (prec, err)
+
+
+# ------------------------------------------------------- frame and scale --
+def test_fp64_path_matches_oracle_on_a_moved_and_scaled_mesh(emu):
+    # the GPU path against the oracle after a rigid motion (rotation of the
+    # rest mesh and its fibers, then a translation) and a change of length
+    # scale; the pins are the same vertices
+    import dataclasses
+
+    mesh = box_beam(2, 2, 5, activation=0.6)
+    rng = np.random.default_rng(9)
+    R0, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    R0 *= np.sign(np.linalg.det(R0))
+    for rest, fib in ((mesh.rest_pos @ R0.T + np.array([0.3, -0.2, 0.1]), mesh.fiber_dir @ R0.T),
+                      (2.0 * mesh.rest_pos, mesh.fiber_dir)):
+        moved = dataclasses.replace(mesh, rest_pos=rest, fiber_dir=fib)
+        o, r = _oracle(moved, 0.6)
+        s, st = _solve_gpu(emu, moved, 0.6)
+        assert st.rel_residual <= 1e-11
+        assert np.abs(s.positions() - r.q).max() / _diag(moved) <= 1e-9
+        s.close()
+
+
+def test_fp64_result_does_not_depend_on_the_first_trial_step(emu):
+    mesh = box_beam(2, 2, 6, activation=0.5)
+    s1, _ = _solve_gpu(emu, mesh, 0.5, ls_sigma0=1.0)
+    s4, _ = _solve_gpu(emu, mesh, 0.5, ls_sigma0=4.0)
+    assert np.abs(s1.positions() - s4.positions()).max() / _diag(mesh) <= 1e-9
+    s1.close()
+    s4.close()
