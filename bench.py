@@ -183,6 +183,12 @@ def solver_nnz(mesh):
     return int(pairs.size + fixed.sum())
 
 
+def threads_used(cpu_s, wall_s):
+    """Threads a host computation kept busy on average: process CPU time (all
+    threads) over wall time, at least 1."""
+    return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
+
+
 def cpu_baseline(workload_name, budget_s=15.0):
     """FP64 oracle on a bounded sample of the workload (tet-iters/s)."""
     from oracle import EmuOracle, OracleParams
@@ -195,7 +201,7 @@ def cpu_baseline(workload_name, budget_s=15.0):
         sample = "box beam 4x4x16, ramp frames"
     o = EmuOracle(mesh, OracleParams(alpha_rel=1.0, weight_mode=0))
     F = None
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     tets_iters = 0
     frames = 0
     for f in range(1, mesh.activations.shape[0]):
@@ -206,9 +212,10 @@ def cpu_baseline(workload_name, budget_s=15.0):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    cores = os.cpu_count()
+    cores = threads_used(time.process_time() - c0, dt)
     return {"value": tets_iters / dt, "unit": "tet-iters/s", "cores": cores, "kind": "oracle",
-            "sample": f"{sample}; frames 1..{frames} ({tets_iters} tet-iters, {dt:.1f} s)"}
+            "sample": f"{sample}; frames 1..{frames} ({tets_iters} tet-iters, {dt:.1f} s; "
+                      f"{os.cpu_count()} host cores, {cores} busy on average)"}
 
 
 def batch_desc(meshes, tol):
@@ -250,7 +257,7 @@ def run_reference(args, rank, world):
     for _ in range(args.warmup):
         r = o.solve(mesh.activations[f], F0=F, tol=args.tol, max_newton=5000)
         F, f = r.F, f % (nf - 1) + 1
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     tet_iters = 0
     for _ in range(args.steps):
         r = o.solve(mesh.activations[f], F0=F, tol=args.tol, max_newton=5000)
@@ -258,7 +265,7 @@ def run_reference(args, rank, world):
         tet_iters += mesh.n_tets * r.iterations
     dt = time.perf_counter() - t0
     value = tet_iters / dt
-    cb = {"value": value, "unit": "tet-iters/s", "cores": os.cpu_count(), "kind": "oracle",
+    cb = {"value": value, "unit": "tet-iters/s", "cores": threads_used(time.process_time() - c0, dt), "kind": "oracle",
           "sample": f"{sample}; {args.steps} timed frames after {args.warmup} warm-up frames "
                     f"({tet_iters} tet-iters, {dt:.1f} s)"}
     line = {"impl": "reference", "metric": "tet-iters/s", "value": value, "unit": "tet-iters/s",
@@ -276,20 +283,21 @@ def run_reference_batch(args):
 
     meshes = batch_set(count=args.meshes, seed=3)
     order = iter(range(len(meshes)))
-    done, tet_iters, dt = 0, 0, 0.0
+    done, tet_iters, dt, cpu = 0, 0, 0.0, 0.0
     for phase, count in (("warmup", args.warmup), ("timed", args.steps)):
         for _ in range(count):
             k = next(order)
             mesh = meshes[k]
-            t0 = time.perf_counter()
+            t0, c0 = time.perf_counter(), time.process_time()
             r = EmuOracle(mesh, OracleParams(alpha_rel=1.0, weight_mode=0)).solve(
                 mesh.activations[0], tol=args.tol, max_newton=5000)
             if phase == "timed":
                 dt += time.perf_counter() - t0
+                cpu += time.process_time() - c0
                 tet_iters += mesh.n_tets * r.iterations
                 done += 1
     value = tet_iters / dt if dt > 0 else 0.0
-    cb = {"value": value, "unit": "tet-iters/s", "cores": os.cpu_count(), "kind": "oracle",
+    cb = {"value": value, "unit": "tet-iters/s", "cores": threads_used(cpu, dt), "kind": "oracle",
           "sample": f"meshes {args.warmup}..{args.warmup + done - 1} of the batch set, from rest "
                     f"({tet_iters} tet-iters, {dt:.1f} s; setup and solve timed)"}
     line = {"impl": "reference", "metric": "tet-iters/s", "value": value, "unit": "tet-iters/s",
