@@ -16,7 +16,14 @@ Reported:
              the host-clocked interval.
   roofline   the kernel with the most device time: algorithmic bytes per
              launch over its average CUDA-event duration, against the
-             measured HBM copy peak.
+             measured HBM copy peak; labelled latency-bound (with its DRAM
+             fraction beside it) when ncu shows its operands stay in L2.
+  per_tet_kernels_hbm, whole_iteration
+             each per-tet kernel's fraction of the HBM peak, and one Newton
+             iteration's algorithmic bytes over its device time.
+  error_vs_oracle
+             positions of the benchmarked configuration on the CPU
+             baseline's sample against the oracle's (re-converged to 1e-10).
   cpu_baseline / --impl reference: the FP64 CPU oracle on a bounded sample of
              the same workload.
 
@@ -115,6 +122,79 @@ def algorithmic_bytes(phase, mixed, m, n, nnz, cg_iters):
     return None
 
 
+# per-tet kernels launched per launch of a profiled phase (the update phase
+# also launches the per-vertex position update)
+PER_TET_KERNELS = {"grad": 1.0, "syrk": 1.0, "dir": 1.0, "ls": 1.0, "update": 0.5}
+
+
+def per_tet_fractions(prof, mixed, m, n, nnz, peak):
+    """Each per-tet kernel's algorithmic bytes per launch over its average
+    CUDA-event duration, against the HBM peak."""
+    out = {}
+    for name, per in PER_TET_KERNELS.items():
+        ms, nl = prof.get(name, (0.0, 0))
+        if nl <= 0 or ms <= 0:
+            continue
+        launches = nl * per
+        b = algorithmic_bytes(name, mixed, m, n, nnz, 0.0)
+        us = 1e3 * ms / launches
+        gbs = b / (us * 1e-6) / 1e9
+        out[name] = {"bytes_per_launch": b, "us_per_launch": round(us, 2), "achieved_gbs": round(gbs, 1),
+                     "frac": round(gbs / peak, 3)}
+    return out
+
+
+def dominant_roofline(prof, mixed, m, n, nnz, cg_total, peak, peak_kind, traffic_table):
+    """Roofline entry of the phase with the most device time. The coupling
+    solve's system (CSR, vectors, coarse rows) is L2-resident on the
+    benchmark meshes: when its measured DRAM traffic is far below the
+    algorithmic bytes it is reported as latency-bound, with both fractions."""
+    name, (ms_tot, nl) = max(prof.items(), key=lambda kv: kv[1][0])
+    total = algorithmic_bytes(name, mixed, m, n, nnz, cg_total)
+    if total is None or nl <= 0 or ms_tot <= 0:
+        return None
+    per_launch = total / nl if name == "pcg" else total
+    avg_s = ms_tot / nl / 1e3
+    achieved = per_launch / avg_s / 1e9
+    tr = traffic_table.get(name)
+    traffic = tr[0] if tr else None
+    bound = "hbm"
+    if traffic is not None and traffic < 0.25 * per_launch:
+        bound = "latency"
+    roof = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "traffic_source": tr[1] if tr else None,
+            "peak_source": peak_kind, "bytes_per_launch": per_launch, "avg_launch_ms": 1e3 * avg_s,
+            "share_of_device_time": ms_tot / max(1e-9, sum(v[0] for v in prof.values()))}
+    if traffic is not None:
+        roof["dram_gbs"] = traffic / avg_s / 1e9
+        roof["dram_frac"] = roof["dram_gbs"] / peak
+    if bound == "latency":
+        roof["note"] = ("L2-resident: DRAM traffic per launch is far below the algorithmic bytes, so frac "
+                        "measures how fast the solve streams its operands from L2; the limit is grid-barrier "
+                        "and L2 latency")
+    return roof
+
+
+def whole_iteration(prof, mixed, m, n, nnz, cg_total, iters, peak, value):
+    """One Newton iteration against the HBM roofline: the algorithmic bytes
+    of every per-tet kernel and of the coupling solve over the device time
+    per iteration, and the measured tet-iters/s against the scope's ceiling
+    peak / (560 + 140 N_cg) bytes per tet-iteration."""
+    if iters <= 0:
+        return None
+    b = 0.0
+    for name, per in PER_TET_KERNELS.items():
+        ms, nl = prof.get(name, (0.0, 0))
+        b += algorithmic_bytes(name, mixed, m, n, nnz, 0.0) * nl * per
+    b += algorithmic_bytes("pcg", mixed, m, n, nnz, cg_total)
+    b /= iters
+    t = sum(v[0] for v in prof.values()) / 1e3 / iters
+    ncg = cg_total / iters
+    ceiling = peak * 1e9 / (560.0 + 140.0 * ncg)
+    return {"bytes_per_iter": b, "us_per_iter": 1e6 * t, "achieved_gbs": b / t / 1e9, "frac": b / t / 1e9 / peak,
+            "scope_ceiling_tet_iters_s": ceiling, "frac_of_scope_ceiling": value / ceiling}
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -189,8 +269,12 @@ def threads_used(cpu_s, wall_s):
     return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
 
 
-def cpu_baseline(workload_name, budget_s=15.0):
-    """FP64 oracle on a bounded sample of the workload (tet-iters/s)."""
+def cpu_baseline(workload_name, budget_s=15.0, ref_tol=1e-10):
+    """FP64 oracle on a bounded sample of the workload (tet-iters/s).
+
+    Returns the baseline entry and, for the parity figure of the line, the
+    sample mesh, the frames it solved and the oracle's positions of the last
+    of them re-converged (untimed) to ``ref_tol`` from its own state."""
     from oracle import EmuOracle, OracleParams
 
     if workload_name in ("mtu", "mtu_small"):
@@ -213,9 +297,34 @@ def cpu_baseline(workload_name, budget_s=15.0):
             break
     dt = time.perf_counter() - t0
     cores = threads_used(time.process_time() - c0, dt)
-    return {"value": tets_iters / dt, "unit": "tet-iters/s", "cores": cores, "kind": "oracle",
-            "sample": f"{sample}; frames 1..{frames} ({tets_iters} tet-iters, {dt:.1f} s; "
-                      f"{os.cpu_count()} host cores, {cores} busy on average)"}
+    ref = o.solve(mesh.activations[frames], F0=F, tol=ref_tol, max_newton=20000)
+    cb = {"value": tets_iters / dt, "unit": "tet-iters/s", "cores": cores, "kind": "oracle",
+          "sample": f"{sample}; frames 1..{frames} ({tets_iters} tet-iters, {dt:.1f} s; "
+                    f"{os.cpu_count()} host cores, {cores} busy on average)"}
+    return cb, {"mesh": mesh, "frames": frames, "q_ref": ref.q, "ref_tol": ref_tol, "sample": sample}
+
+
+def error_vs_oracle(emu, params, ref):
+    """Positions of the GPU path (the bench's parameters) on the baseline's
+    sample, frames 1..k warm-started as the oracle solved them, against the
+    oracle's frame k: max over vertices of |q_gpu - q_oracle| over the rest
+    bounding-box diagonal (the parity metric of the tests)."""
+    mesh = ref["mesh"]
+    s = emu.Solver(mesh, params)
+    st = None
+    for f in range(1, ref["frames"] + 1):
+        s.set_activation(mesh.activations[f])
+        st = s.solve(raise_on_error=False)
+    q = s.positions()
+    s.close()
+    diag = float(np.linalg.norm(mesh.rest_pos.max(0) - mesh.rest_pos.min(0)))
+    disp = float(np.abs(ref["q_ref"] - mesh.rest_pos).max())
+    err = float(np.abs(q - ref["q_ref"]).max())
+    return {"max_pos_err_rel_diag": err / diag, "max_pos_err_rel_disp": err / disp if disp > 0 else None,
+            "bound_rel_diag": 1e-4 if params.precision == emu.PRECISION_MIXED else 1e-9,
+            "gpu_rel_residual": float(st.rel_residual), "gpu_status": int(st.status),
+            "oracle_tol": ref["ref_tol"], "frame": ref["frames"],
+            "sample": f"{ref['sample']}; frame {ref['frames']} after warm-started frames 1..{ref['frames']}"}
 
 
 def batch_desc(meshes, tol):
@@ -500,9 +609,9 @@ def main():
         run_reference(args, rank, world)
         return
 
-    cb = None
+    cb, cb_ref = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(args.workload)  # before any GPU work (no fork after CUDA init)
+        cb, cb_ref = cpu_baseline(args.workload)  # before any GPU work (no fork after CUDA init)
 
     import torch
 
@@ -589,25 +698,19 @@ def main():
     value = tet_iters / (total_ms / 1e3)
     e2e_value = tet_iters / total_e2e
 
-    # roofline of the dominant kernel phase (device time from the library's
-    # per-phase CUDA events on the solver's stream)
+    # roofline (device times from the library's per-phase CUDA events on the
+    # solver's stream, profiled frames)
     peak, peak_kind = hbm_peak()
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    name, (ms_tot, nl) = dom
     nnz = solver_nnz(mesh)
-    total_bytes = algorithmic_bytes(name, mixed, m, n, nnz, float(prof_cg))
-    roof = None
-    if total_bytes is not None and nl > 0 and ms_tot > 0:
-        # per-tet phases: one launch moves total_bytes; the ACAP solve's
-        # bytes are summed over all its CG iterations
-        bytes_per_launch = total_bytes / nl if name == "pcg" else total_bytes
-        achieved = bytes_per_launch / (ms_tot / nl / 1e3) / 1e9
-        traffic = NCU_TRAFFIC.get(name) if (mixed and args.workload == "mtu") else None
-        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic[0] if traffic else None,
-                "traffic_source": traffic[1] if traffic else None, "peak_source": peak_kind,
-                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": ms_tot / nl,
-                "share_of_device_time": ms_tot / max(1e-9, sum(v[0] for v in prof.values()))}
+    cg_per_iter = prof_cg / max(prof_its, 1)
+    dev_ms = sum(v[0] for v in prof.values())
+    per_tet = per_tet_fractions(prof, mixed, m, n, nnz, peak)
+    roof = dominant_roofline(prof, mixed, m, n, nnz, float(prof_cg), peak, peak_kind,
+                             NCU_TRAFFIC if (mixed and args.workload == "mtu") else {})
+    whole = whole_iteration(prof, mixed, m, n, nnz, float(prof_cg), prof_its, peak, value)
+    err = None
+    if cb_ref is not None:
+        err = error_vs_oracle(emu, params, cb_ref)
     line = {
         "metric": "tet-iters/s", "value": value, "unit": "tet-iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -624,6 +727,10 @@ def main():
         "phase_launches": {k: v[1] for k, v in prof.items()},
         "phase_source": f"{n_prof} profiled frames after the timed ones ({prof_its} Newton iterations)",
         "roofline": roof,
+        "per_tet_kernels_hbm": per_tet,
+        "whole_iteration": whole,
+        "cg_iters_per_newton_iter": round(cg_per_iter, 2),
+        "error_vs_oracle": err,
         "cpu_baseline": cb,
         "e2e": {"value": e2e_value, "unit": "tet-iters/s", "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 24 * n},
         "gpu_launches": int(launches),

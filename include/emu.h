@@ -352,11 +352,15 @@ int emu_eval_polar(const double* F, int64_t n, double* R, double* s, void* strea
  * reserved on every GPU that loads the library until the process exits. A
  * mesh needs 96 n_tets + 144 n_verts bytes plus a few KB; larger meshes are
  * rejected with EMU_ERR_INVALID_ARG. The first call on a device looks up the
- * array's device address; make that first call before any stream capture.
- * Every call uses the same array and it keeps the last call's contents, so
- * calls that overlap on the GPU (other streams, other threads, other
- * handles) race: serialise them. Returns EMU_ERR_PCG if the CG iteration
- * cap is reached, EMU_ERR_TIMEOUT if a bounded device wait ran out. */
+ * array's device address (later calls outside stream capture look it up
+ * again); make that first call before any stream capture. The device current
+ * at the call must be the one the handle was created on (else
+ * EMU_ERR_INVALID_ARG). A device reset (cudaDeviceReset) invalidates every
+ * handle, this one included. Every call uses the same array and it keeps the
+ * last call's contents, so calls that overlap on the GPU (other streams,
+ * other threads, other handles) race: serialise them. Returns EMU_ERR_PCG if
+ * the CG iteration cap is reached, EMU_ERR_TIMEOUT if a bounded device wait
+ * ran out; every failure leaves its reason in emu_last_error(). */
 int emu_acap_solve_noalloc(emu_handle* h, const double* F_device, double* q_device, void* stream);
 
 /* ---- profiling ----------------------------------------------------------

@@ -58,6 +58,7 @@ struct Laplacian {
 // Read-only view of a handle's mesh operator, for entry points that live
 // outside the handle's translation unit.
 struct AcapView {
+  int device;            // CUDA device the handle was created on
   int64_t n, m;
   const int4* tet;
   const double* Dinv;    // 9m structure of arrays

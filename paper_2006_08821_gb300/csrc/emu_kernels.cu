@@ -147,6 +147,8 @@ __global__ void __launch_bounds__(128) k_grad(TetArgs<TW> a) {
   double acc[1] = {0.0};
   int bad = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    // tets of bones are no variables of their own (their g, y, U stay zero)
+    if (a.tkind && a.tkind[i] != kTetDeformable) continue;
     const int4 t = a.tet[i];
     double D[9], R[9], sv[6], S[9], F[9], A[9];
     load_dinv(a.Dinv, m, i, D);
@@ -430,6 +432,22 @@ __global__ void __launch_bounds__(128) k_dir(TetArgs<TW> a) {
   const int64_t m = a.m;
   double acc[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (a.tkind) {
+      const int32_t kind = a.tkind[i];
+      if (kind != kTetDeformable) {
+        // a free bone's tet takes the bone's direction, a pinned bone's tet
+        // none; their g . d is the bone's (summed by the bone kernel)
+        double dv[9], D[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          dv[k] = kind >= 0 ? a.bone_st[(size_t)kind * kBoneStride + kBoneD + k] : 0.0;
+          a.d[k * m + i] = (TW)dv[k];
+        }
+        load_dinv(a.Dinv, m, i, D);
+        write_corners(a.contrib, i, a.w[i], dv, D);
+        continue;
+      }
+    }
     TW gm[48];
 #pragma unroll
     for (int k = 0; k < 48; ++k) gm[k] = a.gam[k * m + i];
@@ -619,6 +637,7 @@ __global__ void __launch_bounds__(128) k_gref(TetArgs<double> a, const double* q
   const int64_t m = a.m;
   double acc[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (a.tkind && a.tkind[i] != kTetDeformable) continue;  // bones: summed per bone elsewhere
     double D[9], A[9];
     load_dinv(a.Dinv, m, i, D);
     gather_defgrad(q0, a.tet[i], D, A);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "emu_bones.h"
 #include "emu_internal.h"
 #include "emu_reduce.cuh"
 
@@ -34,6 +35,8 @@ template <typename TW> struct TetArgs {
   const double* z;      // 48 Woodbury coefficients
   DevScalars* sc;
   double* partials;     // per-block partial sums
+  const int32_t* tkind = nullptr;    // bones: kind of each tet (null without bones)
+  const double* bone_st = nullptr;   // bones: free bones' iteration state
 };
 
 void launch_rhs_from_state(const TetArgs<double>& a, int grid, cudaStream_t st);

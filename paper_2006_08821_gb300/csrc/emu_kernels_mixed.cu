@@ -110,6 +110,8 @@ __global__ void __launch_bounds__(128, 4) k_grad_m(MixArgs a) {
   double acc[1] = {0.0};
   int bad = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    // tets of bones are no variables of their own (their g, y, U stay zero)
+    if (a.tkind && a.tkind[i] != kTetDeformable) continue;
     const int4 t = a.tet[i];
     float D[9], R[9], e6[6];
     load9f(a.Dinv, m, i, D);
@@ -413,6 +415,22 @@ __global__ void __launch_bounds__(128, 8) k_dir_m(MixArgs a) {
   double acc[1] = {0.0};
   const float* __restrict__ Uw = a.Uw;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (a.tkind) {
+      const int32_t kind = a.tkind[i];
+      if (kind != kTetDeformable) {
+        // a free bone's tet takes the bone's direction, a pinned bone's tet
+        // none; their g . d is the bone's (summed by the bone kernel)
+        float dv[9], D[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          dv[k] = kind >= 0 ? (float)a.bone_st[(size_t)kind * kBoneStride + kBoneD + k] : 0.f;
+          a.d[k * m + i] = dv[k];
+        }
+        load9f(a.Dinv, m, i, D);
+        corners_f(a.contrib32, i, a.w[i], dv, D);
+        continue;
+      }
+    }
     float v[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) v[k] = 0.f;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "emu_bones.h"
 #include "emu_internal.h"
 
 namespace emu {
@@ -39,6 +40,11 @@ struct MixArgs {
   const double* z;     // 48
   DevScalars* sc;
   double* partials;
+  // bones (Sec. 3.3; null without bones): kind of each tet (kTetDeformable,
+  // kTetPinnedBone or the free bone's index) and the free bones' iteration
+  // state (their directions at kBoneD)
+  const int32_t* tkind = nullptr;
+  const double* bone_st = nullptr;
 };
 
 void launch_grad_mixed(const MixArgs& a, int grid, cudaStream_t st);

@@ -386,3 +386,35 @@ def test_small_activations_act_linearly():
     u2 = o.solve(2e-4, tol=1e-10).q - mesh.rest_pos
     assert np.abs(u2 - 2.0 * u1).max() <= 1e-3 * np.abs(u1).max()
     assert np.abs(u1).max() > 0.0
+
+
+# ------------------------------------------------------- p15: materials --
+def test_lame_parameters_hand_computed():
+    # mu = E / (2 (1 + nu)), lambda = E nu / ((1 + nu)(1 - 2 nu)), worked by hand
+    mu, lam = lame(np.array([6e5, 1e10, 1e8]), np.array([0.45, 0.3, 0.0]))
+    np.testing.assert_allclose(mu, [600000.0 / 2.9, 1e10 / 2.6, 5e7], rtol=1e-15)
+    np.testing.assert_allclose(lam, [270000.0 / 0.145, 3e9 / 0.52, 0.0], rtol=1e-15, atol=0.0)
+    np.testing.assert_allclose(mu[0], 206896.55172413793, rtol=1e-15)
+    np.testing.assert_allclose(lam[0], 1862068.9655172413, rtol=1e-15)
+
+
+@pytest.mark.parametrize("E,nu", [(6e5, 0.45), (1e10, 0.3), (1e8, 0.2)])
+def test_small_strain_uniaxial_stress_recovers_youngs_modulus_and_poisson_ratio(E, nu):
+    # The definitions of E and nu: under a small uniaxial stress the axial
+    # stress over the axial strain is E, and the lateral strain over the
+    # axial strain is -nu. The stress comes from the oracle's neo-Hookean
+    # Piola stress with the oracle's Lame parameters (no fiber term), so a
+    # wrong lame() or a wrong Psi' fails here.
+    mu, lam = lame(E, nu)
+    eps = 1e-7
+    u = np.array([1.0, 0.0, 0.0])
+
+    def lateral_stress(et):
+        F = np.diag([1.0 + eps, 1.0 + et, 1.0 + et])
+        return dpsi(F[None], np.array([mu]), np.array([lam]), np.zeros(1), u[None])[0][1, 1]
+
+    et = so.brentq(lateral_stress, -eps, eps, xtol=1e-22, rtol=1e-15)
+    F = np.diag([1.0 + eps, 1.0 + et, 1.0 + et])
+    P = dpsi(F[None], np.array([mu]), np.array([lam]), np.zeros(1), u[None])[0]
+    np.testing.assert_allclose(P[0, 0] / eps, E, rtol=1e-5)
+    np.testing.assert_allclose(-et / eps, nu, rtol=1e-5)

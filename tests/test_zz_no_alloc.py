@@ -62,6 +62,37 @@ def test_noalloc_coupling_solve_matches_solver_positions(emu, mesh_fn):
     s.close()
 
 
+def test_noalloc_coupling_solve_on_a_mixed_precision_handle(emu):
+    # a mixed handle keeps an FP64 coupling operator built from its FP32
+    # D_m^-1 and weights; the allocation-free call solves Eq. 4 with that
+    # operator for the handle's final F, which must give the positions the
+    # mixed solve reports (both coupling solves converged to 1e-10)
+    import torch
+
+    mesh = box_beam(4, 4, 16, activation=0.5)
+    s = emu.Solver(mesh, emu.Params(tol_rel_residual=1e-6, pcg_tol=1e-10, precision=emu.PRECISION_MIXED))
+    s.set_activation(0.5)
+    st = s.solve()
+    assert st.status == 0
+    q_ref = s.positions()
+    _, _, F = s.element_state()
+    dev = torch.device("cuda:0")
+    tF = torch.tensor(F.reshape(-1, 9), dtype=torch.float64, device=dev)
+    diag = float(np.linalg.norm(mesh.rest_pos.max(0) - mesh.rest_pos.min(0)))
+    outs = []
+    for _ in range(2):
+        tq = torch.full((mesh.n_verts, 3), float("nan"), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        rc = s.acap_solve_noalloc(tF.data_ptr(), tq.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        assert rc == 0, (rc, s.lib.emu_last_error())
+        q = tq.cpu().numpy()
+        err = np.abs(q - q_ref).max() / diag
+        assert err <= 1e-8, err
+        outs.append(q)
+    np.testing.assert_array_equal(outs[0], outs[1])
+    s.close()
+
+
 def test_noalloc_rejects_a_mesh_larger_than_its_fixed_scratch(emu):
     # 401,920 tets need 96 bytes per tet + 144 per vertex: more than the
     # fixed 32 MiB array, so the call must refuse before touching memory
