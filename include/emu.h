@@ -98,13 +98,20 @@ typedef struct {
   int64_t n_fixed;
   const int32_t* fixed_verts;
   const double* fixed_pos;
-  /* Bones and joints (Sec. 3.3): bone_id (n_tets; -1 = deformable, b >= 0 =
-   * bone b) may be NULL; n_joints joints between bones, each with a type
-   * (0 ball, 1 hinge), two bone ids, a point (metres) and, for a hinge, a
-   * unit axis and the half-length of its two axis points. This version's
-   * GPU path has no bones or joints yet: a mesh with a bone tet or a joint
-   * is rejected with EMU_ERR_NOT_IMPLEMENTED before any device work. All
-   * may be NULL / 0. */
+  /* Bones and joints (Sec. 3.3). bone_id (n_tets; -1 = deformable, b >= 0
+   * = bone b, ids contiguous from 0) may be NULL. Every tet of a bone shares
+   * the bone's single deformation gradient F_b; all of a bone's tets have one
+   * material and no vertex belongs to two bones. A bone's vertices are either
+   * all pinned (the bone stays put, F_b = I) or none (a free bone, at most 4;
+   * k_modes must be 48). Activations must be 0 on bone tets.
+   * n_joints joints, each with a type (0 ball, 1 hinge), two bone ids (at
+   * least one free), a point (metres) and, for a hinge, an axis (normalised
+   * on copy) and the half-length of its two axis points (at most 16 joint
+   * points). At each joint point the least-squares affine fits of the two
+   * bones' vertex positions coincide: hard during Newton, a penalty in the
+   * final solve (see eps_bone, eps_joint in emu_params). After a solve the
+   * positions are those of the final coupling solve: each free bone's
+   * vertices are exactly F_b Q_v + t_b. All may be NULL / 0. */
   const int32_t* bone_id;
   int32_t n_joints;
   const int32_t* joint_type;        /* n_joints */
@@ -151,7 +158,14 @@ typedef struct {
  *                   tolerance for the rest of the call.
  *   q_refresh       every q_refresh iterations, and before convergence is
  *                   declared, q is re-solved exactly from the current F
- *                   (default 32). */
+ *                   (default 32).
+ *   eps_bone        slack of the bone rows during Newton (Sec. 3.3, < 0;
+ *                   default -1e-3): each bone tet's ACAP weight grows by
+ *                   Vbar / |eps_bone| (Vbar the mean rest volume).
+ *   eps_joint       slack of the joint rows in the final coupling solve
+ *                   (Sec. 3.3, < 0; default -1e-4): the joints become the
+ *                   penalty Vbar^(1/3) / |eps_joint| |J q|^2 while every
+ *                   bone's vertices follow its affine map exactly. */
 typedef struct {
   double alpha_rel;
   int32_t weight_mode;
@@ -170,6 +184,8 @@ typedef struct {
   uint64_t seed;
   double dq_tol;
   int32_t q_refresh;
+  double eps_bone;
+  double eps_joint;
 } emu_params;
 
 /* Per-solve statistics. */
@@ -360,7 +376,8 @@ int emu_eval_polar(const double* F, int64_t n, double* R, double* s, void* strea
  * last call's contents, so calls that overlap on the GPU (other streams,
  * other threads, other handles) race: serialise them. Returns EMU_ERR_PCG if
  * the CG iteration cap is reached, EMU_ERR_TIMEOUT if a bounded device wait
- * ran out; every failure leaves its reason in emu_last_error(). */
+ * ran out; every failure leaves its reason in emu_last_error(). A handle
+ * whose mesh has joints is refused with EMU_ERR_NOT_IMPLEMENTED. */
 int emu_acap_solve_noalloc(emu_handle* h, const double* F_device, double* q_device, void* stream);
 
 /* ---- profiling ----------------------------------------------------------

@@ -101,6 +101,8 @@ class emu_params(C.Structure):
         ("seed", C.c_uint64),
         ("dq_tol", C.c_double),
         ("q_refresh", C.c_int32),
+        ("eps_bone", C.c_double),
+        ("eps_joint", C.c_double),
     ]
 
 
@@ -212,6 +214,8 @@ class Params:
     seed: int = 12345
     dq_tol: float = 5e-2
     q_refresh: int = 32
+    eps_bone: float = -1e-3
+    eps_joint: float = -1e-4
 
     def to_c(self) -> emu_params:
         p = emu_params()

@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include "emu_bones.h"
+#include "emu_kernels.cuh"
 #include "emu_math.cuh"
 #include "emu_reduce.cuh"
 
@@ -39,31 +40,24 @@ __device__ void bone_state(const BoneArgs& a, int b, bool ident, double* R, doub
     return;
   }
   const int64_t i = a.rep[b], m = a.m;
+  double sv[6];
   if (a.mixed) {
-    const float4 qq = a.quat[i];
-    double qx = qq.x, qy = qq.y, qz = qq.z, qw = qq.w;
-    const double nn = 1.0 / sqrt(qx * qx + qy * qy + qz * qz + qw * qw);
-    qx *= nn;
-    qy *= nn;
-    qz *= nn;
-    qw *= nn;
-    quat_to_R(qx, qy, qz, qw, R);
-    quat_rot_minus_I(qx, qy, qz, qw, RmI);
-    double e6[6];
+    const double* o = a.bst + (size_t)b * kBoneStride;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) e6[k] = (double)a.E[k * m + i];
-    sym_from_s(e6, E);
+    for (int k = 0; k < 9; ++k) R[k] = o[kBoneR + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sv[k] = o[kBoneS + k];
   } else {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      R[k] = a.R[k * m + i];
-      RmI[k] = R[k] - ((k % 4 == 0) ? 1.0 : 0.0);
-    }
-    double sv[6];
+    for (int k = 0; k < 9; ++k) R[k] = a.R[k * m + i];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) sv[k] = a.s[k * m + i] - (k < 3 ? 1.0 : 0.0);
-    sym_from_s(sv, E);
+    for (int k = 0; k < 6; ++k) sv[k] = a.s[k * m + i];
   }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) RmI[k] = R[k] - ((k % 4 == 0) ? 1.0 : 0.0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sv[k] -= 1.0;
+  sym_from_s(sv, E);
 #pragma unroll
   for (int k = 0; k < 9; ++k) S[k] = E[k] + ((k % 4 == 0) ? 1.0 : 0.0);
 }
@@ -254,36 +248,147 @@ __global__ void k_bone_dir(BoneArgs a, const double* __restrict__ z, double* gtd
   }
 }
 
-// ------------------------------------------------------------ state sync --
-__global__ void __launch_bounds__(256) k_bone_sync_state(BoneArgs a, const int32_t* __restrict__ tkind) {
+// ------------------------------------------------------------ line search --
+__global__ void __launch_bounds__(256) k_bone_ls(BoneArgs a, const float* __restrict__ dq32, double rho,
+                                                 double* __restrict__ out) {
+  __shared__ double sFmI[kMaxFreeBones][9], sd[kMaxFreeBones][9];
+  double acc[kLsNV];
+#pragma unroll
+  for (int k = 0; k < kLsNV; ++k) acc[k] = 0.0;
+  const double s0 = a.sc->sigma_start;
+  if (threadIdx.x < a.nfb) {
+    const int b = threadIdx.x;
+    double R[9], RmI[9], S[9], E[9], RE[9];
+    bone_state(a, b, false, R, RmI, S, E);
+    matmul3(R, E, RE);
+    const double* d = a.bst + (size_t)b * kBoneStride + kBoneD;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      sFmI[b][k] = RmI[k] + RE[k];  // F_b - I
+      sd[b][k] = d[k];
+    }
+    if (blockIdx.x == 0) {
+      // the bone's elastic energy change, term by term (one evaluation for all its tets)
+      double Sinv[9], Rtd[9], M[9];
+      const double lnJ = log(inv3(S, Sinv));
+      matTmul3(R, d, Rtd);
+      matmul3(Sinv, Rtd, M);
+      const double trM = M[0] + M[4] + M[8], e2 = inv2(M), detM = det3(M);
+      double FFd = 0.0, dd = 0.0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        FFd += (S[k] - Sinv[k]) * Rtd[k];
+        dd += d[k] * d[k];
+      }
+      double sig = s0;
+      for (int j = 0; j < kLsTrials; ++j) {
+        const double x = sig * trM + sig * sig * e2 + sig * sig * sig * detM;
+        if (x > -1.0) {
+          const double dl = log1p(x);
+          const double nh = sig * FFd + 0.5 * sig * sig * dd - sig * sig * e2 - sig * sig * sig * detM + x_minus_log1p(x);
+          acc[j] += a.Vb[b] * (a.mu[b] * nh + 0.5 * a.lam[b] * dl * (2.0 * lnJ + dl));
+        } else {
+          acc[j] += 1e300;
+        }
+        sig *= rho;
+      }
+    }
+  }
+  __syncthreads();
+  // ACAP coefficients of the bones' tets: D = (G q - I) - (F_b - I), dD = G dq - d_b
+  const int64_t m = a.m, nbt = a.bptr[a.nfb];
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nbt; idx += (int64_t)gridDim.x * blockDim.x) {
+    int b = 0;
+    while (b + 1 < a.nfb && idx >= a.bptr[b + 1]) ++b;
+    const int64_t i = a.btets[idx];
+    const int4 t = a.tet[i];
+    const int64_t v[4] = {t.x, t.y, t.z, t.w};
+    double D[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) D[k] = a.Dinv[k * m + i];
+    double cDd = 0.0, cdd = 0.0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const double u3 = a.q[3 * v[3] + r] - a.Q[3 * v[3] + r];
+      const double w3 = (double)dq32[3 * v[3] + r];
+      double du[3], dQ[3], dw[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        du[k] = (a.q[3 * v[k] + r] - a.Q[3 * v[k] + r]) - u3;
+        dQ[k] = a.Q[3 * v[k] + r] - a.Q[3 * v[3] + r];
+        dw[k] = (double)dq32[3 * v[k] + r] - w3;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double AmI = du[0] * D[c] + du[1] * D[3 + c] + du[2] * D[6 + c] +
+                           (dQ[0] * D[c] + dQ[1] * D[3 + c] + dQ[2] * D[6 + c] - (r == c ? 1.0 : 0.0));
+        const double dA = dw[0] * D[c] + dw[1] * D[3 + c] + dw[2] * D[6 + c];
+        const double Dm = AmI - sFmI[b][3 * r + c], dD = dA - sd[b][3 * r + c];
+        cDd += Dm * dD;
+        cdd += dD * dD;
+      }
+    }
+    const double ci = a.c[i];
+    acc[kLsTrials] += ci * cDd;
+    acc[kLsTrials + 1] += ci * cdd;
+  }
+  block_reduce_write<kLsNV>(acc, out + (size_t)blockIdx.x * kLsNV);
+}
+
+// ------------------------------------------------------------ bone state --
+__global__ void k_bone_update(BoneArgs a) {
+  const int b = threadIdx.x;
+  const double sig = a.sc->sigma;
+  if (b >= a.nfb || sig == 0.0) return;
+  double* o = a.bst + (size_t)b * kBoneStride;
+  double R[9], sv[6], S[9], Rtd[9], X[9], Rx[9], Rn[9], Sn[9], sn[6];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R[k] = o[kBoneR + k];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) sv[k] = o[kBoneS + k];
+  sym_from_s(sv, S);
+  matTmul3(R, o + kBoneD, Rtd);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) X[k] = S[k] + sig * Rtd[k];
+  polar_rotation(X, Rx, 1e-15, 40);
+  matTmul3(Rx, X, Sn);
+  s_from_mat(Sn, sn);
+  matmul3(R, Rx, Rn);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) o[kBoneR + k] = Rn[k];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) o[kBoneS + k] = sn[k];
+}
+
+__global__ void k_bone_state_from_tets(BoneArgs a) {
+  const int b = threadIdx.x;
+  if (b >= a.nfb) return;
+  const int64_t i = a.rep[b], m = a.m;
+  double* o = a.bst + (size_t)b * kBoneStride;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) o[kBoneR + k] = a.R[k * m + i];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) o[kBoneS + k] = a.s[k * m + i];
+}
+
+__global__ void __launch_bounds__(256) k_bone_state_to_tets(BoneArgs a, const int32_t* __restrict__ tkind) {
   const int64_t m = a.m;
+  double* R = const_cast<double*>(a.R);
+  double* s = const_cast<double*>(a.s);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t kind = tkind[i];
     if (kind == kTetDeformable) continue;
     if (kind >= 0) {
-      const int64_t r = a.rep[kind];
-      if (r == i) continue;
-      if (a.mixed) {
-        const_cast<float4*>(a.quat)[i] = a.quat[r];
+      const double* o = a.bst + (size_t)kind * kBoneStride;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) const_cast<float*>(a.E)[k * m + i] = a.E[k * m + r];
-      } else {
+      for (int k = 0; k < 9; ++k) R[k * m + i] = o[kBoneR + k];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) const_cast<double*>(a.R)[k * m + i] = a.R[k * m + r];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) const_cast<double*>(a.s)[k * m + i] = a.s[k * m + r];
-      }
+      for (int k = 0; k < 6; ++k) s[k * m + i] = o[kBoneS + k];
     } else {  // tet of a pinned bone: F = I
-      if (a.mixed) {
-        const_cast<float4*>(a.quat)[i] = make_float4(0.f, 0.f, 0.f, 1.f);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) const_cast<float*>(a.E)[k * m + i] = 0.f;
-      } else {
+      for (int k = 0; k < 9; ++k) R[k * m + i] = (k % 4 == 0) ? 1.0 : 0.0;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) const_cast<double*>(a.R)[k * m + i] = (k % 4 == 0) ? 1.0 : 0.0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) const_cast<double*>(a.s)[k * m + i] = k < 3 ? 1.0 : 0.0;
-      }
+      for (int k = 0; k < 6; ++k) s[k * m + i] = k < 3 ? 1.0 : 0.0;
     }
   }
 }
@@ -547,8 +652,22 @@ void launch_bone_dir(const BoneArgs& a, const double* z, double* gtd_out, cudaSt
   k_bone_dir<<<1, 32, 0, st>>>(a, z, gtd_out);
 }
 
-void launch_bone_sync_state(const BoneArgs& a, const int32_t* tkind, cudaStream_t st) {
-  k_bone_sync_state<<<grid_for(a.m, 256), 256, 0, st>>>(a, tkind);
+void launch_bone_ls(const BoneArgs& a, const float* dq32, double rho, double* partials_out, cudaStream_t st) {
+  k_bone_ls<<<kBoneLsBlocks, 256, 0, st>>>(a, dq32, rho, partials_out);
+}
+
+void launch_bone_update(const BoneArgs& a, cudaStream_t st) {
+  if (a.nfb <= 0) return;
+  k_bone_update<<<1, 32, 0, st>>>(a);
+}
+
+void launch_bone_state_from_tets(const BoneArgs& a, cudaStream_t st) {
+  if (a.nfb <= 0) return;
+  k_bone_state_from_tets<<<1, 32, 0, st>>>(a);
+}
+
+void launch_bone_state_to_tets(const BoneArgs& a, const int32_t* tkind, cudaStream_t st) {
+  k_bone_state_to_tets<<<grid_for(a.m, 256), 256, 0, st>>>(a, tkind);
 }
 
 void launch_joint_project(const JointArgs& j, int64_t n, double* x64, float* x32, cudaStream_t st) {

@@ -39,17 +39,22 @@ namespace emu {
 constexpr int kMaxFreeBones = 4;      // 3 scalar basis columns per free bone of the 16
 constexpr int kMaxJointPts = 16;      // joint points (a hinge has 2, a ball joint 1)
 constexpr int kBoneMeanBlocks = 32;   // blocks per free bone of the Abar reduction
-constexpr int kBoneStride = 96;       // per free bone: g 9, y 9, U 54, d 9 (FP64)
-constexpr int kBoneG = 0, kBoneY = 9, kBoneU = 18, kBoneD = 72;
+constexpr int kBoneStride = 96;       // per free bone: g 9, y 9, U 54, d 9, R 9, s 6 (FP64)
+constexpr int kBoneG = 0, kBoneY = 9, kBoneU = 18, kBoneD = 72, kBoneR = 81, kBoneS = 90;
 
 // tkind[i]: kind of tet i
 constexpr int32_t kTetDeformable = -1;  // an ordinary tet (its own Newton variable)
 constexpr int32_t kTetPinnedBone = -2;  // a tet of a bone whose vertices are all pinned
                                         // b >= 0: a tet of free bone b
 
+// Where a free bone's state (R_b, S_b) lives: on the FP64 path in the FP64
+// (R, s) of its tets (identical copies); on the mixed path in FP64 in the
+// bone's own iteration state (kBoneR, kBoneS), updated by launch_bone_update,
+// because an FP32 rotation of a bone, whose ACAP weight carries the
+// 1/|eps_bone| penalty, leaves a gradient error far above 1e-6.
 struct BoneArgs {
   int nfb;                             // free bones
-  int mixed;                           // state as (quaternion, E) when 1, (R, s) when 0
+  int mixed;                           // 1: state in bst (mixed path), 0: in R, s of the rep tets
   int64_t m, n;
   const int4* tet;
   const double* Dinv;                  // 9 m FP64 structure of arrays
@@ -81,9 +86,21 @@ void launch_bone_mean(const BoneArgs& a, const double* q, cudaStream_t st);
 void launch_bone_eval(const BoneArgs& a, double* gref_out, cudaStream_t st);
 // d_b = -(y_b + (I - N_b) Gbar_b z) per free bone; sum_b g_b . d_b into *gtd_out.
 void launch_bone_dir(const BoneArgs& a, const double* z, double* gtd_out, cudaStream_t st);
-// Copies of a free bone take its representative tet's state; tets of pinned
-// bones are set to R = I, S = I (both state forms as given by ``mixed``).
-void launch_bone_sync_state(const BoneArgs& a, const int32_t* tkind, cudaStream_t st);
+// Line-search terms of the free bones in FP64 for the mixed path: each
+// bone's V_b [Psi(F_b + s_j d_b) - Psi(F_b)] for the kLsTrials trial steps
+// s_j = sigma_start rho^j, and over the bones' tets the ACAP coefficients
+// sum c_i D_i . dD_i and sum c_i |dD_i|^2 (D_i = G_i q - F_b, dD_i = G_i dq
+// - d_b). Written as kBoneLsBlocks block partials of kLsNV values.
+constexpr int kBoneLsBlocks = 32;
+void launch_bone_ls(const BoneArgs& a, const float* dq32, double rho, double* partials_out, cudaStream_t st);
+// F' = R (S + sigma R^T d_b) per free bone, polar re-extraction in FP64, into
+// the bone state (mixed path; sigma from sc, nothing when it is 0).
+void launch_bone_update(const BoneArgs& a, cudaStream_t st);
+// Bone state <- the FP64 (R, s) of each free bone's representative tet.
+void launch_bone_state_from_tets(const BoneArgs& a, cudaStream_t st);
+// FP64 (R, s) of every free bone's tet <- the bone state (a.R, a.s written);
+// tets of pinned bones <- R = I, S = I.
+void launch_bone_state_to_tets(const BoneArgs& a, const int32_t* tkind, cudaStream_t st);
 
 struct JointArgs {
   int npts;                            // joint points (rows of J)

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "emu_bones.h"
+#include "emu_bones_host.h"
 #include "emu_internal.h"
 #include "emu_kernels.cuh"
 #include "emu_mixed.cuh"
@@ -103,6 +104,43 @@ struct emu_handle {
   double *val = nullptr, *ldinv = nullptr, *bfix = nullptr, *qfix = nullptr;
   uint8_t* is_fixed = nullptr;
   int32_t *slot_ptr = nullptr, *slot_idx = nullptr;
+  // ---- affine bones and joints (Sec. 3.3; see emu_bones.h) ----
+  bool has_bones = false;   // some tet belongs to a bone
+  int nb = 0;               // bones (pinned and free)
+  int nfb = 0;              // free bones: Newton variables of their own
+  int npts = 0;             // joint points (rows of J)
+  int njv = 0;              // vertices with a J entry
+  double eps_bone = -1e-3, eps_joint = -1e-4;
+  double Vbar = 0.0;        // mean rest volume
+  double kj = 0.0;          // final joint penalty Vbar^(1/3) / |eps_joint|
+  // host copies
+  std::vector<int32_t> tkind_h, btets_h, bptr_h, rep_h, bvert_h, bvptr_h;
+  std::vector<std::vector<int32_t>> bverts_h;   // vertices of every bone
+  std::vector<int> free_index_h;                // bone -> free-bone index, -1 if pinned
+  std::vector<double> Vb_h, wb_h, mub_h, lamb_h;
+  std::vector<double> w_h;                      // ACAP weights per tet (with the bone penalty)
+  std::vector<int32_t> jv_h;
+  std::vector<double> jw_h, JJinv_h, sgn_h;     // sgn: npts x kMaxFreeBones, (J zeta_b)_r
+  std::vector<uint8_t> jfree_h;
+  std::vector<int32_t> frowptr_h, fcol_h;       // final-solve Laplacian (CSR)
+  std::vector<double> fval_h, fldinv_h, zrhs_h;
+  std::vector<uint8_t> fin_fixed_h;
+  double Ainv_h[kMaxFreeBones * kMaxFreeBones] = {0};
+  // device arrays
+  int32_t *tkind = nullptr, *btets = nullptr, *bvert = nullptr;
+  double *gbar = nullptr, *cconst = nullptr, *bpart = nullptr, *cadd = nullptr, *bst = nullptr, *Qd = nullptr;
+  int32_t* jv = nullptr;
+  double *jw = nullptr, *Sinv = nullptr, *JJinv = nullptr, *Y64 = nullptr, *jlam = nullptr;
+  float* Y32 = nullptr;
+  uint8_t *jfree = nullptr, *jmask = nullptr;
+  int32_t *frowptr = nullptr, *fcol = nullptr;
+  double *fval = nullptr, *fldinv = nullptr, *zeta = nullptr, *fdt = nullptr;
+  uint8_t* fin_fixed = nullptr;
+  int64_t fnnz = 0;
+  BoneArgs bargs() const;
+  JointArgs jargs() const;
+  FinalArgs fargs() const;
+
   // launch shapes
   int grid_tet = 1, grid_syrk = 1, grid_pcg3 = 1, grid_pcg16 = 1;
   int grid_tet4 = 1;  // one wave of the 4-blocks-per-SM mixed gradient and line-search kernels
@@ -289,6 +327,8 @@ struct emu_handle {
     a.z = z;
     a.sc = sc;
     a.partials = part_grad;
+    a.tkind = tkind;
+    a.bone_st = bst;
     return a;
   }
 };
@@ -319,6 +359,8 @@ template <> inline TetArgs<double> emu_handle::args<double>() {
   a.z = z;
   a.sc = sc;
   a.partials = part_grad;
+  a.tkind = tkind;
+  a.bone_st = bst;
   return a;
 }
 template <> inline TetArgs<float> emu_handle::args<float>() {
@@ -347,6 +389,8 @@ template <> inline TetArgs<float> emu_handle::args<float>() {
   a.z = z;
   a.sc = sc;
   a.partials = part_grad;
+  a.tkind = tkind;
+  a.bone_st = bst;
   return a;
 }
 

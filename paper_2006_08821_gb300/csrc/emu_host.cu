@@ -110,10 +110,12 @@ int validate_mesh(const emu_mesh_desc* d) {
   for (int64_t i = 0; i < 3 * d->n_verts; ++i)
     if (!std::isfinite(d->rest_pos[i])) return fail(EMU_ERR_INVALID_ARG, "non-finite rest position");
   if (d->n_joints < 0) return fail(EMU_ERR_INVALID_ARG, "n_joints must be >= 0");
-  if (d->n_joints > 0) return fail(EMU_ERR_NOT_IMPLEMENTED, "joints (Sec. 3.3) are not supported by the GPU path yet");
+  if (d->n_joints > 0 && (!d->joint_type || !d->joint_bones || !d->joint_point || !d->joint_axis ||
+                          !d->joint_half_length))
+    return fail(EMU_ERR_INVALID_ARG, "missing joint array");
   if (d->bone_id)
     for (int64_t i = 0; i < d->n_tets; ++i)
-      if (d->bone_id[i] >= 0) return fail(EMU_ERR_NOT_IMPLEMENTED, "bones (Sec. 3.3) are not supported by the GPU path yet");
+      if (d->bone_id[i] < -1) return fail(EMU_ERR_INVALID_ARG, "bone_id must be -1 or a bone index");
   return EMU_OK;
 }
 
@@ -133,6 +135,8 @@ int validate_params(const emu_params* p) {
   if (p->mode_iters < 1 || p->mode_iters > 50) return fail(EMU_ERR_INVALID_ARG, "mode_iters must be 1..50");
   if (!(p->dq_tol > 0.0 && p->dq_tol < 1.0)) return fail(EMU_ERR_INVALID_ARG, "dq_tol must be in (0, 1)");
   if (p->q_refresh < 1) return fail(EMU_ERR_INVALID_ARG, "q_refresh must be >= 1");
+  if (!(p->eps_bone < 0.0) || !(p->eps_joint < 0.0) || !std::isfinite(p->eps_bone) || !std::isfinite(p->eps_joint))
+    return fail(EMU_ERR_INVALID_ARG, "eps_bone and eps_joint must be negative");
   return EMU_OK;
 }
 
@@ -185,6 +189,14 @@ constexpr double kStallBand = 10.0;
 constexpr int kEscalateIters = 50;
 constexpr int kStallIters = 200;
 
+// Coupling solves in FP64 CG: on the FP64 path, and on the mixed path when
+// the mesh has bones. A bone tet's ACAP weight carries the 1/|eps_bone|
+// penalty, which multiplies the Laplacian's condition number by about
+// 1000: beyond what an FP32 CG resolves (measured on the 40,152-tet arm:
+// mixed with FP32 dq solves took 2,765 Newton iterations over three
+// frames where the FP64 path took 608).
+bool cg64(const emu_handle* h) { return !h->mixed || h->has_bones; }
+
 int refresh_begin(emu_handle* h, double /*tol*/) {
   h->ph_begin();
   if (h->mixed)
@@ -198,18 +210,36 @@ int refresh_begin(emu_handle* h, double /*tol*/) {
   EMU_CK(cudaGetLastError());
   const int rgrid = (int)std::min<int64_t>(std::max<int64_t>(1, (h->n + 255) / 256), 2 * (int64_t)h->sms);
   h->ph_begin();
-  EMU_CK(launch_residual64(h->n, h->rowptr, h->col, h->val, h->b, h->q0, nullptr, nullptr, h->part_pcg, rgrid,
-                           h->small + 8, h->st));
-  h->ph_end(EMU_PHASE_PCG, 2);
+  if (h->npts > 0) {
+    // with joints the residual of the constrained problem is the projected one
+    double* rs = h->b + 9 * h->n;
+    EMU_CK(launch_residual64(h->n, h->rowptr, h->col, h->val, h->b, h->q0, nullptr, rs, h->part_pcg, rgrid,
+                             h->small + 8, h->st, h->jmask));
+    launch_joint_rproj(h->jargs(), rs, nullptr, h->small + 8, h->st);
+    h->ph_end(EMU_PHASE_PCG, 3);
+  } else {
+    EMU_CK(launch_residual64(h->n, h->rowptr, h->col, h->val, h->b, h->q0, nullptr, nullptr, h->part_pcg, rgrid,
+                             h->small + 8, h->st));
+    h->ph_end(EMU_PHASE_PCG, 2);
+  }
   return EMU_OK;
 }
 
 int refresh_residual(emu_handle* h) {
   const int rgrid = (int)std::min<int64_t>(std::max<int64_t>(1, (h->n + 255) / 256), 2 * (int64_t)h->sms);
+  const bool c64 = cg64(h);
+  float* r32 = c64 ? nullptr : h->r32;
   h->ph_begin();
-  EMU_CK(launch_residual64(h->n, h->rowptr, h->col, h->val, h->b, h->q, h->mixed ? h->r32 : nullptr,
-                           h->mixed ? nullptr : h->b + 3 * h->n, h->part_pcg, rgrid, h->small, h->st));
-  h->ph_end(EMU_PHASE_PCG, 2);
+  if (h->npts > 0) {
+    EMU_CK(launch_residual64(h->n, h->rowptr, h->col, h->val, h->b, h->q, r32, h->b + 3 * h->n, h->part_pcg, rgrid,
+                             h->small, h->st, h->jmask));
+    launch_joint_rproj(h->jargs(), h->b + 3 * h->n, r32, h->small, h->st);
+    h->ph_end(EMU_PHASE_PCG, 3);
+  } else {
+    EMU_CK(launch_residual64(h->n, h->rowptr, h->col, h->val, h->b, h->q, r32, c64 ? h->b + 3 * h->n : nullptr,
+                             h->part_pcg, rgrid, h->small, h->st));
+    h->ph_end(EMU_PHASE_PCG, 2);
+  }
   EMU_CK(cudaMemcpyAsync(h->o6_host, h->small, 14 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   return EMU_OK;
 }
@@ -231,15 +261,16 @@ double refresh_round_tol(const emu_handle* h, double tol) {
   double need = 0.5;
   for (int j = 0; j < 3; ++j)
     if (o[j] > 0.0) need = std::min(need, 0.2 * tol * std::sqrt(o[8 + j] / o[j]));
-  return std::max(need, h->mixed ? 1e-6 : 1e-12);
+  return std::max(need, cg64(h) ? 1e-12 : 1e-6);
 }
 
 int refresh_correction(emu_handle* h, double round_tol) {
-  if (h->mixed) {
+  if (!cg64(h)) {
     EMU_CK(cudaMemsetAsync(h->e32, 0, 12 * h->n, h->st));
     h->ph_begin();
     EMU_CK(run_pcg32(h, h->r32, h->e32, round_tol));
     EMU_CK(launch_axpy_f2d(3 * h->n, h->e32, h->q, h->st));
+    joints_project(h, h->q, nullptr);  // J q = 0 again (the joint rows of Sec. 3.3)
     h->ph_end(EMU_PHASE_PCG, 2);
     return EMU_OK;
   }
@@ -249,6 +280,7 @@ int refresh_correction(emu_handle* h, double round_tol) {
   h->ph_begin();
   EMU_CK(launch_pcg<double>(3, h->pcg64(r64, e64, round_tol), h->grid_pcg3, h->st));
   EMU_CK(launch_axpy_d2d(3 * h->n, e64, h->q, h->st));
+  joints_project(h, h->q, nullptr);
   h->ph_end(EMU_PHASE_PCG, 2);
   return EMU_OK;
 }
@@ -279,6 +311,7 @@ int solve_dq(emu_handle* h) {
     EMU_CK(cudaGetLastError());
     h->ph_begin();
     EMU_CK(launch_pcg<double>(3, h->pcg64(h->b, h->dq, tol), h->grid_pcg3, h->st));
+    joints_project(h, h->dq, nullptr);
     h->ph_end(EMU_PHASE_PCG, 1);
     return EMU_OK;
   }
@@ -287,7 +320,19 @@ int solve_dq(emu_handle* h) {
   h->ph_end(EMU_PHASE_ASSEMBLE, 1);
   EMU_CK(cudaGetLastError());
   h->ph_begin();
+  if (cg64(h)) {
+    // mixed path with bones: the FP32 right-hand side, the solve in FP64
+    // (dq in FP64 for the position update, an FP32 copy for the per-tet kernels)
+    EMU_CK(cudaMemsetAsync(h->b, 0, 24 * h->n, h->st));
+    EMU_CK(launch_axpy_f2d(3 * h->n, h->b32, h->b, h->st));
+    EMU_CK(launch_pcg<double>(3, h->pcg64(h->b, h->dq, tol), h->grid_pcg3, h->st));
+    joints_project(h, h->dq, nullptr);
+    launch_d2f(3 * h->n, h->dq, h->dq32, h->st);
+    h->ph_end(EMU_PHASE_PCG, 4);
+    return EMU_OK;
+  }
   EMU_CK(run_pcg32(h, h->b32, h->dq32, tol));
+  joints_project(h, nullptr, h->dq32);
   h->ph_end(EMU_PHASE_PCG, 1);
   return EMU_OK;
 }
@@ -307,7 +352,7 @@ int set_rest_state(emu_handle* h) {
     EMU_CK(cudaMemsetAsync(h->dq32, 0, 3 * h->n * 4, h->st));
   }
   EMU_CK(cudaStreamSynchronize(h->st));
-  return EMU_OK;
+  return bones_state_rest(h);
 }
 
 int read_scalars(emu_handle* h) {
@@ -325,7 +370,8 @@ int build_modes(emu_handle* h) {
   const int64_t n = h->n;
   std::vector<double> X(n * 16, 0.0);
   std::vector<uint8_t> fixed(n);
-  EMU_CK(cudaMemcpy(fixed.data(), h->is_fixed, n, cudaMemcpyDeviceToHost));
+  EMU_CK(cudaMemcpyAsync(fixed.data(), h->is_fixed, n, cudaMemcpyDeviceToHost, h->st));
+  EMU_CK(cudaStreamSynchronize(h->st));
   uint64_t seed = h->prm.seed ^ 0x5EEDF00Dull;
   for (int64_t v = 0; v < n; ++v)
     for (int j = 0; j < 16; ++j) {
@@ -336,25 +382,17 @@ int build_modes(emu_handle* h) {
   double* Yd = h->scratch16 + n * 16;
   EMU_CK(cudaMemcpyAsync(Xd, X.data(), X.size() * 8, cudaMemcpyHostToDevice, h->st));
   const int ggrid = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 511) / 512), 2 * h->sms);
-  for (int it = 0; it < h->prm.mode_iters; ++it) {
-    // Y = L^-1 X (pinned rows: right-hand side 0)
-    EMU_CK(cudaMemsetAsync(Yd, 0, n * 16 * 8, h->st));
-    PcgArgsT<double> a = h->pcg64(Xd, Yd, 1e-6);
-    a.max_iter = std::max(h->prm.pcg_max, 1000);
-    a.iters_out = nullptr;
-    a.fail_out = nullptr;
-    EMU_CK(launch_pcg<double>(16, a, h->grid_pcg16, h->st));
-    // orthonormalise: Y^T Y = L L^T, X = Y L^-T
-    launch_gram16(n, Yd, ggrid, h->part_pcg, h->st);
+  // X = Y T with Y^T Y = V diag(lambda) V^T, T = V diag(lambda^-1/2):
+  // orthonormal columns; directions with a negligible Gram eigenvalue (fewer
+  // free vertices than modes) are dropped as zero columns
+  auto orthonormalise = [&](const double* Ysrc, bool last) -> int {
+    launch_gram16(n, Ysrc, ggrid, h->part_pcg, h->st);
     launch_reduce_cols(h->part_pcg, ggrid, 256, h->small, h->st);
     std::vector<double> Gm(256);
     EMU_CK(cudaMemcpyAsync(Gm.data(), h->small, 256 * 8, cudaMemcpyDeviceToHost, h->st));
     EMU_CK(cudaStreamSynchronize(h->st));
     for (int i = 0; i < 16; ++i)
       for (int j = 0; j < 16; ++j) Gm[16 * i + j] = 0.5 * (Gm[16 * i + j] + Gm[16 * j + i]);
-    // X = Y T with T = V diag(lambda^-1/2): orthonormal columns; directions
-    // with a negligible Gram eigenvalue (fewer free vertices than modes)
-    // are dropped as zero columns.
     std::vector<double> Ev;
     host_jacobi_eig(Gm, Ev, 16);
     double lmax = 0.0;
@@ -368,20 +406,50 @@ int build_modes(emu_handle* h) {
       for (int i = 0; i < 16; ++i) T[16 * i + j] = Ev[16 * i + j] * sc_;
     }
     // drop unused modes (k_modes < 48) after the last iteration
-    if (it + 1 == h->prm.mode_iters)
+    if (last)
       for (int i = 0; i < 16; ++i)
         for (int j = h->kmodes; j < 16; ++j) T[16 * i + j] = 0.0;
     EMU_CK(cudaMemcpyAsync(h->small, T.data(), 256 * 8, cudaMemcpyHostToDevice, h->st));
-    EMU_CK(cudaMemcpyAsync(Xd, Yd, n * 16 * 8, cudaMemcpyDeviceToDevice, h->st));
+    if (Ysrc != Xd) EMU_CK(cudaMemcpyAsync(Xd, Ysrc, n * 16 * 8, cudaMemcpyDeviceToDevice, h->st));
     launch_xform16(n, h->small, Xd, h->st);
     EMU_CK(cudaGetLastError());
     EMU_CK(cudaStreamSynchronize(h->st));
+    return EMU_OK;
+  };
+  for (int it = 0; it < h->prm.mode_iters; ++it) {
+    // Y = L^-1 X (pinned rows: right-hand side 0)
+    EMU_CK(cudaMemsetAsync(Yd, 0, n * 16 * 8, h->st));
+    PcgArgsT<double> a = h->pcg64(Xd, Yd, 1e-6);
+    a.max_iter = std::max(h->prm.pcg_max, 1000);
+    a.iters_out = nullptr;
+    a.fail_out = nullptr;
+    EMU_CK(launch_pcg<double>(16, a, h->grid_pcg16, h->st));
+    // with joints, the basis lives in the null space of the joint rows (a
+    // Galerkin basis of the constrained coupling problem keeps the
+    // quasi-Newton matrix positive definite)
+    int rc = joints_project_basis(h, Yd);
+    if (rc) return rc;
+    rc = orthonormalise(Yd, it + 1 == h->prm.mode_iters && h->nfb == 0);
+    if (rc) return rc;
+  }
+  if (h->nfb > 0) {
+    // the last 3 columns per free bone become the constrained responses of q
+    // to the bone's F_b: without them the bone's block of the approximate
+    // Hessian misses how q follows F_b (bone tets weigh ~1000x)
+    int rc = bones_basis_responses(h, Xd);
+    if (rc) return rc;
+    rc = orthonormalise(Xd, true);
+    if (rc) return rc;
   }
   if (h->mixed)
     launch_gamma<float>(h->m, h->tet, h->Dinv, Xd, h->gam32, h->st);
   else
     launch_gamma<double>(h->m, h->tet, h->Dinv, Xd, h->gam64, h->st);
   EMU_CK(cudaGetLastError());
+  {
+    int rc = bones_after_gamma(h);  // the bones' mean mode gradients and constant capacitance terms
+    if (rc) return rc;
+  }
   // coarse space of the ACAP preconditioner: Phi and (Phi^T L Phi)^+
   EMU_CK(cudaMemcpyAsync(h->phi64, Xd, n * 16 * 8, cudaMemcpyDeviceToDevice, h->st));
   if (h->mixed) launch_d2f(n * 16, h->phi64, h->phi32, h->st);
@@ -411,6 +479,21 @@ int build_modes(emu_handle* h) {
   h->coarse_ready = emax > 0.0;
   h->aphi_ready = h->mixed && h->rpt32 > 0;
   return EMU_OK;
+}
+
+// Zeroes the per-tet iteration arrays of the kernels in use (bone tets keep
+// zero gradient, y and chart factor throughout).
+bool zero_tet_work(emu_handle* h) {
+  const int64_t m = h->m;
+  bool ok = cudaMemsetAsync(h->g, 0, 72 * m, h->st) == cudaSuccess;
+  if (h->y64) ok = ok && cudaMemsetAsync(h->y64, 0, 72 * m, h->st) == cudaSuccess &&
+                   cudaMemsetAsync(h->Uw64, 0, 432 * m, h->st) == cudaSuccess &&
+                   cudaMemsetAsync(h->d64, 0, 72 * m, h->st) == cudaSuccess;
+  if (h->y32) ok = ok && cudaMemsetAsync(h->y32, 0, 36 * m, h->st) == cudaSuccess &&
+                   cudaMemsetAsync(h->Uw32, 0, 216 * m, h->st) == cudaSuccess &&
+                   cudaMemsetAsync(h->d32, 0, 36 * m, h->st) == cudaSuccess &&
+                   cudaMemsetAsync(h->g32, 0, 36 * m, h->st) == cudaSuccess;
+  return ok && cudaStreamSynchronize(h->st) == cudaSuccess;
 }
 
 // Every device buffer of a handle (n, m, mixed and sms set). In dry mode
@@ -446,7 +529,7 @@ bool alloc_device(emu_handle* h, int64_t nnz) {
   h->grid_pcg16 = pcg_max_grid(16, n);
   const int pcg_part = std::max(h->grid_pcg3 * (4 * 3 + 3 * kModes), h->grid_pcg16 * 64);  // per-block partials
   const int64_t gpart = std::max<int64_t>(h->grid_tet * (int64_t)kLsNV, 256 * (int64_t)(2 * h->sms + 1));
-  ok = ok && h->get(h->part_grad, gpart) && h->get(h->part_dir, h->grid_tet) && h->get(h->part_ls, h->grid_tet * kLsNV) &&
+  ok = ok && h->get(h->part_grad, gpart) && h->get(h->part_dir, h->grid_tet + 1) && h->get(h->part_ls, (h->grid_tet + kBoneLsBlocks) * kLsNV) &&
        h->get(h->part_pcg, std::max<int64_t>(pcg_part, 256 * (int64_t)(2 * h->sms + 1))) &&
        h->get(h->cpart, std::max<int64_t>(h->grid_syrk, kTcBlocksPerSM * (int64_t)h->sms) * (kCapEntries + kK)) && h->get(h->z, kK) && h->get(h->cfull, kCapEntries + kK) && h->get(h->small, 256) &&
        h->get(h->sc, 1) && h->get(h->bar, 1);
@@ -454,12 +537,14 @@ bool alloc_device(emu_handle* h, int64_t nnz) {
   ok = ok && h->get(h->rowptr, n + 1) && h->get(h->col, nnz) && h->get(h->val, nnz) && h->get(h->ldinv, n) &&
        h->get(h->bfix, 3 * n) && h->get(h->qfix, 3 * n) && h->get(h->is_fixed, n) && h->get(h->slot_ptr, n + 1) &&
        h->get(h->slot_idx, 4 * m);
+  ok = ok && bones_alloc(h);
   return ok;
 }
 
 int compute_gref(emu_handle* h) {
   TetArgs<double> a = h->args<double>();
   launch_gref(a, h->q0, h->grid_tet, h->part_grad, h->small, h->st);
+  bones_gref(h, h->small);  // the free bones' |g(I)|^2 (their tets are skipped above)
   double g2 = 0.0;
   EMU_CK(cudaMemcpyAsync(&g2, h->small, 8, cudaMemcpyDeviceToHost, h->st));
   EMU_CK(cudaStreamSynchronize(h->st));
@@ -476,6 +561,7 @@ void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 bool acap_view(const emu_handle* h, AcapView* v) {
   if (!h || !v) return false;
   v->device = h->device;
+  v->npts = h->npts;
   v->n = h->n;
   v->m = h->m;
   v->tet = h->tet;
@@ -524,6 +610,8 @@ void emu_default_params(emu_params* p) {
   p->dq_tol = 5e-2;
   p->q_refresh = 32;
   p->seed = 12345;
+  p->eps_bone = -1e-3;
+  p->eps_joint = -1e-4;
 }
 
 const char* emu_status_string(int status) {
@@ -580,14 +668,6 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
   const int64_t n = desc->n_verts, m = desc->n_tets;
   h->n = n;
   h->m = m;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    delete h;
-    return fail(EMU_ERR_CUDA, "no CUDA device");
-  }
-  h->device = dev;
-  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
-
   // ---- geometry (Eq. 2), volumes, orientation ----
   const double* Q = desc->rest_pos;
   std::vector<int32_t> tet(4 * m);
@@ -640,22 +720,43 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     for (int64_t i = 0; i < m; ++i) V[i] = (double)(float)V[i];
   }
 
+  // ---- pins ----
+  std::vector<uint8_t> is_fixed(n, 0);
+  std::vector<double> qfix(Q, Q + 3 * n);
+  for (int64_t k = 0; k < desc->n_fixed; ++k) {
+    const int32_t v = desc->fixed_verts[k];
+    is_fixed[v] = 1;
+    if (desc->fixed_pos)
+      for (int r = 0; r < 3; ++r) qfix[3 * v + r] = desc->fixed_pos[3 * k + r];
+  }
+
+  // ---- bones and joints (Sec. 3.3) ----
+  rc = bones_prepare(h, desc, tet, V, is_fixed);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+
   // ---- materials, weights (Eq. 3 with the Sec. 3.3 weights option) ----
   std::vector<double> mu(m), lam(m), wv(m), cv(m), uv(3 * m, 0.0);
-  double mu_ref = 1e300;
+  double mu_ref = 1e300, mu_ref_all = 1e300;
   for (int64_t i = 0; i < m; ++i) {
     const int k = desc->material_id[i];
     const double E = desc->youngs[k], nu = desc->poisson[k];
     mu[i] = E / (2.0 * (1.0 + nu));
     lam[i] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-    mu_ref = std::min(mu_ref, mu[i]);
+    mu_ref_all = std::min(mu_ref_all, mu[i]);
+    // mu_ref: the softest material that is not bone
+    if (!h->has_bones || h->tkind_h[i] == kTetDeformable) mu_ref = std::min(mu_ref, mu[i]);
   }
+  if (mu_ref > 1e299) mu_ref = mu_ref_all;
   h->mu_ref = mu_ref;
   h->alpha = prm.alpha_rel * mu_ref;
   h->kappa = prm.fiber_scale * mu_ref;
   double fl = 0.0;
+  for (int64_t i = 0; i < m; ++i) wv[i] = prm.weight_mode == 1 ? V[i] * std::max(1.0, mu[i] / mu_ref) : V[i];
+  bones_weights(h, V, wv);  // bone tets: V_i + Vbar / |eps_bone|
   for (int64_t i = 0; i < m; ++i) {
-    wv[i] = prm.weight_mode == 1 ? V[i] * std::max(1.0, mu[i] / mu_ref) : V[i];
     if (h->mixed) wv[i] = (double)(float)wv[i];
     cv[i] = h->alpha * wv[i];
     fl += (V[i] * mu[i]) * (V[i] * mu[i]);
@@ -673,17 +774,8 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
   }
   h->floor = 1e-12 * std::sqrt(fl);
   h->V_h = V;
+  bones_weight_sums(h, wv);
   h->q_tol = std::max(1e-13, std::min(prm.pcg_tol, 1e-2 * prm.tol_rel_residual));
-
-  // ---- pins ----
-  std::vector<uint8_t> is_fixed(n, 0);
-  std::vector<double> qfix(Q, Q + 3 * n);
-  for (int64_t k = 0; k < desc->n_fixed; ++k) {
-    const int32_t v = desc->fixed_verts[k];
-    is_fixed[v] = 1;
-    if (desc->fixed_pos)
-      for (int r = 0; r < 3; ++r) qfix[3 * v + r] = desc->fixed_pos[3 * k + r];
-  }
 
   // ---- scalar ACAP Laplacian L_ab = sum_i w_i gradN_a . gradN_b (Eq. 4) ----
   std::vector<std::pair<int64_t, double>> trip;
@@ -741,7 +833,21 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     for (int64_t k = 0; k < 4 * m; ++k) slot_idx[fillp[tet[k]]++] = (int32_t)k;
   }
 
-  // ---- device allocation ----
+  // final-solve operator of the bones (Sec. 3.3)
+  rc = bones_final_host(h, tet, Dinv, wv, is_fixed);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+
+  // ---- device allocation (every host-side check has passed) ----
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    delete h;
+    return fail(EMU_ERR_CUDA, "no CUDA device");
+  }
+  h->device = dev;
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t nnz = (int64_t)colv.size();
   bool ok = alloc_device(h, nnz);
   if (!ok) {
@@ -814,16 +920,28 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     delete h;
     return fail(EMU_ERR_CUDA, "upload failed");
   }
+  // tets of bones are never written by the gradient kernels: their
+  // per-iteration g, y, U stay zero (the capacitance and B y skip them)
+  if (h->has_bones) {
+    ok = zero_tet_work(h) && bones_upload(h, Q) == EMU_OK;
+    if (!ok) {
+      h->release();
+      delete h;
+      return fail(EMU_ERR_CUDA, "bone set-up upload failed");
+    }
+  }
 
   // ---- rest state: R = I, S = I, q = q*(I) ----
   rc = set_rest_state(h);
   // the normaliser of the exact solve is the residual at q0: here q0 = Q
   if (!rc && cudaMemcpyAsync(h->q0, h->q, 24 * n, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess)
     rc = fail(EMU_ERR_CUDA, "copy q0");
+  if (!rc) rc = joints_setup_device(h);  // joint corrections for the coupling solves
   if (!rc) rc = refresh_q(h, h->q_tol);
   if (!rc && cudaMemcpyAsync(h->q0, h->q, 24 * n, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess)
     rc = fail(EMU_ERR_CUDA, "copy q0");
   if (!rc) rc = build_modes(h);
+  if (!rc) rc = final_setup_device(h);
   if (!rc) rc = read_scalars(h);
   if (!rc && h->sc_host->barrier_timeout) rc = fail(EMU_ERR_TIMEOUT, "grid barrier timed out during setup");
   if (rc) {
@@ -841,6 +959,8 @@ int emu_set_activation(emu_handle* h, const double* a, int64_t count) {
   std::vector<double> ka(h->m);
   for (int64_t i = 0; i < h->m; ++i) {
     if (!(a[i] >= 0.0) || !std::isfinite(a[i])) return fail(EMU_ERR_INVALID_ARG, "activation must be finite and >= 0");
+    if (h->has_bones && a[i] != 0.0 && h->tkind_h[i] != kTetDeformable)
+      return fail(EMU_ERR_INVALID_ARG, "activation must be 0 on bone tets");
     ka[i] = h->kappa * a[i];
   }
   EMU_CK(cudaMemcpyAsync(h->ka, ka.data(), 8 * h->m, cudaMemcpyHostToDevice, h->st));
@@ -921,6 +1041,11 @@ int enqueue_grad(emu_handle* h) {
     launch_reduce_grad(h->part_grad, h->grid_tet, h->sc, nullptr, nullptr, h->st);
     h->ph_end(EMU_PHASE_SMALL, 1);
   }
+  if (h->nfb > 0) {  // the free bones' virtual elements (Sec. 3.3)
+    h->ph_begin();
+    bones_after_grad(h);
+    h->ph_end(EMU_PHASE_SMALL, 0);
+  }
   EMU_CK(cudaGetLastError());
   EMU_CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st));
   return EMU_OK;
@@ -941,7 +1066,11 @@ int enqueue_step(emu_handle* h) {
   }
   h->ph_end(EMU_PHASE_SYRK, 1);
   h->ph_begin();
-  launch_cap_solve(h->cpart, syrk_blocks, h->cfull, h->z, h->sc, h->mixed, h->st);
+  // the 48 x 48 factor in FP32 on the mixed path, in FP64 with bones (their
+  // 1/|eps_bone|-weighted terms widen the capacitance's spectrum)
+  launch_cap_solve(h->cpart, syrk_blocks, h->cfull, h->z, h->sc, h->mixed && !h->has_bones, h->st,
+                   bones_cap_addend(h));
+  bones_before_dir(h);
   h->ph_end(EMU_PHASE_SMALL, 2);
   h->ph_begin();
   if (h->mixed) {
@@ -964,10 +1093,14 @@ int enqueue_step(emu_handle* h) {
     al.partials = h->part_ls;
     LsSelect sel;  // the line-search kernel's last block selects the step
     sel.dir_partials = h->part_dir;
-    sel.nblk_dir = h->grid_tet;
+    sel.nblk_dir = dir_partial_count(h);
     sel.sigma0 = h->sigma0_now;
     sel.rho = h->prm.ls_rho;
     sel.c_armijo = h->prm.ls_c;
+    if (h->nfb > 0) {  // the free bones' terms in FP64, after the kernel's own partials
+      launch_bone_ls(h->bargs(), h->dq32, h->prm.ls_rho, h->part_ls + (size_t)h->grid_tet4 * kLsNV, h->st);
+      sel.nblk_extra = kBoneLsBlocks;
+    }
     launch_ls_mixed(al, h->grid_tet4, sel, h->st);
     h->ph_end(EMU_PHASE_LS, 1);
   } else {
@@ -976,14 +1109,18 @@ int enqueue_step(emu_handle* h) {
     launch_ls<double>(al, h->grid_tet, h->prm.ls_rho, h->st);
     h->ph_end(EMU_PHASE_LS, 1);
     h->ph_begin();
-    launch_ls_select(h->part_dir, h->grid_tet, h->part_ls, h->grid_tet, h->sc, h->sigma0_now, h->prm.ls_rho,
-                     h->prm.ls_c, h->st);
+    launch_ls_select(h->part_dir, dir_partial_count(h), h->part_ls, h->grid_tet, h->sc, h->sigma0_now,
+                     h->prm.ls_rho, h->prm.ls_c, h->st);
     h->ph_end(EMU_PHASE_SMALL, 1);
   }
   h->ph_begin();
   if (h->mixed) {
     launch_update_mixed(am, h->grid_tet, h->st);
-    launch_update_verts_f(h->n, h->sc, h->dq32, h->q, h->st);
+    bones_update_mixed(h);
+    if (cg64(h))
+      launch_update_verts(h->n, h->sc, h->dq, h->q, h->st);
+    else
+      launch_update_verts_f(h->n, h->sc, h->dq32, h->q, h->st);
   } else {
     launch_update_tets<double>(a64, h->grid_tet, h->st);
     launch_update_verts(h->n, h->sc, h->dq, h->q, h->st);
@@ -1039,6 +1176,21 @@ void drop_iteration_graph(emu_handle* h) {
   h->iter_exec_dq = -1.0;
 }
 
+// dq tolerance a solve starts with: params.dq_tol, or the tighter one a
+// stalled earlier solve settled on (with_base). With free bones (Sec. 3.3)
+// at most kBoneDqTol: a bone tet's ACAP weight carries the 1/|eps_bone|
+// penalty, and a loosely solved dq misses how the soft tissue follows the
+// bone, so the line search rejects steps (measured on the arm assemblies:
+// 576 tets FP64, 452 Newton iterations and a line-search failure near
+// 1.6e-10 at 5e-2 against 74 iterations to 1e-10 at 1e-6; 40,152 tets FP64,
+// 2,856 iterations over three frames at 5e-2 against 608 at 1e-4).
+constexpr double kBoneDqTol = 1e-4;
+double start_dq_tol(const emu_handle* h, bool with_base = true) {
+  double t = (with_base && h->dq_tol_base > 0.0) ? h->dq_tol_base : h->prm.dq_tol;
+  if (h->nfb > 0) t = std::min(t, kBoneDqTol);
+  return t;
+}
+
 // Precision escalation of a mixed handle whose residual has stalled at the
 // rounding floor of its FP32 per-tet arithmetic: the state (quaternion, E)
 // is converted to (R, s) and the FP64 kernels take over for the rest of the
@@ -1050,9 +1202,11 @@ bool escalate(emu_handle* h) {
     const int64_t m = h->m;
     if (!(h->get(h->gam64, 48 * m) && h->get(h->y64, 9 * m) && h->get(h->d64, 9 * m) && h->get(h->Uw64, 54 * m)))
       return false;
+    if (h->has_bones && !zero_tet_work(h)) return false;
     launch_gamma<double>(m, h->tet, h->Dinv, h->phi64, h->gam64, h->st);
   }
   launch_mixed_to_Rs(h->m, h->quat, h->E32, h->R, h->s, h->st);
+  bones_state_to_element_arrays(h);  // the FP64 kernels keep a bone's state in its tets
   if (cudaMemsetAsync(h->dq, 0, 24 * h->n, h->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return false;
   drop_iteration_graph(h);
   h->mixed = false;
@@ -1063,6 +1217,7 @@ bool escalate(emu_handle* h) {
 // Back to the mixed kernels at the end of an escalated solve.
 void deescalate(emu_handle* h) {
   if (!h->escalated) return;
+  bones_state_from_rep(h);
   launch_Rs_to_mixed(h->m, h->R, h->s, h->quat, h->E32, h->st);
   cudaMemsetAsync(h->dq32, 0, 12 * h->n, h->st);
   drop_iteration_graph(h);
@@ -1104,7 +1259,7 @@ int task_step(SolveTask* t) {
           return abort(fail(EMU_ERR_CUDA, "cudaMemcpyAsync failed"));
         t->gnorm_ref = h->gref > h->floor ? h->gref : 0.0;
         t->since = h->prm.q_refresh;  // iterations since q was last solved exactly
-        h->dq_tol_now = h->dq_tol_base > 0.0 ? h->dq_tol_base : h->prm.dq_tol;
+        h->dq_tol_now = start_dq_tol(h);
         t->phase = SolveTask::TOP;
         break;
       }
@@ -1175,13 +1330,13 @@ int task_step(SolveTask* t) {
         // into later solves on the handle.
         if (t->res > tol && t->best_res <= kStallBand * tol) {
           if (t->it - t->best_it >= kEscalateIters) {
-            const double dq_tight = std::max(h->q_tol, 1e-2 * h->prm.dq_tol);
+            const double dq_tight = std::max(h->q_tol, 1e-2 * start_dq_tol(h, false));
             bool restart = false;
             if (h->sigma0_now > 1.0) {
               h->sigma0_now = 1.0;
               restart = true;
             } else if (h->mixed && escalate(h)) {
-              h->dq_tol_now = h->dq_tol_base > 0.0 ? h->dq_tol_base : h->prm.dq_tol;
+              h->dq_tol_now = start_dq_tol(h);
               restart = true;
             } else if (h->dq_tol_now > dq_tight) {
               // later solves on this handle (the next frames) start tight
@@ -1260,6 +1415,11 @@ int task_step(SolveTask* t) {
       case SolveTask::FINISH: {
         deescalate(h);
         if (cudaStreamSynchronize(h->st) != cudaSuccess) return abort(fail(EMU_ERR_CUDA, "cudaStreamSynchronize failed"));
+        // with free bones, the final coupling solve of Sec. 3.3 gives the positions
+        if (h->nfb > 0 && (t->status == EMU_OK || t->status == EMU_ERR_NOT_CONVERGED)) {
+          const int frc = bones_final_solve(h);
+          if (frc) return abort(frc);
+        }
         h->prof_flush();
         auto t1 = std::chrono::steady_clock::now();
         if (t->stats) {
@@ -1312,6 +1472,8 @@ int emu_required_bytes(const emu_mesh_desc* desc, const emu_params* params, size
   h.n = desc->n_verts;
   h.m = desc->n_tets;
   h.mixed = prm.precision == EMU_PRECISION_MIXED;
+  if (desc->bone_id)
+    for (int64_t i = 0; i < h.m && !h.has_bones; ++i) h.has_bones = desc->bone_id[i] >= 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return fail(EMU_ERR_CUDA, "no CUDA device");
   if (cudaDeviceGetAttribute(&h.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -1377,6 +1539,7 @@ int emu_get_element_state(emu_handle* h, double* R, double* s, double* F) {
   int rc;
   if (h->mixed) {
     launch_mixed_to_Rs(m, h->quat, h->E32, h->R, h->s, h->st);
+    bones_state_to_element_arrays(h);  // the bones' FP64 states
     EMU_CK(cudaGetLastError());
   }
   if (R && (rc = soa_to_aos(h->R, 9, R))) return rc;
@@ -1405,14 +1568,19 @@ int emu_set_element_state(emu_handle* h, const double* R, const double* s, const
     EMU_CK(cudaMemcpyAsync(h->s, tmp.data(), 48 * m, cudaMemcpyHostToDevice, h->st));
     EMU_CK(cudaStreamSynchronize(h->st));
   }
+  if (h->mixed && (R || s) && (!R || !s)) {
+    // keep the untouched part: bring the current state to (R, s) first
+    std::vector<double> Rc(9 * m), sc_(6 * m);
+    int rc = emu_get_element_state(h, R ? nullptr : Rc.data(), s ? nullptr : sc_.data(), nullptr);
+    if (rc) return rc;
+    return emu_set_element_state(h, R ? R : Rc.data(), s ? s : sc_.data(), q);
+  }
+  if (h->has_bones && (R || s)) {
+    // a free bone's tets share one state: every copy takes its first tet's
+    bones_state_from_element_arrays(h);
+    EMU_CK(cudaGetLastError());
+  }
   if (h->mixed && (R || s)) {
-    if (!R || !s) {
-      // keep the untouched part: bring the current state to (R, s) first
-      std::vector<double> Rc(9 * m), sc_(6 * m);
-      int rc = emu_get_element_state(h, R ? nullptr : Rc.data(), s ? nullptr : sc_.data(), nullptr);
-      if (rc) return rc;
-      return emu_set_element_state(h, R ? R : Rc.data(), s ? s : sc_.data(), q);
-    }
     launch_Rs_to_mixed(m, h->R, h->s, h->quat, h->E32, h->st);
     EMU_CK(cudaGetLastError());
     EMU_CK(cudaStreamSynchronize(h->st));

@@ -59,6 +59,7 @@ struct Laplacian {
 // outside the handle's translation unit.
 struct AcapView {
   int device;            // CUDA device the handle was created on
+  int npts;              // joint rows (Sec. 3.3) of the handle's coupling problem
   int64_t n, m;
   const int4* tet;
   const double* Dinv;    // 9m structure of arrays

@@ -309,7 +309,8 @@ template <typename TW> void launch_syrk(const TetArgs<TW>& a, int grid, double* 
 
 // One warp per entry of C and B y sums that entry's per-block partials
 // (entry-major, coalesced) with a fixed shuffle tree.
-__global__ void __launch_bounds__(256) k_reduce_cpart(const double* __restrict__ cpart, int nblk, double* __restrict__ cfull) {
+__global__ void __launch_bounds__(256) k_reduce_cpart(const double* __restrict__ cpart, int nblk, double* __restrict__ cfull,
+                                                      const double* __restrict__ cadd) {
   const int e = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (e >= kCapEntries + kK) return;
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(256) k_reduce_cpart(const double* __restrict__
   for (int b = lane; b < nblk; b += 32) x += cpart[(size_t)e * nblk + b];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  if (lane == 0) cfull[e] = x;
+  if (lane == 0) cfull[e] = cadd ? x + cadd[e] : x;
 }
 
 // Factor C = L L^T (C symmetrised) and solve z = C^-1 (B y), in T arithmetic
@@ -413,9 +414,9 @@ __global__ void k_ls_reset(DevScalars* sc, double sigma0) {
 void launch_ls_reset(DevScalars* sc, double sigma0, cudaStream_t st) { k_ls_reset<<<1, 1, 0, st>>>(sc, sigma0); }
 
 void launch_cap_solve(const double* cpart, int nblk, const double* cfull_scratch, double* z, DevScalars* sc,
-                      bool fp32_factor, cudaStream_t st) {
+                      bool fp32_factor, cudaStream_t st, const double* cadd) {
   double* cfull = const_cast<double*>(cfull_scratch);
-  k_reduce_cpart<<<(kCapEntries + kK + 7) / 8, 256, 0, st>>>(cpart, nblk, cfull);
+  k_reduce_cpart<<<(kCapEntries + kK + 7) / 8, 256, 0, st>>>(cpart, nblk, cfull, cadd);
   if (fp32_factor)
     k_cap_solve<float><<<1, 256, 0, st>>>(cfull, z, sc);
   else
@@ -530,13 +531,15 @@ __global__ void __launch_bounds__(128) k_ls(TetArgs<TW> a, double rho) {
     matTmul3(R, d, Rtd);
     matmul3(Sinv, Rtd, M);
     const double trM = M[0] + M[4] + M[8];
-    const double trM2 = M[0] * M[0] + M[4] * M[4] + M[8] * M[8] + 2.0 * (M[1] * M[3] + M[2] * M[6] + M[5] * M[7]);
-    const double e2 = 0.5 * (trM * trM - trM2);
+    const double e2 = inv2(M);
     const double detM = det3(M);
-    double Fd = 0.0, dd = 0.0;
+    // <F - F^-T, d> = <S - S^-1, R^T d>: the O(|d|) parts of mu <F, d> and
+    // mu tr(F^-1 d) cancel before they are formed (a stiff, barely strained
+    // element, a bone, would otherwise keep only their rounding)
+    double FFd = 0.0, dd = 0.0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      Fd += F[k] * d[k];
+      FFd += (S[k] - Sinv[k]) * Rtd[k];
       dd += d[k] * d[k];
     }
     double Fu[3], du[3];
@@ -553,9 +556,10 @@ __global__ void __launch_bounds__(128) k_ls(TetArgs<TW> a, double rho) {
       const double x = sig * trM + sig * sig * e2 + sig * sig * sig * detM;
       double dpsi;
       if (x > -1.0) {
+        // mu [s <F, d> + s^2 |d|^2 / 2 - log1p(x)] with log1p(x) = x - (x - log1p x)
         const double dl = log1p(x);
-        dpsi = md.mu * (sig * Fd + 0.5 * sig * sig * dd) - md.mu * dl + 0.5 * md.lam * dl * (2.0 * lnJ + dl) +
-               md.ka * (2.0 * sig * Fudu + sig * sig * dudu);
+        const double nh = sig * FFd + 0.5 * sig * sig * dd - sig * sig * e2 - sig * sig * sig * detM + x_minus_log1p(x);
+        dpsi = md.mu * nh + 0.5 * md.lam * dl * (2.0 * lnJ + dl) + md.ka * (2.0 * sig * Fudu + sig * sig * dudu);
         dpsi *= md.V;
       } else {
         dpsi = 1e300;

@@ -58,8 +58,10 @@ void launch_reduce_grad(const double* partials, int nblk, DevScalars* sc, double
                         cudaStream_t st);
 // cpart: entry-major partials (kCapEntries + kK entries x nblk blocks);
 // cfull_scratch receives their sums. fp32_factor: factor and solve in FP32.
+// cadd (null, or kCapEntries + kK values) is added to the summed entries
+// (the bones' terms of Sec. 3.3).
 void launch_cap_solve(const double* cpart, int nblk, const double* cfull_scratch, double* z, DevScalars* sc,
-                      bool fp32_factor, cudaStream_t st);
+                      bool fp32_factor, cudaStream_t st, const double* cadd = nullptr);
 // Restart the line search: ls_fail = 0, sigma_start = sigma0.
 void launch_ls_reset(DevScalars* sc, double sigma0, cudaStream_t st);
 void launch_ls_select(const double* dir_partials, int nblk_dir, const double* ls_partials, int nblk_ls,

@@ -494,6 +494,9 @@ __global__ void __launch_bounds__(128) k_ls_m(MixArgs a, LsSelect sel) {
 #pragma unroll
   for (int k = 0; k < kLsNV; ++k) acc[k] = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    // free bones' tets: their terms come from the FP64 bone kernel (a stiff
+    // bone's energy change is beyond FP32); pinned bones' tets contribute 0
+    if (a.tkind && a.tkind[i] != kTetDeformable) continue;
     const int4 t = a.tet[i];
     float D[9], R[9], e6[6], dA[9], d[9];
     load9f(a.Dinv, m, i, D);
@@ -560,7 +563,8 @@ __global__ void __launch_bounds__(128) k_ls_m(MixArgs a, LsSelect sel) {
   block_reduce_write<kLsNV>(acc, a.partials + (size_t)blockIdx.x * kLsNV);
   // the last block to finish sums every block's partials and selects the step
   if (last_block(&a.sc->ticket[kTicketLs])) {
-    ls_select_block(sel.dir_partials, sel.nblk_dir, a.partials, gridDim.x, a.sc, sel.sigma0, sel.rho, sel.c_armijo);
+    ls_select_block(sel.dir_partials, sel.nblk_dir, a.partials, gridDim.x + sel.nblk_extra, a.sc, sel.sigma0, sel.rho,
+                    sel.c_armijo);
     if (threadIdx.x == 0) a.sc->ticket[kTicketLs] = 0u;
   }
 }
@@ -578,6 +582,7 @@ __global__ void __launch_bounds__(128) k_update_m(MixArgs a) {
   const float sig = (float)sigd;
   const int64_t m = a.m;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (a.tkind && a.tkind[i] != kTetDeformable) continue;  // bones: FP64 state of their own
     float R[9], e6[6], d[9], Rtd[9], Y[9];
     load_state(a, i, R, e6);
     load9f(a.d, m, i, d);
@@ -619,21 +624,34 @@ void launch_update_verts_f(int64_t n, const DevScalars* sc, const float* dq, dou
 __global__ void __launch_bounds__(256) k_rhs_state_m(MixArgs a) {
   const int64_t m = a.m;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const float4 qq = a.quat[i];
-    double qx = qq.x, qy = qq.y, qz = qq.z, qw = qq.w;
-    const double nn = 1.0 / sqrt(qx * qx + qy * qy + qz * qz + qw * qw);
-    qx *= nn;
-    qy *= nn;
-    qz *= nn;
-    qw *= nn;
+    const int32_t kind = a.tkind ? a.tkind[i] : kTetDeformable;
     double R[9], e6[6], S[9], F[9];
-    quat_to_R(qx, qy, qz, qw, R);
+    if (kind >= 0) {  // a free bone's tet: the bone's FP64 state
+      const double* o = a.bone_st + (size_t)kind * kBoneStride;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) e6[k] = (double)a.E[k * m + i];
-    sym_from_s(e6, S);
-    S[0] += 1.0;
-    S[4] += 1.0;
-    S[8] += 1.0;
+      for (int k = 0; k < 9; ++k) R[k] = o[kBoneR + k];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) e6[k] = o[kBoneS + k];
+      sym_from_s(e6, S);
+    } else if (kind == kTetPinnedBone) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) R[k] = S[k] = (k % 4 == 0) ? 1.0 : 0.0;
+    } else {
+      const float4 qq = a.quat[i];
+      double qx = qq.x, qy = qq.y, qz = qq.z, qw = qq.w;
+      const double nn = 1.0 / sqrt(qx * qx + qy * qy + qz * qz + qw * qw);
+      qx *= nn;
+      qy *= nn;
+      qz *= nn;
+      qw *= nn;
+      quat_to_R(qx, qy, qz, qw, R);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) e6[k] = (double)a.E[k * m + i];
+      sym_from_s(e6, S);
+      S[0] += 1.0;
+      S[4] += 1.0;
+      S[8] += 1.0;
+    }
     matmul3(R, S, F);
     double D[9];
 #pragma unroll

@@ -547,6 +547,16 @@ EMU_HD float x_minus_log1p(float x) {
   return x - log1pf(x);
 }
 
+// FP64: the series up to x^20 for |x| < 0.05 (next term below 0.05^19 relative).
+EMU_HD double x_minus_log1p(double x) {
+  if (fabs(x) < 0.05) {
+    double s = 1.0 / 20;
+    for (int k = 19; k >= 2; --k) s = 1.0 / k - x * s;
+    return x * x * s;
+  }
+  return x - log1p(x);
+}
+
 // Stretch quantities from E = S - I (FP32, difference-free):
 //   S, S^-1, ln J = log1p(tr E + e2(E) + det E), and S - S^-1 = (2E + E^2) S^-1.
 struct StretchE {

@@ -55,6 +55,9 @@ struct LsSelect {
   const double* dir_partials;
   int nblk_dir;
   double sigma0, rho, c_armijo;
+  // blocks of line-search partials written after the kernel's own (the free
+  // bones' FP64 terms, Sec. 3.3), summed by the selection too
+  int nblk_extra = 0;
 };
 // Trial energies of one pass and, in its last block, the selected step
 // (k_ls_select's work); the gradient kernel likewise leaves ||g||^2 in sc.

@@ -111,6 +111,8 @@ extern "C" int emu_acap_solve_noalloc(emu_handle* h, const double* F_device, dou
   if (e != cudaSuccess) return noalloc_fail(EMU_ERR_CUDA, "cudaGetDevice", e);
   if (cur != v.device)
     return noalloc_fail(EMU_ERR_INVALID_ARG, "the current device is not the one the handle was created on");
+  if (v.npts > 0)
+    return noalloc_fail(EMU_ERR_NOT_IMPLEMENTED, "a handle with joints (their rows need the solver's own buffers)");
   cudaStream_t st = (cudaStream_t)stream;
   const int grid = v.grid_pcg;
   // scratch layout: corner terms, right-hand side, five CG vectors, partial

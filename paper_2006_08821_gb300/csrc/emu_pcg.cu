@@ -431,20 +431,23 @@ __global__ void __launch_bounds__(256) k_residual64(int64_t n, const int32_t* __
                                                     const int32_t* __restrict__ col, const double* __restrict__ val,
                                                     const double* __restrict__ b, const double* __restrict__ x,
                                                     float* __restrict__ r32, double* __restrict__ r64,
-                                                    double* __restrict__ partials) {
+                                                    double* __restrict__ partials, const uint8_t* __restrict__ skip) {
   __shared__ double sm[8 * 6];
   double loc[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     double acc[3];
     spmv_row<3, double>(rowptr, col, val, x, v, acc);
+    const bool sum = !(skip && skip[v]);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const double bv = b[3 * v + j];
       const double rv = bv - acc[j];
       if (r32) r32[3 * v + j] = (float)rv;
       if (r64) r64[3 * v + j] = rv;
-      loc[j] += rv * rv;
-      loc[3 + j] += bv * bv;
+      if (sum) {
+        loc[j] += rv * rv;
+        loc[3 + j] += bv * bv;
+      }
     }
   }
   block_partials<6>(loc, partials + (size_t)blockIdx.x * 6, sm);
@@ -465,8 +468,8 @@ __global__ void __launch_bounds__(256) k_axpy_f2d(int64_t n3, const float* __res
 
 cudaError_t launch_residual64(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* b,
                               const double* x, float* r32, double* r64, double* partials, int grid, double* out6,
-                              cudaStream_t st) {
-  k_residual64<<<grid, 256, 0, st>>>(n, rowptr, col, val, b, x, r32, r64, partials);
+                              cudaStream_t st, const uint8_t* skip) {
+  k_residual64<<<grid, 256, 0, st>>>(n, rowptr, col, val, b, x, r32, r64, partials, skip);
   k_sum_partials6<<<1, 32, 0, st>>>(partials, grid, out6);
   return cudaGetLastError();
 }

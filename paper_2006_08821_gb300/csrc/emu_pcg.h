@@ -75,10 +75,11 @@ cudaError_t launch_aphi32(int64_t n, const int32_t* rowptr, const int32_t* col, 
 
 // FP64 residual r = b - K x (3 columns), written as float (r32) and/or double
 // (r64) when those are non-null; out6 receives sum |r_j|^2 (j < 3) and
-// sum |b_j|^2 (3 + j).
+// sum |b_j|^2 (3 + j), over the rows v with skip[v] == 0 (all rows when skip
+// is null).
 cudaError_t launch_residual64(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* b,
                               const double* x, float* r32, double* r64, double* partials, int grid, double* out6,
-                              cudaStream_t st);
+                              cudaStream_t st, const uint8_t* skip = nullptr);
 // x += e (float correction into the FP64 iterate), 3n values.
 cudaError_t launch_axpy_f2d(int64_t n3, const float* e, double* x, cudaStream_t st);
 // x += e, 3n values (FP64).

@@ -70,7 +70,8 @@ def _desc(mesh):
 
 @pytest.mark.parametrize("mutate,code", [
     ("bad_index", -1), ("no_pins", -1), ("bad_poisson", -1), ("bad_kmodes", -1), ("empty", -1),
-    ("nan_rest", -1), ("bad_material", -1), ("bone", -10), ("joint", -10), ("neg_joints", -1),
+    ("nan_rest", -1), ("bad_material", -1), ("bone", -1), ("joint", -1), ("neg_joints", -1),
+    ("joint_without_bones", -1), ("bone_id_below_minus_one", -1),
 ])
 def test_create_rejects_invalid_input_before_touching_the_device(lib, mutate, code):
     from paper_2006_08821_gb300 import binding as B
@@ -92,13 +93,27 @@ def test_create_rejects_invalid_input_before_touching_the_device(lib, mutate, co
         d.n_fixed = 0
     if mutate == "empty":
         d.n_tets = 0
-    if mutate == "bone":  # bones exist in the oracle only: EMU_ERR_NOT_IMPLEMENTED
+    if mutate in ("bone", "bone_id_below_minus_one"):
+        # tet 0 touches the pinned face: a bone with part of its vertices pinned
         bid = np.full(mesh.n_tets, -1, dtype=np.int32)
-        bid[0] = 0
+        bid[0] = 0 if mutate == "bone" else -2
         keep.append(bid)
         d.bone_id = bid.ctypes.data_as(C.POINTER(C.c_int32))
-    if mutate == "joint":
+    if mutate == "joint":  # joint arrays missing
         d.n_joints = 1
+    if mutate == "joint_without_bones":
+        jt = np.array([1], dtype=np.int32)
+        jb = np.array([0, 1], dtype=np.int32)
+        jp = np.zeros(3)
+        ja = np.array([0.0, 1.0, 0.0])
+        jh = np.array([0.01])
+        keep += [jt, jb, jp, ja, jh]
+        d.n_joints = 1
+        d.joint_type = jt.ctypes.data_as(C.POINTER(C.c_int32))
+        d.joint_bones = jb.ctypes.data_as(C.POINTER(C.c_int32))
+        d.joint_point = jp.ctypes.data_as(C.POINTER(C.c_double))
+        d.joint_axis = ja.ctypes.data_as(C.POINTER(C.c_double))
+        d.joint_half_length = jh.ctypes.data_as(C.POINTER(C.c_double))
     if mutate == "neg_joints":
         d.n_joints = -1
     p = B.Params().to_c()

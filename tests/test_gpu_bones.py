@@ -1,0 +1,206 @@
+"""GPU parity of affine bones and joints (Sec. 3.3) against the bone oracle.
+
+The assembly is the arm of the synthetic inputs at its smallest size: two
+2 x 2 x 4-cell box bones (bone 1 pinned), a hinge in the gap between them
+and a small fusiform muscle spanning both (576 tets). Parity is on the
+positions after the final coupling solve (bone rows hard, joints a
+penalty), relative to the rest bounding-box diagonal:
+
+  * FP64 path: 1e-9, both sides converged to a relative residual of 3e-11
+    (the GPU) and 2e-11 (the oracle; 3e-11 or 5e-11 where its line search
+    cannot resolve the energy decrease that far). The bone's modulus is
+    1.7e4 times the muscle's: below about 2e-11 the FP64 rounding of the
+    energy change exceeds the Armijo margin on both sides (measured: the
+    oracle's line search fails at 1e-11, the GPU's near 4e-11). The
+    oracle's own positions move by 7.8e-10 of the diagonal between 1e-10
+    and 3e-11;
+  * mixed path: 1e-4 at the GPU's relative residual 1e-6.
+
+The GPU result must also satisfy, by itself, what the final solve imposes:
+the pinned bone at rest, the free bone's vertices on an affine map of its
+own F_b, the hinge nearly closed and F_b a rotation about the hinge axis.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from emu_inputs import arm_assembly
+from oracle import OracleParams
+from oracle.bones import BoneOracle
+
+pytestmark = pytest.mark.gpu
+
+PRM = OracleParams(alpha_rel=1.0, weight_mode=0)
+
+
+@pytest.fixture(scope="module")
+def emu():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2006_08821_gb300 import build as b
+
+    b.build()
+    import paper_2006_08821_gb300 as emu
+
+    emu.load_library()
+    return emu
+
+
+@pytest.fixture(scope="module")
+def arm():
+    return arm_assembly(bone_w=2, bone_len=4, r0=2.0, frames=4)
+
+
+def _oracle_solve(o, a, X0=None):
+    for tol in (2e-11, 3e-11, 5e-11):
+        try:
+            return o.solve(a, X0=X0, tol=tol)
+        except RuntimeError:  # the line search cannot resolve the decrease
+            continue
+    return o.solve(a, X0=X0, tol=1e-10)
+
+
+@pytest.fixture(scope="module")
+def oracle_frame2(arm):
+    o = BoneOracle(arm, PRM)
+    return o, _oracle_solve(o, arm.activations[2])
+
+
+def _diag(mesh):
+    return float(np.linalg.norm(mesh.rest_pos.max(0) - mesh.rest_pos.min(0)))
+
+
+TOL64 = 3e-11  # the GPU's FP64 parity tolerance on the assemblies
+
+
+def _gpu(emu, mesh, a, precision=0, tol=TOL64, **kw):
+    s = emu.Solver(mesh, emu.Params(tol_rel_residual=tol, precision=precision, **kw))
+    s.set_activation(a)
+    st = s.solve()
+    return s, st
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(0, TOL64, 1e-9), (1, 1e-6, 1e-4)])
+def test_arm_assembly_matches_the_bone_oracle(emu, arm, oracle_frame2, precision, tol, bound):
+    o, r = oracle_frame2
+    s, st = _gpu(emu, arm, arm.activations[2], precision=precision, tol=tol)
+    assert st.status == 0 and st.rel_residual <= tol, (st.status, st.rel_residual)
+    q = s.positions()
+    err = np.abs(q - r.q).max() / _diag(arm)
+    assert err <= bound, (err, st.newton_iters, r.iterations)
+    s.close()
+
+
+def test_final_solve_on_the_gpu_makes_the_bones_affine_and_keeps_the_hinge(emu, arm):
+    s, st = _gpu(emu, arm, arm.activations[2])
+    q = s.positions()
+    R, _, F = s.element_state()
+    s.close()
+    diag = _diag(arm)
+    v1 = np.unique(arm.tets[arm.bone_id == 0])
+    v2 = np.unique(arm.tets[arm.bone_id == 1])
+    np.testing.assert_array_equal(q[v1], arm.rest_pos[v1])          # pinned bone at rest
+    t2 = np.nonzero(arm.bone_id == 1)[0]
+    Fb = F[t2[0]]
+    np.testing.assert_array_equal(F[t2], np.broadcast_to(Fb, F[t2].shape))  # one F per bone
+    aff = q[v2] - arm.rest_pos[v2] @ Fb.T
+    assert np.abs(aff - aff.mean(0)).max() <= 1e-12 * diag          # q_v = F_b Q_v + t_b
+    disp = np.abs(q - arm.rest_pos).max()
+    assert disp > 1e-3 * diag
+    # the hinge's two points: each bone's affine map carries them to the same place
+    j = arm.joints[0]
+    ax = np.asarray(j["axis"]) / np.linalg.norm(j["axis"])
+    for sgn in (1.0, -1.0):
+        p = np.asarray(j["point"]) + sgn * j["half_length"] * ax
+        x2 = Fb @ p + aff.mean(0)
+        assert np.linalg.norm(x2 - p) <= 1e-5 * disp
+    # F_b is a rotation about the hinge axis by a visible angle
+    U, S, Vt = np.linalg.svd(Fb)
+    Rb = U @ Vt
+    assert np.abs(S - 1.0).max() <= 1e-6
+    angle = np.arccos(np.clip(0.5 * (np.trace(Rb) - 1.0), -1.0, 1.0))
+    axis = np.array([Rb[2, 1] - Rb[1, 2], Rb[0, 2] - Rb[2, 0], Rb[1, 0] - Rb[0, 1]])
+    axis /= np.linalg.norm(axis)
+    assert angle > 0.05
+    assert abs(axis @ ax) >= 1.0 - 1e-8
+
+
+def test_warm_started_frames_match_the_bone_oracle(emu, arm):
+    o = BoneOracle(arm, PRM)
+    # warm starts land nearer the FP64 energy floor: 5e-11 (measured error at
+    # 5e-11 against the oracle at 2e-11: 2.3e-10 of the diagonal)
+    s = emu.Solver(arm, emu.Params(tol_rel_residual=5e-11))
+    X = None
+    for f in (1, 2, 3):
+        a = arm.activations[f]
+        r = _oracle_solve(o, a, X0=X)
+        X = r.F
+        s.set_activation(a)
+        st = s.solve()
+        assert st.status == 0
+        err = np.abs(s.positions() - r.q).max() / _diag(arm)
+        assert err <= 1e-9, (f, err)
+    s.close()
+
+
+@pytest.mark.parametrize("variant", ["ball", "no_joint"])
+def test_ball_joint_and_a_free_bone_without_joint_match_the_oracle(emu, arm, variant):
+    joints = None if variant == "no_joint" else [dict(type="ball", bones=(0, 1), point=arm.joints[0]["point"])]
+    mesh = dataclasses.replace(arm, joints=joints)
+    r = _oracle_solve(BoneOracle(mesh, PRM), mesh.activations[2])
+    s, st = _gpu(emu, mesh, mesh.activations[2])
+    assert st.status == 0
+    err = np.abs(s.positions() - r.q).max() / _diag(mesh)
+    assert err <= 1e-9, err
+    s.close()
+
+
+def test_only_a_pinned_bone(emu, arm):
+    # bone 2 turned into muscle: one pinned bone, no free bone, no joint
+    bid = arm.bone_id.copy()
+    mat = arm.material_id.copy()
+    mat[bid == 1] = 0
+    bid[bid == 1] = -1
+    mesh = dataclasses.replace(arm, bone_id=bid, material_id=mat, joints=None)
+    r = _oracle_solve(BoneOracle(mesh, PRM), mesh.activations[2])
+    s, st = _gpu(emu, mesh, mesh.activations[2])
+    assert st.status == 0
+    err = np.abs(s.positions() - r.q).max() / _diag(mesh)
+    assert err <= 1e-9, err
+    s.close()
+
+
+def test_bone_assembly_is_the_same_alone_and_in_a_batch(emu, arm):
+    import torch
+
+    a = arm.activations[2]
+    solo, _ = _gpu(emu, arm, a, precision=1, tol=1e-6)
+    q_solo = solo.positions()
+    solo.close()
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    ss = [emu.Solver(arm, emu.Params(tol_rel_residual=1e-6, precision=1), stream=st.cuda_stream) for st in streams]
+    for s in ss:
+        s.set_activation(a)
+    stats = emu.batch_solve(ss)
+    assert all(st.status == 0 for st in stats)
+    for s in ss:
+        np.testing.assert_array_equal(s.positions(), q_solo)
+        s.close()
+
+
+def test_invalid_bone_inputs_are_rejected(emu, arm):
+    # a bone with only part of its vertices pinned
+    v2 = np.unique(arm.tets[arm.bone_id == 1])
+    bad = dataclasses.replace(arm, fixed_verts=np.concatenate([arm.fixed_verts, v2[:1]]).astype(np.int32))
+    with pytest.raises(emu.EmuError) as e:
+        emu.Solver(bad, emu.Params())
+    assert e.value.code == -1
+    # activation on a bone tet
+    s = emu.Solver(arm, emu.Params())
+    a = arm.activations[2].copy()
+    a[np.nonzero(arm.bone_id == 1)[0][0]] = 0.1
+    with pytest.raises(emu.EmuError):
+        s.set_activation(a)
+    s.close()
