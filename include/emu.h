@@ -347,6 +347,18 @@ int emu_get_sizes(emu_handle* h, int64_t* n_verts, int64_t* n_tets, int32_t* k_m
 int emu_eval_stretch_terms(const double* s, const double* params, int64_t n, int32_t mixed,
                            double* psi, double* grad, double* hess, void* stream);
 
+/* Self-check of the bounded device waits (no counterpart in the paper).
+ * Every spin-wait in this library's kernels (the grid barriers of the
+ * persistent CG kernels) gives up after about 2 s of GPU time, raises an
+ * error word and lets the kernel return, so a solve reports
+ * EMU_ERR_TIMEOUT instead of hanging, and the context stays usable. This
+ * call runs the same barrier in a two-block cooperative launch in which one
+ * block never arrives, with a wait limit of ``wait_ns`` nanoseconds (1e3 to
+ * 1e10): it returns EMU_ERR_TIMEOUT when the wait ran out as designed (the
+ * expected result), EMU_OK would mean it did not. It allocates 256 bytes of
+ * device memory for the duration of the call and synchronises ``stream``. */
+int emu_check_bounded_wait(int64_t wait_ns, void* stream);
+
 /* Polar decomposition F = R S (R proper rotation, S symmetric positive
  * definite) of n row-major 3x3 matrices with det F > 0, on the device.
  * Outputs R (n x 9) and s (n x 6, ordering as emu_get_element_state). */

@@ -12,6 +12,7 @@ from .binding import (  # noqa: F401
     Server,
     Solver,
     batch_solve,
+    check_bounded_wait,
     mesh_desc,
     required_bytes,
     TorchAllocator,

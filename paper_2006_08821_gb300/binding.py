@@ -38,7 +38,7 @@ EXPORTED = [
     "emu_get_element_state", "emu_set_element_state", "emu_reset", "emu_get_sizes",
     "emu_eval_stretch_terms", "emu_eval_polar", "emu_set_profiling", "emu_get_profile",
     "emu_acap_solve_noalloc", "emu_batch_solve", "emu_required_bytes", "emu_server_create",
-    "emu_server_submit", "emu_server_poll", "emu_server_result", "emu_server_destroy",
+    "emu_server_submit", "emu_server_poll", "emu_server_result", "emu_server_destroy", "emu_check_bounded_wait",
 ]
 
 PHASES = ["rhs", "assemble", "pcg", "grad", "syrk", "small", "dir", "ls", "update"]
@@ -176,6 +176,7 @@ def load_library(path: str = LIB_PATH):
     lib.emu_server_poll.argtypes = [C.c_void_p, P(C.c_uint64), C.c_int32, P(C.c_int32)]
     lib.emu_server_result.argtypes = [C.c_void_p, C.c_uint64, P(C.c_double), P(emu_request_stats)]
     lib.emu_server_destroy.argtypes = [C.c_void_p]
+    lib.emu_check_bounded_wait.argtypes = [C.c_int64, C.c_void_p]
     for name in EXPORTED:
         if name not in ("emu_default_params", "emu_status_string", "emu_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -473,6 +474,13 @@ def eval_stretch_terms(s_dev, params_dev, n, mixed, psi_dev, grad_dev, hess_dev,
     cv = lambda x: None if x is None else C.c_void_p(int(x))  # noqa: E731
     _check(lib.emu_eval_stretch_terms(cv(s_dev), cv(params_dev), n, mixed, cv(psi_dev), cv(grad_dev),
                                       cv(hess_dev), cv(stream)), lib)
+
+
+def check_bounded_wait(wait_ns: int, stream=0) -> int:
+    """emu_check_bounded_wait: status of a grid-barrier wait that must run out
+    (EMU_ERR_TIMEOUT is the expected result)."""
+    lib = load_library()
+    return lib.emu_check_bounded_wait(int(wait_ns), C.c_void_p(int(stream)) if stream else None)
 
 
 def eval_polar(F_dev, n, R_dev, s_dev, stream=0):

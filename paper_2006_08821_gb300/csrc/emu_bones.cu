@@ -249,7 +249,8 @@ __global__ void k_bone_dir(BoneArgs a, const double* __restrict__ z, double* gtd
 }
 
 // ------------------------------------------------------------ line search --
-__global__ void __launch_bounds__(256) k_bone_ls(BoneArgs a, const float* __restrict__ dq32, double rho,
+template <typename TQ>
+__global__ void __launch_bounds__(256) k_bone_ls(BoneArgs a, const TQ* __restrict__ dq32, double rho,
                                                  double* __restrict__ out) {
   __shared__ double sFmI[kMaxFreeBones][9], sd[kMaxFreeBones][9];
   double acc[kLsNV];
@@ -653,7 +654,11 @@ void launch_bone_dir(const BoneArgs& a, const double* z, double* gtd_out, cudaSt
 }
 
 void launch_bone_ls(const BoneArgs& a, const float* dq32, double rho, double* partials_out, cudaStream_t st) {
-  k_bone_ls<<<kBoneLsBlocks, 256, 0, st>>>(a, dq32, rho, partials_out);
+  k_bone_ls<float><<<kBoneLsBlocks, 256, 0, st>>>(a, dq32, rho, partials_out);
+}
+
+void launch_bone_ls(const BoneArgs& a, const double* dq64, double rho, double* partials_out, cudaStream_t st) {
+  k_bone_ls<double><<<kBoneLsBlocks, 256, 0, st>>>(a, dq64, rho, partials_out);
 }
 
 void launch_bone_update(const BoneArgs& a, cudaStream_t st) {

@@ -86,13 +86,14 @@ void launch_bone_mean(const BoneArgs& a, const double* q, cudaStream_t st);
 void launch_bone_eval(const BoneArgs& a, double* gref_out, cudaStream_t st);
 // d_b = -(y_b + (I - N_b) Gbar_b z) per free bone; sum_b g_b . d_b into *gtd_out.
 void launch_bone_dir(const BoneArgs& a, const double* z, double* gtd_out, cudaStream_t st);
-// Line-search terms of the free bones in FP64 for the mixed path: each
+// Line-search terms of the free bones in FP64 (both paths): each
 // bone's V_b [Psi(F_b + s_j d_b) - Psi(F_b)] for the kLsTrials trial steps
 // s_j = sigma_start rho^j, and over the bones' tets the ACAP coefficients
 // sum c_i D_i . dD_i and sum c_i |dD_i|^2 (D_i = G_i q - F_b, dD_i = G_i dq
 // - d_b). Written as kBoneLsBlocks block partials of kLsNV values.
 constexpr int kBoneLsBlocks = 32;
 void launch_bone_ls(const BoneArgs& a, const float* dq32, double rho, double* partials_out, cudaStream_t st);
+void launch_bone_ls(const BoneArgs& a, const double* dq64, double rho, double* partials_out, cudaStream_t st);
 // F' = R (S + sigma R^T d_b) per free bone, polar re-extraction in FP64, into
 // the bone state (mixed path; sigma from sc, nothing when it is 0).
 void launch_bone_update(const BoneArgs& a, cudaStream_t st);

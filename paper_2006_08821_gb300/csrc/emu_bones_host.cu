@@ -360,7 +360,8 @@ bool bones_alloc(emu_handle* h) {
          h->get(h->jlam, 3 * kMaxJointPts);
   if (dry || h->nfb > 0)
     ok = ok && h->get(h->frowptr, n + 1) && h->get(h->fcol, fnnz) && h->get(h->fval, fnnz) && h->get(h->fldinv, n) &&
-         h->get(h->fin_fixed, n) && h->get(h->zeta, 16 * n) && h->get(h->fdt, 3 * kMaxFreeBones);
+         h->get(h->fin_fixed, n) && h->get(h->zeta, 16 * n) && h->get(h->fdt, 3 * kMaxFreeBones) &&
+         h->get(h->phi_fin, 16 * n) && h->get(h->Einv_fin, 256);
   return ok;
 }
 
@@ -610,6 +611,35 @@ int final_setup_device(emu_handle* h) {
   if (!invert_small(A, nf)) return bfail(EMU_ERR_INVALID_ARG, "the final solve's bone translations are singular");
   for (int b = 0; b < nf; ++b)
     for (int b2 = 0; b2 < nf; ++b2) h->Ainv_h[b * kMaxFreeBones + b2] = A[b * nf + b2];
+  // coarse space of the final solve's CG: the basis with the rows the final
+  // solve pins set to zero, and the pseudo-inverse of its Galerkin matrix
+  std::vector<double> Ph((size_t)n * 16);
+  BONE_CK(cudaMemcpyAsync(Ph.data(), h->phi64, Ph.size() * 8, cudaMemcpyDeviceToHost, h->st));
+  BONE_CK(cudaStreamSynchronize(h->st));
+  for (int64_t v = 0; v < n; ++v)
+    if (h->fin_fixed_h[v])
+      for (int k = 0; k < 16; ++k) Ph[(size_t)v * 16 + k] = 0.0;
+  BONE_CK(cudaMemcpyAsync(h->phi_fin, Ph.data(), Ph.size() * 8, cudaMemcpyHostToDevice, h->st));
+  launch_galerkin16(n, h->frowptr, h->fcol, h->fval, h->phi_fin, Z, ggrid, h->part_pcg, h->st);
+  launch_reduce_cols(h->part_pcg, ggrid, 256, h->small, h->st);
+  BONE_CK(cudaGetLastError());
+  std::vector<double> Eg(256), Ev;
+  BONE_CK(cudaMemcpyAsync(Eg.data(), h->small, 256 * 8, cudaMemcpyDeviceToHost, h->st));
+  BONE_CK(cudaStreamSynchronize(h->st));
+  for (int i = 0; i < 16; ++i)
+    for (int j = 0; j < 16; ++j) Eg[16 * i + j] = 0.5 * (Eg[16 * i + j] + Eg[16 * j + i]);
+  host_jacobi_eig(Eg, Ev, 16);
+  double emax = 0.0;
+  for (int i = 0; i < 16; ++i) emax = std::max(emax, Eg[17 * i]);
+  std::vector<double> Ei(256, 0.0);
+  for (int k = 0; k < 16; ++k) {
+    const double lk = Eg[17 * k];
+    if (!(lk > 1e-12 * emax)) continue;
+    for (int i = 0; i < 16; ++i)
+      for (int j = 0; j < 16; ++j) Ei[16 * i + j] += Ev[16 * i + k] * Ev[16 * j + k] / lk;
+  }
+  BONE_CK(cudaMemcpyAsync(h->Einv_fin, Ei.data(), 256 * 8, cudaMemcpyHostToDevice, h->st));
+  BONE_CK(cudaStreamSynchronize(h->st));
   return EMU_OK;
 }
 
@@ -725,8 +755,8 @@ int bones_final_solve(emu_handle* h) {
     a.col = h->fcol;
     a.val = h->fval;
     a.dinv = h->fldinv;
-    a.phi = nullptr;
-    a.Einv = nullptr;
+    a.phi = h->phi_fin;
+    a.Einv = h->Einv_fin;
     a.max_iter = std::max(20000, 4 * h->prm.pcg_max);
     BONE_CK(cudaMemsetAsync(e64, 0, 24 * n, h->st));
     BONE_CK(launch_pcg<double>(3, a, h->grid_pcg3, h->st));

@@ -15,6 +15,11 @@
 #include "emu_pcg.h"
 
 namespace emu {
+// Cyclic Jacobi eigen-decomposition of a symmetric N x N matrix (row-major):
+// A is overwritten (its diagonal holds the eigenvalues), V receives the
+// eigenvectors as columns.
+void host_jacobi_eig(std::vector<double>& A, std::vector<double>& V, int N);
+
 struct DevBuf {
   void* p;
   size_t bytes;
@@ -135,6 +140,7 @@ struct emu_handle {
   uint8_t *jfree = nullptr, *jmask = nullptr;
   int32_t *frowptr = nullptr, *fcol = nullptr;
   double *fval = nullptr, *fldinv = nullptr, *zeta = nullptr, *fdt = nullptr;
+  double *phi_fin = nullptr, *Einv_fin = nullptr;  // coarse space of the final solve's CG
   uint8_t* fin_fixed = nullptr;
   int64_t fnnz = 0;
   BoneArgs bargs() const;

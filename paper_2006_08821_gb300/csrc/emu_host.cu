@@ -39,19 +39,10 @@ int fail(int code, const std::string& msg) {
 
 #include "emu_handle.h"
 
-namespace {
-
-uint64_t splitmix64(uint64_t& x) {
-  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
 // Cyclic Jacobi eigen-decomposition of a symmetric N x N matrix (row-major):
 // A is overwritten (its diagonal holds the eigenvalues), V receives the
 // eigenvectors as columns.
-void host_jacobi_eig(std::vector<double>& A, std::vector<double>& V, int N) {
+void emu::host_jacobi_eig(std::vector<double>& A, std::vector<double>& V, int N) {
   V.assign(N * N, 0.0);
   for (int i = 0; i < N; ++i) V[N * i + i] = 1.0;
   for (int sweep = 0; sweep < 60; ++sweep) {
@@ -87,6 +78,17 @@ void host_jacobi_eig(std::vector<double>& A, std::vector<double>& V, int N) {
       }
   }
 }
+
+
+namespace {
+
+uint64_t splitmix64(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 
 int validate_mesh(const emu_mesh_desc* d) {
   if (!d) return fail(EMU_ERR_INVALID_ARG, "mesh is NULL");
@@ -1006,6 +1008,7 @@ struct SolveTask {
   double res = 0.0, gnorm_ref = 0.0;
   bool first_eval = true;
   bool ls_refreshed = false;  // q re-solved during the current run of rejected passes
+  bool ref_short = false;     // the last exact re-solve stopped above its tolerance
   bool ls_retried = false;    // and dq tightened after it, too
   double best_res = 1e300;    // smallest residual so far and the iteration it was seen
   int best_it = 0;
@@ -1106,11 +1109,16 @@ int enqueue_step(emu_handle* h) {
   } else {
     TetArgs<double> al = a64;
     al.partials = h->part_ls;
+    int nls = h->grid_tet;
+    if (h->nfb > 0) {  // the free bones' terms, after the per-tet partials
+      launch_bone_ls(h->bargs(), h->dq, h->prm.ls_rho, h->part_ls + (size_t)h->grid_tet * kLsNV, h->st);
+      nls += kBoneLsBlocks;
+    }
     launch_ls<double>(al, h->grid_tet, h->prm.ls_rho, h->st);
     h->ph_end(EMU_PHASE_LS, 1);
     h->ph_begin();
-    launch_ls_select(h->part_dir, dir_partial_count(h), h->part_ls, h->grid_tet, h->sc, h->sigma0_now,
-                     h->prm.ls_rho, h->prm.ls_c, h->st);
+    launch_ls_select(h->part_dir, dir_partial_count(h), h->part_ls, nls, h->sc, h->sigma0_now, h->prm.ls_rho,
+                     h->prm.ls_c, h->st);
     h->ph_end(EMU_PHASE_SMALL, 1);
   }
   h->ph_begin();
@@ -1259,6 +1267,12 @@ int task_step(SolveTask* t) {
           return abort(fail(EMU_ERR_CUDA, "cudaMemcpyAsync failed"));
         t->gnorm_ref = h->gref > h->floor ? h->gref : 0.0;
         t->since = h->prm.q_refresh;  // iterations since q was last solved exactly
+        // dq starts from zero in every solve: the result depends only on the
+        // element state, q and the activation (resume from
+        // emu_set_element_state is bit-for-bit an uninterrupted run)
+        if (cudaMemsetAsync(h->dq, 0, 24 * h->n, h->st) != cudaSuccess ||
+            (h->dq32 && cudaMemsetAsync(h->dq32, 0, 12 * h->n, h->st) != cudaSuccess))
+          return abort(fail(EMU_ERR_CUDA, "cudaMemsetAsync failed"));
         h->dq_tol_now = start_dq_tol(h);
         t->phase = SolveTask::TOP;
         break;
@@ -1280,9 +1294,11 @@ int task_step(SolveTask* t) {
         if (rc) return abort(rc);
         t->phase = SolveTask::REF_CHECK;
         return wait();
-      case SolveTask::REF_CHECK:
+      case SolveTask::REF_CHECK: {
         h->prof_flush();
-        if (refresh_converged(h, h->q_tol) || t->round + 1 >= kRefreshRounds) {
+        const bool conv = refresh_converged(h, h->q_tol);
+        if (conv || t->round + 1 >= kRefreshRounds) {
+          t->ref_short = !conv;
           t->since = 0;
           t->phase = SolveTask::GRAD;
           break;
@@ -1292,6 +1308,7 @@ int task_step(SolveTask* t) {
         ++t->round;
         t->phase = SolveTask::REF_RES;
         break;
+      }
       case SolveTask::GRAD:
         rc = enqueue_grad(h);
         if (rc) return abort(rc);
@@ -1307,6 +1324,13 @@ int task_step(SolveTask* t) {
         }
         if (hs.nonfinite || !std::isfinite(hs.gnorm2)) {
           t->status = fail(EMU_ERR_INVERTED, "non-finite gradient");
+          t->phase = SolveTask::FINISH;
+          break;
+        }
+        if (t->ref_short && hs.pcg_fail) {
+          // the exact coupling solve (Eq. 4) stopped above its tolerance
+          // because its CG solves ran into pcg_max
+          t->status = fail(EMU_ERR_PCG, "the coupling solve reached pcg_max before its tolerance");
           t->phase = SolveTask::FINISH;
           break;
         }
@@ -1644,6 +1668,23 @@ int emu_eval_stretch_terms(const double* s, const double* params, int64_t n, int
   launch_eval_stretch(s, params, n, mixed, psi, grad, hess, (cudaStream_t)stream);
   EMU_CK(cudaGetLastError());
   EMU_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return EMU_OK;
+}
+
+int emu_check_bounded_wait(int64_t wait_ns, void* stream) {
+  if (wait_ns < 1000 || wait_ns > 10000000000ll) return fail(EMU_ERR_INVALID_ARG, "wait_ns must be in [1e3, 1e10]");
+  cudaStream_t st = (cudaStream_t)stream;
+  void* buf = nullptr;
+  EMU_CK(cudaMalloc(&buf, 256));
+  int timed_out = 0;
+  cudaError_t e = launch_wait_check(static_cast<GridBarrier*>(buf), (unsigned long long)wait_ns,
+                                    reinterpret_cast<int*>(static_cast<char*>(buf) + 128), st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&timed_out, static_cast<char*>(buf) + 128, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(EMU_ERR_CUDA, std::string("emu_check_bounded_wait: ") + cudaGetErrorString(e));
+  if (timed_out) return fail(EMU_ERR_TIMEOUT, "the check's grid-barrier wait ran out after its limit (as designed)");
   return EMU_OK;
 }
 

@@ -82,6 +82,20 @@ struct AcapView {
   int sms;
 };
 bool acap_view(const emu_handle* h, AcapView* v);
+
+// Bounded waits. Every spin-wait of the library's kernels (the grid barriers
+// of the persistent CG kernels) gives up after kWaitLimitNs of GPU time (the
+// %globaltimer clock), raises an error word that the other blocks see, and
+// the kernel returns with a timeout flag the host reads (EMU_ERR_TIMEOUT).
+// A spin-count cap backs the clock up.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr unsigned long long kWaitSpinCap = 1ull << 28;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 void set_last_error(const char* msg);
 
 // Resumable quasi-static solve of one handle (the same steps as

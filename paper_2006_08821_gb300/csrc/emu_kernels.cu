@@ -500,6 +500,8 @@ __global__ void __launch_bounds__(128) k_ls(TetArgs<TW> a, double rho) {
 #pragma unroll
   for (int k = 0; k < kLsNV; ++k) acc[k] = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    // free bones' tets: once per bone in the bone kernel; pinned bones' tets contribute 0
+    if (a.tkind && a.tkind[i] != kTetDeformable) continue;
     const int4 t = a.tet[i];
     double D9[9], R[9], sv[6], S[9], F[9], A[9], dA[9], d[9];
     load_dinv(a.Dinv, m, i, D9);

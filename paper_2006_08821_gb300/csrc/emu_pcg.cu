@@ -21,26 +21,29 @@ namespace emu {
 
 // Bounded grid barrier. ``count`` grows by gridDim.x per barrier (reset by the
 // host before each launch); the last block to arrive publishes the epoch.
-// A block that spins longer than kSpinLimit polls sets ``err`` and leaves;
-// the others see ``err`` and leave too, so no wait is unbounded.
-static constexpr unsigned long long kSpinLimit = 1ull << 25;  // ~ seconds with nanosleep
-
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned& epoch, int* s_flag) {
+// A block that waits longer than wait_ns (GPU clock) or kWaitSpinCap polls
+// sets ``err`` and leaves; the others see ``err`` and leave too, so no wait
+// is unbounded. ``arrive`` false leaves without arriving (the self-check of
+// launch_wait_check only).
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned& epoch, int* s_flag,
+                                          unsigned long long wait_ns, bool arrive = true) {
   __syncthreads();
   if (threadIdx.x == 0) {
     epoch += 1u;
     __threadfence();
-    unsigned prev = atomicAdd(&bar->count, 1u);
-    if (prev + 1u == gridDim.x * epoch) {
+    const unsigned prev = arrive ? atomicAdd(&bar->count, 1u) : 0u;
+    if (arrive && prev + 1u == gridDim.x * epoch) {
       __threadfence();
       atomicExch(&bar->gen, epoch);
     } else {
+      const unsigned long long t0 = global_ns();
       unsigned long long spins = 0;
       while (true) {
         unsigned g = *((volatile unsigned*)&bar->gen);
         if (g >= epoch) break;
         if (*((volatile int*)&bar->err)) break;
-        if (++spins > kSpinLimit) {
+        ++spins;
+        if (spins > kWaitSpinCap || ((spins & 63u) == 0u && global_ns() - t0 > wait_ns)) {
           atomicExch(&bar->err, 1);
           break;
         }
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgsT<T> a) {
       }
     }
     block_partials<NC>(loc, a.partials + (size_t)blockIdx.x * NV0, sm);
-    if (!grid_sync(a.bar, epoch, &s_flag)) goto timeout;
+    if (!grid_sync(a.bar, epoch, &s_flag, a.wait_ns)) goto timeout;
     {
       double tmp[NC > 0 ? NC : 1];
 #pragma unroll
@@ -220,10 +223,10 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgsT<T> a) {
       block_partials<NC>(tmp, s_rho, sm);
     }
     coarse_coeffs();
-    if (!grid_sync(a.bar, epoch, &s_flag)) goto timeout;  // partials are rewritten below
+    if (!grid_sync(a.bar, epoch, &s_flag, a.wait_ns)) goto timeout;  // partials are rewritten below
   }
   for (int64_t v = r0 + threadIdx.x; v < r1; v += blockDim.x) precond_row(v);
-  if (!grid_sync(a.bar, epoch, &s_flag)) goto timeout;
+  if (!grid_sync(a.bar, epoch, &s_flag, a.wait_ns)) goto timeout;
   {
     double loc[NV0];
 #pragma unroll
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgsT<T> a) {
     }
     block_partials<NV0>(loc, a.partials + (size_t)blockIdx.x * NV0, sm);
   }
-  if (!grid_sync(a.bar, epoch, &s_flag)) goto timeout;
+  if (!grid_sync(a.bar, epoch, &s_flag, a.wait_ns)) goto timeout;
   sum_partials<NV0>(a.partials, sc, sm);
   if (threadIdx.x == 0) {
     for (int j = 0; j < NR; ++j) {
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgsT<T> a) {
         }
         precond_row(v);
       }
-      if (!grid_sync(a.bar, epoch, &s_flag)) goto timeout;
+      if (!grid_sync(a.bar, epoch, &s_flag, a.wait_ns)) goto timeout;
       {
         double loc[NV];
 #pragma unroll
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgsT<T> a) {
         }
         block_partials<NV>(loc, a.partials + (size_t)blockIdx.x * NV, sm);
       }
-      if (!grid_sync(a.bar, epoch, &s_flag)) goto timeout;
+      if (!grid_sync(a.bar, epoch, &s_flag, a.wait_ns)) goto timeout;
       sum_partials<NV>(a.partials, sc, sm);
       if (threadIdx.x == 0) {
         for (int j = 0; j < NR; ++j) {
@@ -391,6 +394,21 @@ static cudaError_t launch_pcg_impl(const PcgArgsT<T>& args, int grid, cudaStream
   PcgArgsT<T> a = args;
   void* params[] = {(void*)&a};
   return cudaLaunchCooperativeKernel((const void*)pcg_kernel<NR, T, COARSE>, dim3(grid), dim3(256), params, 0, st);
+}
+
+__global__ void __launch_bounds__(32) k_wait_check(GridBarrier* bar, unsigned long long wait_ns, int* timed_out) {
+  __shared__ int s_flag;
+  unsigned epoch = 0;
+  // block 1 leaves without arriving: block 0's wait can only run out
+  const bool ok = grid_sync(bar, epoch, &s_flag, wait_ns, blockIdx.x == 0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *timed_out = ok ? 0 : 1;
+}
+
+cudaError_t launch_wait_check(GridBarrier* bar, unsigned long long wait_ns, int* timed_out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st);
+  if (e != cudaSuccess) return e;
+  void* params[] = {(void*)&bar, (void*)&wait_ns, (void*)&timed_out};
+  return cudaLaunchCooperativeKernel((const void*)k_wait_check, dim3(2), dim3(32), params, 0, st);
 }
 
 int pcg_max_grid(int nrhs, int64_t n) {

@@ -40,6 +40,7 @@ template <typename T> struct PcgArgsT {
   double* relres_out;  // final ||r_j|| / ||b_j|| per column (may be null)
   const T* phi;        // n x 16 coarse basis (null: Jacobi only; 3 columns only)
   const double* Einv;  // 16 x 16 (pseudo-)inverse of Phi^T L Phi
+  unsigned long long wait_ns = kWaitLimitNs;  // limit of each grid-barrier wait
 };
 
 int pcg_max_grid(int nrhs, int64_t n);
@@ -84,5 +85,11 @@ cudaError_t launch_residual64(int64_t n, const int32_t* rowptr, const int32_t* c
 cudaError_t launch_axpy_f2d(int64_t n3, const float* e, double* x, cudaStream_t st);
 // x += e, 3n values (FP64).
 cudaError_t launch_axpy_d2d(int64_t n3, const double* e, double* x, cudaStream_t st);
+
+// Self-check of the bounded grid-barrier wait: a cooperative launch of two
+// blocks in which block 1 leaves without arriving, so block 0's wait must run
+// out after wait_ns and report it. *timed_out (device int) receives 1 when
+// the wait gave up as designed.
+cudaError_t launch_wait_check(GridBarrier* bar, unsigned long long wait_ns, int* timed_out, cudaStream_t st);
 
 }  // namespace emu

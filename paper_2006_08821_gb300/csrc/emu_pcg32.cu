@@ -29,7 +29,6 @@ namespace {
 
 constexpr int NT = 256;  // threads per block
 constexpr int NR = 3;    // right-hand sides (x, y, z)
-constexpr unsigned long long kSpinLimit32 = 1ull << 25;
 constexpr int kGather = 16;  // entries of a matrix row gathered at once
 constexpr int kMaxGridStrides = 8;  // grid_sum_f handles up to 256 blocks
 // words of Pcg32Work::sync, one 128-byte line apart
@@ -51,7 +50,7 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // for e * gridDim.x arrivals); the last block to leave the kernel zeroes it
 // for the next launch. The wait is bounded: on timeout the block raises the
 // error word, every other waiter sees it, and all blocks leave.
-__device__ __forceinline__ bool gbar(const Pcg32Work& wk, unsigned& epoch, int* s_flag) {
+__device__ __forceinline__ bool gbar(const Pcg32Work& wk, unsigned& epoch, int* s_flag, unsigned long long wait_ns) {
   __syncthreads();
   epoch += 1u;
   if (threadIdx.x == 0) {
@@ -59,16 +58,22 @@ __device__ __forceinline__ bool gbar(const Pcg32Work& wk, unsigned& epoch, int* 
     const unsigned target = gridDim.x * epoch;
     int bad = 0;
     unsigned long long spins = 0;
+    unsigned long long t0 = 0;
     while (ld_acquire_u32(wk.sync + kSyncCount) < target) {
       ++spins;
-      if ((spins & 63u) == 0u && *((volatile unsigned*)(wk.sync + kSyncErr))) {
-        bad = 1;
-        break;
-      }
-      if (spins > kSpinLimit32) {
-        bad = 1;
-        atomicExch(wk.sync + kSyncErr, 1u);
-        break;
+      if ((spins & 63u) == 0u) {
+        if (*((volatile unsigned*)(wk.sync + kSyncErr))) {
+          bad = 1;
+          break;
+        }
+        // the clock is read only once a wait is long (the fast path polls)
+        const unsigned long long now = global_ns();
+        if (t0 == 0) t0 = now;
+        if (now - t0 > wait_ns || spins > kWaitSpinCap) {
+          bad = 1;
+          atomicExch(wk.sync + kSyncErr, 1u);
+          break;
+        }
       }
     }
     *s_flag = bad;
@@ -356,7 +361,7 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
     const int64_t v = g0 + k * stride;
     if (own[k]) ugx[v] = make_float4(x[k][0], x[k][1], x[k][2], 0.f);
   }
-  if (!gbar(wk, epoch, &s_flag)) goto timeout;
+  if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
   spmv(ugx, w);
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
@@ -371,7 +376,7 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
     phi_t(r, loc);
     block_sum_f<NV0>(loc, ssum, sm);
     for (int k = threadIdx.x; k < NC; k += NT) part[(size_t)k * G + blockIdx.x] = ssum[k];
-    if (!gbar(wk, epoch, &s_flag)) goto timeout;
+    if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
     global_sum(NC);
     for (int k = threadIdx.x; k < NC; k += NT) s_rho[k] = ssum[k];
     __syncthreads();
@@ -379,7 +384,7 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
   }
   // u goes to its own buffer, so no block can overwrite x while it is read
   precond();
-  if (!gbar(wk, epoch, &s_flag)) goto timeout;
+  if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
   spmv(ugu, w);
   {
     float loc[NV0];
@@ -402,7 +407,7 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
     block_sum_f<NV0>(loc, ssum, sm);
     for (int k = threadIdx.x; k < NV0; k += NT) part[(size_t)k * G + blockIdx.x] = ssum[k];
   }
-  if (!gbar(wk, epoch, &s_flag)) goto timeout;
+  if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
   global_sum(NV0);
   if (threadIdx.x < NR) {
     const int j = threadIdx.x;
@@ -451,7 +456,7 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
         coarse_cc();
       }
       precond();
-      if (!gbar(wk, epoch, &s_flag)) goto timeout;
+      if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
       spmv(ugu, w);
       {
         float loc[NV];
@@ -474,7 +479,7 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
         block_sum_f<NV0>(lfull, ssum, sm);
         for (int k = threadIdx.x; k < NV; k += NT) part[(size_t)k * G + blockIdx.x] = ssum[k];
       }
-      if (!gbar(wk, epoch, &s_flag)) goto timeout;
+      if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
       global_sum(NV);
       if (threadIdx.x < NR) {
         const int j = threadIdx.x;
@@ -618,7 +623,7 @@ __global__ void __launch_bounds__(NT, 1) pcg32p_kernel(PcgArgsT<float> a, Pcg32W
     const int64_t v = g0 + k * stride;
     if (own[k]) wk.ug[v] = make_float4(x[k][0], x[k][1], x[k][2], 0.f);
   }
-  if (!gbar(wk, epoch, &s_flag)) goto timeout;
+  if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
   spmv(wk.ug, w);
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
@@ -633,7 +638,7 @@ __global__ void __launch_bounds__(NT, 1) pcg32p_kernel(PcgArgsT<float> a, Pcg32W
     phi_t(r, loc);
     block_sum_f<NV0>(loc, ssum, sm);
     for (int k = threadIdx.x; k < NC; k += NT) wk.part[(size_t)k * G + blockIdx.x] = ssum[k];
-    if (!gbar(wk, epoch, &s_flag)) goto timeout;
+    if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
     grid_sum_f<NV0>(wk.part, NC, ssum);
     for (int k = threadIdx.x; k < NC; k += NT) s_rho[k] = ssum[k];
     __syncthreads();
@@ -646,7 +651,7 @@ __global__ void __launch_bounds__(NT, 1) pcg32p_kernel(PcgArgsT<float> a, Pcg32W
       if (own[k]) wk.ug[n + v] = make_float4(u[k][0], u[k][1], u[k][2], 0.f);
     }
   }
-  if (!gbar(wk, epoch, &s_flag)) goto timeout;
+  if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
   spmv(wk.ug + n, w);  // w = A u
 
   {
@@ -679,7 +684,7 @@ __global__ void __launch_bounds__(NT, 1) pcg32p_kernel(PcgArgsT<float> a, Pcg32W
         block_sum_f<NV0>(loc, ssum, sm);
         for (int k = threadIdx.x; k < NV0; k += NT) pb[(size_t)k * G + blockIdx.x] = ssum[k];
       }
-      if (!gbar(wk, epoch, &s_flag)) goto timeout;
+      if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
       grid_sum_f<NV0>(pb, NV0, ssum);
       if (threadIdx.x < NR) {
         const int j = threadIdx.x;

@@ -129,9 +129,10 @@ def test_final_solve_on_the_gpu_makes_the_bones_affine_and_keeps_the_hinge(emu, 
 
 def test_warm_started_frames_match_the_bone_oracle(emu, arm):
     o = BoneOracle(arm, PRM)
-    # warm starts land nearer the FP64 energy floor: 5e-11 (measured error at
-    # 5e-11 against the oracle at 2e-11: 2.3e-10 of the diagonal)
-    s = emu.Solver(arm, emu.Params(tol_rel_residual=5e-11))
+    # a frame started from the previous frame's state ends nearer the FP64
+    # energy floor, which lies near 1e-10 on the first frame (measured: the
+    # line search stops between 7e-11 and 1.1e-10 there): 2e-10
+    s = emu.Solver(arm, emu.Params(tol_rel_residual=2e-10))
     X = None
     for f in (1, 2, 3):
         a = arm.activations[f]
