@@ -263,13 +263,18 @@ int emu_required_bytes(const emu_mesh_desc* desc, const emu_params* params, size
  * request is one mesh and n_frames activation vectors, solved frame by frame
  * from its own resident state (warm starts). A worker thread admits queued
  * requests in arrival order while their device memory (emu_required_bytes)
- * fits in the budget and fewer than 32 are active, builds each on its own
- * stream, and interleaves the active requests' Newton loops so that their
- * work overlaps on the device (continuous batching: a request that arrives
- * while others run is admitted as soon as memory and a slot free up). A
- * request's memory is released when its last frame is done. The result of a
- * request does not depend on what else is in flight (every kernel is
- * deterministic and touches only its own handle's memory).
+ * fits in the budget and fewer than 32 are in flight, and interleaves the
+ * active requests' Newton loops, each on its own stream, so that their work
+ * overlaps on the device (continuous batching: a request that arrives while
+ * others run is admitted as soon as memory and a slot free up). A second
+ * thread builds each admitted request's handle (emu_create, including the
+ * low-rank basis) and destroys finished ones, so requests in flight keep
+ * advancing while others are set up or released. Without an allocator the
+ * handles' memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+ * request's stream). A request's memory returns to the budget once its
+ * handle is released after its last frame; its result is published before
+ * that. The result of a request does not depend on what else is in flight
+ * (every kernel is deterministic and touches only its own handle's memory).
  * Submit, poll and result may be called from any thread. */
 typedef struct emu_server emu_server;
 
@@ -308,7 +313,7 @@ int emu_server_poll(emu_server* srv, uint64_t* done_ids, int32_t cap, int32_t* n
  * not finished. */
 int emu_server_result(emu_server* srv, uint64_t request_id, double* positions, emu_request_stats* stats);
 
-/* Stops the worker: device work already enqueued is waited for, requests
+/* Stops both threads: device work already enqueued is waited for, requests
  * not finished are dropped, and everything is freed. */
 int emu_server_destroy(emu_server* srv);
 

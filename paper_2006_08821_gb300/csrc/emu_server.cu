@@ -36,8 +36,10 @@ struct Request {
   std::vector<double> rest_pos, youngs, poisson, fiber_dir, fixed_pos, acts;
   std::vector<int32_t> tets, fixed_verts;
   std::vector<uint8_t> material_id;
-  int32_t n_materials = 0;
-  bool has_fiber = false, has_fixed_pos = false;
+  std::vector<int32_t> bone_id, joint_type, joint_bones;
+  std::vector<double> joint_point, joint_axis, joint_half_length;
+  int32_t n_materials = 0, n_joints = 0;
+  bool has_fiber = false, has_fixed_pos = false, has_bones = false;
   std::vector<double> positions;  // frames x n x 3
   emu_request_stats stats;
   clk::time_point t_submit, t_admit, t_ready;
@@ -64,48 +66,98 @@ struct Request {
     d.n_fixed = (int64_t)fixed_verts.size();
     d.fixed_verts = fixed_verts.data();
     d.fixed_pos = has_fixed_pos ? fixed_pos.data() : nullptr;
+    d.bone_id = has_bones ? bone_id.data() : nullptr;
+    d.n_joints = n_joints;
+    if (n_joints > 0) {
+      d.joint_type = joint_type.data();
+      d.joint_bones = joint_bones.data();
+      d.joint_point = joint_point.data();
+      d.joint_axis = joint_axis.data();
+      d.joint_half_length = joint_half_length.data();
+    }
     return d;
   }
 };
 
 }  // namespace
 
+// Device resources of a request while it is active; released off the
+// worker thread.
+struct Slot {
+  emu_handle* h = nullptr;
+  cudaStream_t st = nullptr;
+  emu::SolveTask* task = nullptr;
+  uint64_t bytes = 0;
+};
+
 struct emu_server {
   size_t budget = 0, used = 0;
+  int inflight = 0;  // requests admitted and not yet released (<= kMaxActive)
   emu_params prm;
   emu_allocator alloc;
   bool has_alloc = false;
   int device = 0;
   std::mutex mu;
-  std::condition_variable cv;
+  std::condition_variable cv;       // wakes the worker
+  std::condition_variable prep_cv;  // wakes the set-up thread
   bool stop = false;
   std::deque<std::unique_ptr<Request>> queue;            // submitted, not admitted
+  std::deque<std::unique_ptr<Request>> to_build;         // admitted, handle not built yet
+  std::deque<std::unique_ptr<Request>> built;            // handle built, not yet stepped
+  std::deque<Slot> to_release;                           // finished, handle to destroy
   std::map<uint64_t, std::unique_ptr<Request>> done;     // finished, result not taken
   std::deque<uint64_t> unreported;                       // finished, not yet polled
   std::map<uint64_t, int> ids;                           // every id in use
   std::vector<std::unique_ptr<Request>> active;          // worker-owned
-  std::thread worker;
+  std::thread worker, prep;
 
   void run();
-  void admit(Request* r);
+  void run_prep();
+  void build(Request* r);
   void finish(std::unique_ptr<Request> r);
+  void publish(std::unique_ptr<Request> r);  // with mu held
   bool advance(Request* r);  // true when the request is finished
 };
 
 namespace {
 
-void release_slot(Request* r) {
-  if (r->task) emu::task_delete(r->task);
-  r->task = nullptr;
-  if (r->h) emu_destroy(r->h);  // waits for the handle's stream
+Slot take_slot(Request* r) {
+  Slot s;
+  s.h = r->h;
+  s.st = r->st;
+  s.task = r->task;
+  s.bytes = r->stats.device_bytes;
   r->h = nullptr;
-  if (r->st) cudaStreamDestroy(r->st);
   r->st = nullptr;
+  r->task = nullptr;
+  return s;
 }
+
+void release_slot(Slot& s) {
+  if (s.task) emu::task_delete(s.task);
+  s.task = nullptr;
+  if (s.h) emu_destroy(s.h);  // waits for the handle's stream
+  s.h = nullptr;
+  if (s.st) cudaStreamDestroy(s.st);
+  s.st = nullptr;
+}
+
+// Stream-ordered device memory for the requests' handles when the caller
+// gives no allocator: allocation and release are enqueued on the handle's
+// stream, so building or destroying one request's handle never waits for
+// the device work of the others.
+void* async_alloc(void*, size_t bytes, void* stream) {
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, (cudaStream_t)stream) != cudaSuccess) return nullptr;
+  return p;
+}
+void async_free(void*, void* p, size_t, void* stream) { cudaFreeAsync(p, (cudaStream_t)stream); }
 
 }  // namespace
 
-void emu_server::admit(Request* r) {
+// Set-up of an admitted request (on the set-up thread): its stream, handle
+// (emu_create), first activation and solve task.
+void emu_server::build(Request* r) {
   r->t_admit = clk::now();
   r->stats.queue_ms = ms_between(r->t_submit, r->t_admit);
   int rc = EMU_OK;
@@ -115,7 +167,7 @@ void emu_server::admit(Request* r) {
   }
   if (rc == EMU_OK) {
     emu_mesh_desc d = r->desc();
-    rc = emu_create(&d, &prm, has_alloc ? &alloc : nullptr, r->st, &r->h);
+    rc = emu_create(&d, &prm, &alloc, r->st, &r->h);
   }
   r->t_ready = clk::now();
   r->stats.setup_ms = ms_between(r->t_admit, r->t_ready);
@@ -124,12 +176,8 @@ void emu_server::admit(Request* r) {
     r->task = emu::task_new(r->h, &r->fstats);
     if (!r->task) rc = EMU_ERR_OOM;
   }
-  if (rc != EMU_OK) {
-    r->stats.status = rc;
-    return;
-  }
   r->frame = 0;
-  r->waiting = emu::task_step(r->task) != 0;
+  if (rc != EMU_OK) r->stats.status = rc;
 }
 
 // Steps the request's task if its device work is done; on a finished frame
@@ -172,40 +220,65 @@ bool emu_server::advance(Request* r) {
   return false;
 }
 
-void emu_server::finish(std::unique_ptr<Request> r) {
-  const clk::time_point t = clk::now();
-  r->stats.solve_ms = ms_between(r->t_ready, t);
-  r->stats.latency_ms = ms_between(r->t_submit, t);
-  release_slot(r.get());
+void emu_server::publish(std::unique_ptr<Request> r) {
   r->acts.clear();
   r->acts.shrink_to_fit();
-  std::lock_guard<std::mutex> lk(mu);
-  used -= (size_t)r->stats.device_bytes;
   unreported.push_back(r->id);
   done[r->id] = std::move(r);
 }
 
+// A finished request (worker thread): its result is published at once, its
+// handle goes to the set-up thread for release (budget and slot are freed
+// there, after the release).
+void emu_server::finish(std::unique_ptr<Request> r) {
+  const clk::time_point t = clk::now();
+  r->stats.solve_ms = ms_between(r->t_ready, t);
+  r->stats.latency_ms = ms_between(r->t_submit, t);
+  Slot s = take_slot(r.get());
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    publish(std::move(r));
+    to_release.push_back(s);
+  }
+  prep_cv.notify_one();
+}
+
+// Worker: admission by budget and slot count, then it only steps the active
+// requests' solve tasks; building and destroying handles (emu_create's
+// set-up of the basis, emu_destroy's release) run on the set-up thread, so
+// requests in flight keep advancing meanwhile.
 void emu_server::run() {
   cudaSetDevice(device);
   for (;;) {
-    std::vector<std::unique_ptr<Request>> admitted;
+    std::vector<std::unique_ptr<Request>> ready;
+    bool admitted = false;
     {
       std::unique_lock<std::mutex> lk(mu);
-      if (active.empty()) cv.wait(lk, [&] { return stop || !queue.empty(); });
+      auto can_admit = [&] {
+        return !queue.empty() && inflight < (int)kMaxActive &&
+               used + (size_t)queue.front()->stats.device_bytes <= budget;
+      };
+      if (active.empty()) cv.wait(lk, [&] { return stop || !built.empty() || can_admit(); });
       if (stop) break;
       // admission in arrival order while memory and a slot are free
-      while (!queue.empty() && active.size() + admitted.size() < kMaxActive &&
-             used + (size_t)queue.front()->stats.device_bytes <= budget) {
+      while (can_admit()) {
         used += (size_t)queue.front()->stats.device_bytes;
-        admitted.push_back(std::move(queue.front()));
+        ++inflight;
+        to_build.push_back(std::move(queue.front()));
         queue.pop_front();
+        admitted = true;
+      }
+      while (!built.empty()) {
+        ready.push_back(std::move(built.front()));
+        built.pop_front();
       }
     }
-    for (auto& r : admitted) {
-      admit(r.get());
+    if (admitted) prep_cv.notify_one();
+    bool progressed = admitted || !ready.empty();
+    for (auto& r : ready) {
+      r->waiting = emu::task_step(r->task) != 0;
       active.push_back(std::move(r));
     }
-    bool progressed = !admitted.empty();
     for (size_t k = 0; k < active.size();) {
       Request* r = active[k].get();
       const bool was_waiting = r->waiting;
@@ -220,8 +293,60 @@ void emu_server::run() {
     }
     if (!progressed) std::this_thread::yield();
   }
-  for (auto& r : active) release_slot(r.get());
+  for (auto& r : active) {
+    Slot s = take_slot(r.get());
+    release_slot(s);
+  }
   active.clear();
+}
+
+// Set-up thread: builds admitted requests' handles and releases finished
+// ones (releases first, so memory returns to the budget as early as possible).
+void emu_server::run_prep() {
+  cudaSetDevice(device);
+  for (;;) {
+    std::unique_ptr<Request> job;
+    Slot rel;
+    bool has_rel = false;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      prep_cv.wait(lk, [&] { return stop || !to_build.empty() || !to_release.empty(); });
+      if (!to_release.empty()) {
+        rel = to_release.front();
+        to_release.pop_front();
+        has_rel = true;
+      } else if (stop) {
+        break;
+      } else {
+        job = std::move(to_build.front());
+        to_build.pop_front();
+      }
+    }
+    if (has_rel) {
+      release_slot(rel);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        used -= (size_t)rel.bytes;
+        --inflight;
+      }
+      cv.notify_one();
+      continue;
+    }
+    build(job.get());
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (job->stats.status != EMU_OK) {  // set-up failed: the request ends here
+        Slot s = take_slot(job.get());
+        const clk::time_point t = clk::now();
+        job->stats.latency_ms = ms_between(job->t_submit, t);
+        publish(std::move(job));
+        to_release.push_back(s);
+      } else {
+        built.push_back(std::move(job));
+      }
+    }
+    cv.notify_one();
+  }
 }
 
 extern "C" {
@@ -241,6 +366,10 @@ int emu_server_create(size_t budget_bytes, const emu_params* params, const emu_a
   if (alloc && alloc->alloc && alloc->free) {
     s->alloc = *alloc;
     s->has_alloc = true;
+  } else {
+    s->alloc.ctx = nullptr;
+    s->alloc.alloc = async_alloc;
+    s->alloc.free = async_free;
   }
   s->budget = budget_bytes;
   if (cudaGetDevice(&s->device) != cudaSuccess) {
@@ -249,8 +378,17 @@ int emu_server_create(size_t budget_bytes, const emu_params* params, const emu_a
     return EMU_ERR_CUDA;
   }
   try {
+    s->prep = std::thread([s] { s->run_prep(); });
     s->worker = std::thread([s] { s->run(); });
   } catch (...) {
+    if (s->prep.joinable()) {
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+      }
+      s->prep_cv.notify_all();
+      s->prep.join();
+    }
     delete s;
     emu::set_last_error("emu_server_create: cannot start the worker thread");
     return EMU_ERR_OOM;
@@ -296,6 +434,17 @@ int emu_server_submit(emu_server* srv, const emu_mesh_desc* mesh, const double* 
     r->fixed_verts.assign(mesh->fixed_verts, mesh->fixed_verts + mesh->n_fixed);
     r->has_fixed_pos = mesh->fixed_pos != nullptr;
     if (r->has_fixed_pos) r->fixed_pos.assign(mesh->fixed_pos, mesh->fixed_pos + 3 * mesh->n_fixed);
+    r->has_bones = mesh->bone_id != nullptr;
+    if (r->has_bones) r->bone_id.assign(mesh->bone_id, mesh->bone_id + m);
+    r->n_joints = mesh->n_joints;
+    if (r->n_joints > 0) {
+      const int32_t j = r->n_joints;
+      r->joint_type.assign(mesh->joint_type, mesh->joint_type + j);
+      r->joint_bones.assign(mesh->joint_bones, mesh->joint_bones + 2 * j);
+      r->joint_point.assign(mesh->joint_point, mesh->joint_point + 3 * j);
+      r->joint_axis.assign(mesh->joint_axis, mesh->joint_axis + 3 * j);
+      r->joint_half_length.assign(mesh->joint_half_length, mesh->joint_half_length + j);
+    }
     r->acts.assign(activations, activations + (size_t)n_frames * m);
     r->positions.assign((size_t)n_frames * 3 * n, 0.0);
   } catch (...) {
@@ -368,7 +517,15 @@ int emu_server_destroy(emu_server* srv) {
     srv->stop = true;
   }
   srv->cv.notify_all();
+  srv->prep_cv.notify_all();
   if (srv->worker.joinable()) srv->worker.join();
+  if (srv->prep.joinable()) srv->prep.join();
+  // handles built or finished but not yet released
+  for (auto& s : srv->to_release) release_slot(s);
+  for (auto& r : srv->built) {
+    Slot s = take_slot(r.get());
+    release_slot(s);
+  }
   delete srv;
   return EMU_OK;
 }

@@ -112,3 +112,59 @@ def test_admission_waits_for_memory_and_rejects_a_mesh_over_budget(emu):
             srv.submit(big, np.full((1, big.tets.shape[0]), 0.5), 3)
     finally:
         srv.close()
+
+
+def test_requests_arriving_mid_flight_overlap_and_each_matches_its_solo_run(emu):
+    # continuous batching: requests submitted while others are being solved
+    # (and while others are being set up) are admitted and run concurrently;
+    # each result is bit-identical to the same request served alone, and the
+    # whole mix takes clearly less than the requests one after another
+    p = emu.Params(tol_rel_residual=1e-6, precision=emu.PRECISION_MIXED)
+    reqs = _requests()
+    srv = emu.Server(64 << 30, p)
+    try:
+        solo_q, solo_s = [], []
+        for k, (mesh, acts) in enumerate(reqs):
+            t0 = time.time()
+            srv.submit(mesh, acts, 1000 + k)
+            q, st = _wait(srv, [1000 + k])[1000 + k]
+            solo_s.append(time.time() - t0)
+            assert st.status == 0
+            solo_q.append(q)
+        t0 = time.time()
+        srv.submit(reqs[3][0], reqs[3][1], 3)  # the largest first
+        srv.submit(reqs[1][0], reqs[1][1], 1)
+        time.sleep(0.05)  # the rest arrive while those two are in flight
+        for k in (0, 2, 4):
+            srv.submit(reqs[k][0], reqs[k][1], k)
+        res = _wait(srv, list(range(len(reqs))))
+        makespan = time.time() - t0
+        for k in range(len(reqs)):
+            q, st = res[k]
+            assert st.status == 0 and st.frames_done == reqs[k][1].shape[0]
+            assert np.array_equal(q, solo_q[k]), k
+        assert makespan < 0.8 * sum(solo_s), (makespan, solo_s)
+    finally:
+        srv.close()
+
+
+def test_a_request_with_bones_and_a_hinge_is_served_like_a_plain_solve(emu):
+    from emu_inputs import arm_assembly
+
+    arm = arm_assembly(bone_w=2, bone_len=4, r0=2.0, frames=4)
+    p = emu.Params(tol_rel_residual=1e-6, precision=emu.PRECISION_MIXED)
+    s = emu.Solver(arm, p)
+    ref = []
+    for f in (1, 2):
+        s.set_activation(arm.activations[f])
+        assert s.solve().status == 0
+        ref.append(s.positions())
+    s.close()
+    srv = emu.Server(16 << 30, p)
+    try:
+        srv.submit(arm, arm.activations[1:3], 7)
+        q, st = _wait(srv, [7])[7]
+        assert st.status == 0 and st.frames_done == 2
+        assert np.array_equal(q, np.stack(ref))
+    finally:
+        srv.close()
