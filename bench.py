@@ -123,8 +123,9 @@ def algorithmic_bytes(phase, mixed, m, n, nnz, cg_iters):
 
 
 # per-tet kernels launched per launch of a profiled phase (the update phase
-# also launches the per-vertex position update)
-PER_TET_KERNELS = {"grad": 1.0, "syrk": 1.0, "dir": 1.0, "ls": 1.0, "update": 0.5}
+# also launches the per-vertex position update, the mixed gradient phase the
+# per-vertex split of the displacement)
+PER_TET_KERNELS = {"grad": 0.5, "syrk": 1.0, "dir": 1.0, "ls": 1.0, "update": 0.5}
 
 
 def per_tet_fractions(prof, mixed, m, n, nnz, peak):

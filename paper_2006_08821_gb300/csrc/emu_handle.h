@@ -67,6 +67,7 @@ struct emu_handle {
         *u32 = nullptr, *ka32 = nullptr, *E32 = nullptr, *g32 = nullptr, *dq32 = nullptr, *b32 = nullptr,
         *r32 = nullptr, *e32 = nullptr;
   float4* quat = nullptr;
+  float *uh32 = nullptr, *ul32 = nullptr;  // q - Q as a float pair (hi, lo), 3n each
   float* E0 = nullptr;     // 9m: G_i Q - I of the FP32 D_m^-1
   double* Qrest = nullptr;  // 3n rest positions
   float *val32 = nullptr, *ldinv32 = nullptr;
@@ -321,6 +322,8 @@ struct emu_handle {
     a.E = E32;
     a.q = q;
     a.Q = Qrest;
+    a.uh = uh32;
+    a.ul = ul32;
     a.E0 = E0;
     a.dq = dq32;
     a.g = g32;

@@ -514,7 +514,8 @@ bool alloc_device(emu_handle* h, int64_t nnz) {
          h->get(h->E32, 6 * m) && h->get(h->g32, 9 * m) && h->get(h->quat, m) && h->get(h->dq32, 3 * n) &&
          h->get(h->b32, 3 * n) && h->get(h->r32, 3 * n) && h->get(h->e32, 3 * n) && h->get(h->fr, 3 * n) &&
          h->get(h->fu, 3 * n) && h->get(h->fw, 3 * n) && h->get(h->fp, 3 * n) && h->get(h->fs, 3 * n) &&
-         h->get(h->E0, 9 * m) && h->get(h->Qrest, 3 * n) && h->get(h->contrib32, 12 * m);
+         h->get(h->E0, 9 * m) && h->get(h->Qrest, 3 * n) && h->get(h->contrib32, 12 * m) &&
+         h->get(h->uh32, 3 * n) && h->get(h->ul32, 3 * n);
   } else
     ok = ok && h->get(h->gam64, 48 * m) && h->get(h->y64, 9 * m) && h->get(h->d64, 9 * m) && h->get(h->Uw64, 54 * m);
   ok = ok && h->get(h->pr, 16 * n) && h->get(h->pu, 16 * n) && h->get(h->pw, 16 * n) && h->get(h->pp, 16 * n) &&
@@ -1034,11 +1035,14 @@ namespace {
 // enqueue the gradient and its reduction, then wait for the scalars
 int enqueue_grad(emu_handle* h) {
   h->ph_begin();
-  if (h->mixed)
+  if (h->mixed) {
+    // the displacement's float pair for this iteration's per-tet kernels
+    launch_split_disp(h->n, h->q, h->Qrest, h->uh32, h->ul32, h->st);
     launch_grad_mixed(h->margs(), h->grid_tet4, h->st);
-  else
+  } else {
     launch_grad<double>(h->args<double>(), h->grid_tet, h->st);
-  h->ph_end(EMU_PHASE_GRAD, 1);
+  }
+  h->ph_end(EMU_PHASE_GRAD, h->mixed ? 2 : 1);
   if (!h->mixed) {  // the mixed gradient kernel reduces ||g||^2 in its last block
     h->ph_begin();
     launch_reduce_grad(h->part_grad, h->grid_tet, h->sc, nullptr, nullptr, h->st);

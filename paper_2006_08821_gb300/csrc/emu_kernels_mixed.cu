@@ -38,17 +38,20 @@ __device__ __forceinline__ ElemMat<float> load_mat_f(const MixArgs& a, int64_t i
   return e;
 }
 
-// A - I = G_i (q - Q) + (G_i Q - I): the displacement edges are formed in
-// FP64 and rounded once, so A - I keeps its relative precision.
-__device__ __forceinline__ void defgrad_disp(const double* __restrict__ q, const double* __restrict__ Q, int4 t,
+// A - I = G_i (q - Q) + (G_i Q - I). The displacement edges come from the
+// float pair uh + ul = q - Q: (uh_k - uh_3) is rounded relative to the edge
+// itself (not to the displacement), and (ul_k - ul_3) restores the part the
+// FP32 rounding of the displacement dropped, so A - I keeps the relative
+// precision the FP64 difference gave, with FP32 arithmetic only.
+__device__ __forceinline__ void defgrad_disp(const float* __restrict__ uh, const float* __restrict__ ul, int4 t,
                                              const float* D, const float* __restrict__ E0, int64_t m, int64_t i,
                                              float* AmI) {
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    const double u3 = q[3 * (int64_t)t.w + r] - Q[3 * (int64_t)t.w + r];
-    const float e0 = (float)((q[3 * (int64_t)t.x + r] - Q[3 * (int64_t)t.x + r]) - u3);
-    const float e1 = (float)((q[3 * (int64_t)t.y + r] - Q[3 * (int64_t)t.y + r]) - u3);
-    const float e2 = (float)((q[3 * (int64_t)t.z + r] - Q[3 * (int64_t)t.z + r]) - u3);
+    const float h3 = uh[3 * (int64_t)t.w + r], l3 = ul[3 * (int64_t)t.w + r];
+    const float e0 = (uh[3 * (int64_t)t.x + r] - h3) + (ul[3 * (int64_t)t.x + r] - l3);
+    const float e1 = (uh[3 * (int64_t)t.y + r] - h3) + (ul[3 * (int64_t)t.y + r] - l3);
+    const float e2 = (uh[3 * (int64_t)t.z + r] - h3) + (ul[3 * (int64_t)t.z + r] - l3);
 #pragma unroll
     for (int c = 0; c < 3; ++c) AmI[3 * r + c] = e0 * D[c] + e1 * D[3 + c] + e2 * D[6 + c] + E0[(3 * r + c) * m + i];
   }
@@ -58,7 +61,7 @@ __device__ __forceinline__ void defgrad_disp(const double* __restrict__ q, const
 __device__ __forceinline__ void mismatch(const MixArgs& a, int4 t, const float* Dm, int64_t i, const float4 qq,
                                          const float* RE, float* Dk) {
   float AmI[9], RmI[9];
-  defgrad_disp(a.q, a.Q, t, Dm, a.E0, a.m, i, AmI);
+  defgrad_disp(a.uh, a.ul, t, Dm, a.E0, a.m, i, AmI);
   quat_rot_minus_I(qq.x, qq.y, qq.z, qq.w, RmI);
 #pragma unroll
   for (int k = 0; k < 9; ++k) Dk[k] = (AmI[k] - RmI[k]) - RE[k];
@@ -107,7 +110,10 @@ __device__ __forceinline__ void corners_f(TO* __restrict__ contrib, int64_t i, f
 // ------------------------------------------------------------ gradient ----
 __global__ void __launch_bounds__(128, 4) k_grad_m(MixArgs a) {
   const int64_t m = a.m;
-  double acc[1] = {0.0};
+  // per-thread sums in FP32 (a few tets each), FP64 from the block sum on:
+  // GB300's FP64 pipe issues far below its FP32 rate, and per-tet FP64
+  // conversions and adds bound these kernels (measured on the line search)
+  float accf = 0.f;
   int bad = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     // tets of bones are no variables of their own (their g, y, U stay zero)
@@ -127,15 +133,15 @@ __global__ void __launch_bounds__(128, 4) k_grad_m(MixArgs a) {
     matmul3(R, Em, RE);
     mismatch(a, t, D, i, a.quat[i], RE, Dk);
     float g[9];
-    double gg = 0.0;
+    float gg = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       g[k] = mat.V * RP[k] - c * Dk[k];
-      gg += (double)g[k] * (double)g[k];
+      gg = fmaf(g[k], g[k], gg);
       a.g[k * m + i] = g[k];
     }
     if (!isfinite(gg)) bad = 1;
-    acc[0] += gg;
+    accf += gg;
     float M6[36], U[54];
     stretch_hessian(st.Sinv, st.lnJ, mat, M6);
     bool ok = true;
@@ -148,6 +154,7 @@ __global__ void __launch_bounds__(128, 4) k_grad_m(MixArgs a) {
 #pragma unroll
     for (int k = 0; k < 54; ++k) a.Uw[k * m + i] = U[k];
   }
+  double acc[1] = {(double)accf};
   block_reduce_write<1>(acc, a.partials + blockIdx.x);
   if (bad) atomicExch(&a.sc->nonfinite, 1);
   // the last block to finish sums the squared gradient norm
@@ -412,7 +419,7 @@ __global__ void __launch_bounds__(128, 8) k_dir_m(MixArgs a) {
   if (threadIdx.x < kK) sz[threadIdx.x] = (float)a.z[threadIdx.x];
   __syncthreads();
   const int64_t m = a.m;
-  double acc[1] = {0.0};
+  float accf = 0.f;  // per-thread g . d in FP32, FP64 from the block sum on
   const float* __restrict__ Uw = a.Uw;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     if (a.tkind) {
@@ -463,18 +470,19 @@ __global__ void __launch_bounds__(128, 8) k_dir_m(MixArgs a) {
       v[c] -= acc_c;
     }
     float dv[9];
-    double gtd = 0.0;
+    float gtd = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       dv[k] = -(a.y[k * m + i] + v[k]);
       a.d[k * m + i] = dv[k];
-      gtd += (double)a.g[k * m + i] * (double)dv[k];
+      gtd = fmaf(a.g[k * m + i], dv[k], gtd);
     }
-    acc[0] += gtd;
+    accf += gtd;
     float D[9];
     load9f(a.Dinv, m, i, D);
     corners_f(a.contrib32, i, a.w[i], dv, D);
   }
+  double acc[1] = {(double)accf};
   block_reduce_write<1>(acc, a.partials + blockIdx.x);
 }
 
@@ -487,12 +495,13 @@ void launch_dir_mixed(const MixArgs& a, int grid, cudaStream_t st) { k_dir_m<<<g
 //   + lam/2 log1p(x) (2 ln J + log1p(x)) + ka (2 s (Fu).(du) + s^2 |du|^2),
 // with F - F^-T = R (2E + E^2) S^-1; plus the ACAP coefficients.
 __global__ void __launch_bounds__(128) k_ls_m(MixArgs a, LsSelect sel) {
-  const double rho = sel.rho;
+  const float rho = (float)sel.rho;
   const int64_t m = a.m;
-  const double s0 = a.sc->sigma_start;
-  double acc[kLsNV];
+  const float s0 = (float)a.sc->sigma_start;
+  // per-thread sums in FP32 (a few tets each), FP64 from the block sum on
+  float accf[kLsNV];
 #pragma unroll
-  for (int k = 0; k < kLsNV; ++k) acc[k] = 0.0;
+  for (int k = 0; k < kLsNV; ++k) accf[k] = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     // free bones' tets: their terms come from the FP64 bone kernel (a stiff
     // bone's energy change is beyond FP32); pinned bones' tets contribute 0
@@ -517,8 +526,8 @@ __global__ void __launch_bounds__(128) k_ls_m(MixArgs a, LsSelect sel) {
       cDd += Dm[k] * dDk;
       cdd += dDk * dDk;
     }
-    acc[kLsTrials] += (double)(c * cDd);
-    acc[kLsTrials + 1] += (double)(c * cdd);
+    accf[kLsTrials] += c * cDd;
+    accf[kLsTrials + 1] += c * cdd;
     const ElemMat<float> md = load_mat_f(a, i);
     float Rtd[9], M[9], F[9];
     matTmul3(R, d, Rtd);
@@ -541,25 +550,28 @@ __global__ void __launch_bounds__(128) k_ls_m(MixArgs a, LsSelect sel) {
     }
     const float Fudu = Fu[0] * du[0] + Fu[1] * du[1] + Fu[2] * du[2];
     const float dudu = du[0] * du[0] + du[1] * du[1] + du[2] * du[2];
-    float sig = (float)s0;
+    float sig = s0;
 #pragma unroll
     for (int j = 0; j < kLsTrials; ++j) {
       const float x = sig * trM + sig * sig * e2 + sig * sig * sig * detM;
-      double dpsi;
+      float dpsi;
       if (x > -1.f) {
         const float dl = log1pf(x);
         const float nh = md.mu * (sig * FFd + 0.5f * sig * sig * dd - sig * sig * e2 - sig * sig * sig * detM +
                                   x_minus_log1p(x));
         const float vol = 0.5f * md.lam * dl * (2.f * st.lnJ + dl);
         const float fib = md.ka * (2.f * sig * Fudu + sig * sig * dudu);
-        dpsi = (double)(md.V * (nh + vol + fib));
+        dpsi = md.V * (nh + vol + fib);
       } else {
-        dpsi = 1e300;
+        dpsi = INFINITY;  // an inverted trial: never accepted
       }
-      acc[j] += dpsi;
-      sig *= (float)rho;
+      accf[j] += dpsi;
+      sig *= rho;
     }
   }
+  double acc[kLsNV];
+#pragma unroll
+  for (int k = 0; k < kLsNV; ++k) acc[k] = (double)accf[k];
   block_reduce_write<kLsNV>(acc, a.partials + (size_t)blockIdx.x * kLsNV);
   // the last block to finish sums every block's partials and selects the step
   if (last_block(&a.sc->ticket[kTicketLs])) {
@@ -608,6 +620,23 @@ __global__ void __launch_bounds__(256) k_update_verts_f(int64_t n3, const DevSca
   if (sig == 0.0) return;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x)
     q[k] += sig * (double)dq[k];
+}
+
+__global__ void __launch_bounds__(256) k_split_disp(int64_t n3, const double* __restrict__ q, const double* __restrict__ Q,
+                                                    float* __restrict__ uh, float* __restrict__ ul) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x) {
+    const double u = q[k] - Q[k];
+    const float hi = (float)u;
+    uh[k] = hi;
+    ul[k] = (float)(u - (double)hi);
+  }
+}
+
+void launch_split_disp(int64_t n, const double* q, const double* Q, float* uh, float* ul, cudaStream_t st) {
+  const int64_t n3 = 3 * n;
+  int grid = (int)((n3 + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_split_disp<<<grid, 256, 0, st>>>(n3, q, Q, uh, ul);
 }
 
 void launch_update_verts_f(int64_t n, const DevScalars* sc, const float* dq, double* q, cudaStream_t st) {

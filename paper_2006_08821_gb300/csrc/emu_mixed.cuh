@@ -28,6 +28,11 @@ struct MixArgs {
   float* E;            // 6m stretch coordinates of S - I
   const double* q;     // 3n
   const double* Q;     // 3n rest positions
+  // displacement q - Q as an unevaluated float pair (hi + lo, 3n each),
+  // refreshed from q before every gradient: the per-tet kernels form the
+  // edges of G_i (q - Q) in FP32 from it without losing the FP64 difference
+  const float* uh;
+  const float* ul;
   const float* E0;     // 9m: G_i Q - I (rounding of the FP32 D_m^-1, static)
   const float* dq;     // 3n
   float* g;            // 9m
@@ -72,6 +77,9 @@ constexpr int kTcBlocksPerSM = 2;
 // Per-device kernel attributes of the TC SYRK (before its first launch).
 cudaError_t prepare_syrk_tc();
 void launch_update_verts_f(int64_t n, const DevScalars* sc, const float* dq, double* q, cudaStream_t st);
+// uh + ul = q - Q: hi = the FP32 rounding of the FP64 difference, lo = the
+// FP32 rounding of what hi leaves over.
+void launch_split_disp(int64_t n, const double* q, const double* Q, float* uh, float* ul, cudaStream_t st);
 void launch_assemble_f(int64_t n, const int32_t* slot_ptr, const int32_t* slot_idx, const float* contrib32,
                        const uint8_t* is_fixed, float* b, cudaStream_t st);
 // state conversion: (quat, E) <-> (R 9m, s 6m) FP64 structure of arrays
