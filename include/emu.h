@@ -148,12 +148,13 @@ typedef struct {
  *                   MIXED is for tol_rel_residual >= 1e-6 or so: its FP32
  *                   rounding floor can lie above a tighter tolerance, and a
  *                   solve then runs to max_newton; use FP64 there.
- *   mode_iters      subspace iterations used to build the low-rank basis.
+ *   mode_iters      subspace iterations used to build the low-rank basis
+ *                   (default 8).
  *   seed            seeds the random start of the subspace iteration.
  *   dq_tol          relative residual of the per-iteration solve for the
  *                   change of q along the search direction (q*(F + s d) =
  *                   q + s dq, q* being affine); q itself is then updated by
- *                   linearity (default 5e-2). After a line search fails,
+ *                   linearity (default 8e-2). After a line search fails,
  *                   q is re-solved and dq is solved to the exact-solve
  *                   tolerance for the rest of the call.
  *   q_refresh       every q_refresh iterations, and before convergence is
@@ -266,9 +267,9 @@ int emu_required_bytes(const emu_mesh_desc* desc, const emu_params* params, size
  * fits in the budget and fewer than 32 are in flight, and interleaves the
  * active requests' Newton loops, each on its own stream, so that their work
  * overlaps on the device (continuous batching: a request that arrives while
- * others run is admitted as soon as memory and a slot free up). A second
- * thread builds each admitted request's handle (emu_create, including the
- * low-rank basis) and destroys finished ones, so requests in flight keep
+ * others run is admitted as soon as memory and a slot free up). Four
+ * set-up threads build admitted requests' handles (emu_create, including the
+ * low-rank basis) and destroy finished ones, so requests in flight keep
  * advancing while others are set up or released. Without an allocator the
  * handles' memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
  * request's stream). A request's memory returns to the budget once its
@@ -313,7 +314,7 @@ int emu_server_poll(emu_server* srv, uint64_t* done_ids, int32_t cap, int32_t* n
  * not finished. */
 int emu_server_result(emu_server* srv, uint64_t request_id, double* positions, emu_request_stats* stats);
 
-/* Stops both threads: device work already enqueued is waited for, requests
+/* Stops the threads: device work already enqueued is waited for, requests
  * not finished are dropped, and everything is freed. */
 int emu_server_destroy(emu_server* srv);
 

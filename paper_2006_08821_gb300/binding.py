@@ -211,9 +211,9 @@ class Params:
     pcg_tol: float = 1e-8
     pcg_max: int = 5000
     precision: int = PRECISION_FP64
-    mode_iters: int = 4
+    mode_iters: int = 8
     seed: int = 12345
-    dq_tol: float = 5e-2
+    dq_tol: float = 8e-2
     q_refresh: int = 32
     eps_bone: float = -1e-3
     eps_joint: float = -1e-4

@@ -609,8 +609,8 @@ void emu_default_params(emu_params* p) {
   p->pcg_tol = 1e-8;
   p->pcg_max = 5000;
   p->precision = EMU_PRECISION_FP64;
-  p->mode_iters = 4;
-  p->dq_tol = 5e-2;
+  p->mode_iters = 8;
+  p->dq_tol = 8e-2;
   p->q_refresh = 32;
   p->seed = 12345;
   p->eps_bone = -1e-3;

@@ -11,6 +11,8 @@
 //   * the polar update works on I + Y with the rotation kept as a quaternion
 //     and R - I written without cancellation.
 #include <cuda_runtime.h>
+
+#include <mutex>
 #include <math.h>
 #include <stdint.h>
 
@@ -391,6 +393,8 @@ __global__ void __launch_bounds__(256, kTcBlocksPerSM) k_syrk_tc(MixArgs a, doub
 // (once per device; call outside stream capture).
 cudaError_t prepare_syrk_tc() {
   static bool attr_set[64] = {false};
+  static std::mutex mu;  // handles may be built from several threads
+  std::lock_guard<std::mutex> lock(mu);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

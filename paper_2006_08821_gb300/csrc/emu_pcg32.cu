@@ -17,6 +17,8 @@
 // pcg32p_kernel below is the pipelined variant with one.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include <algorithm>
 #include <stdint.h>
 
@@ -798,6 +800,8 @@ cudaError_t prepare32() {
   const size_t smem = C ? sizeof(float4) * (kModes / 4) * RPT * NT : 0;
   if (smem <= 48 * 1024) return cudaSuccess;
   static bool set[64] = {false};
+  static std::mutex mu;  // handles may be built from several threads
+  std::lock_guard<std::mutex> lock(mu);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -842,6 +846,8 @@ constexpr size_t pipe_smem() {
 template <int RPT>
 cudaError_t prepare32p() {
   static bool set[64] = {false};
+  static std::mutex mu;  // handles may be built from several threads
+  std::lock_guard<std::mutex> lock(mu);
   if (pipe_smem<RPT>() <= 48 * 1024) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

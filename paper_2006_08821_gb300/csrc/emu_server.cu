@@ -23,6 +23,7 @@ namespace {
 
 using clk = std::chrono::steady_clock;
 constexpr size_t kMaxActive = 32;
+constexpr int kPrepThreads = 4;  // handles built (and released) concurrently
 
 double ms_between(clk::time_point a, clk::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
@@ -109,7 +110,8 @@ struct emu_server {
   std::deque<uint64_t> unreported;                       // finished, not yet polled
   std::map<uint64_t, int> ids;                           // every id in use
   std::vector<std::unique_ptr<Request>> active;          // worker-owned
-  std::thread worker, prep;
+  std::thread worker;
+  std::vector<std::thread> prep;  // set-up threads
 
   void run();
   void run_prep();
@@ -378,17 +380,16 @@ int emu_server_create(size_t budget_bytes, const emu_params* params, const emu_a
     return EMU_ERR_CUDA;
   }
   try {
-    s->prep = std::thread([s] { s->run_prep(); });
+    for (int k = 0; k < kPrepThreads; ++k) s->prep.emplace_back([s] { s->run_prep(); });
     s->worker = std::thread([s] { s->run(); });
   } catch (...) {
-    if (s->prep.joinable()) {
-      {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->stop = true;
-      }
-      s->prep_cv.notify_all();
-      s->prep.join();
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stop = true;
     }
+    s->prep_cv.notify_all();
+    for (auto& t : s->prep)
+      if (t.joinable()) t.join();
     delete s;
     emu::set_last_error("emu_server_create: cannot start the worker thread");
     return EMU_ERR_OOM;
@@ -519,7 +520,8 @@ int emu_server_destroy(emu_server* srv) {
   srv->cv.notify_all();
   srv->prep_cv.notify_all();
   if (srv->worker.joinable()) srv->worker.join();
-  if (srv->prep.joinable()) srv->prep.join();
+  for (auto& t : srv->prep)
+    if (t.joinable()) t.join();
   // handles built or finished but not yet released
   for (auto& s : srv->to_release) release_slot(s);
   for (auto& r : srv->built) {

@@ -166,7 +166,8 @@ def test_only_a_pinned_bone(emu, arm):
     bid[bid == 1] = -1
     mesh = dataclasses.replace(arm, bone_id=bid, material_id=mat, joints=None)
     r = _oracle_solve(BoneOracle(mesh, PRM), mesh.activations[2])
-    s, st = _gpu(emu, mesh, mesh.activations[2])
+    # no free bone: no bone term in the line search, the floor lies lower
+    s, st = _gpu(emu, mesh, mesh.activations[2], tol=1e-11)
     assert st.status == 0
     err = np.abs(s.positions() - r.q).max() / _diag(mesh)
     assert err <= 1e-9, err
