@@ -47,7 +47,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from emu_inputs import batch_set, box_beam, mtu_for_tet_count, muscle_tendon_unit, request_stream  # noqa: E402
+from emu_inputs import arm_assembly, batch_set, box_beam, mtu_for_tet_count, muscle_tendon_unit, request_stream  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -91,6 +91,15 @@ def make_workload(name):
     if name == "mtu_small":
         mesh = muscle_tendon_unit(8, 8, 32, h=0.01, radius_cells=12.9 / 4, frames=60)
         return mesh, f"muscle-tendon unit 8x8x32 ({mesh.n_tets} tets), 60-frame ramp, rel residual 1e-6"
+    if name == "arm":
+        # the arm-like assembly at the largest size the method converges on
+        # within the Newton cap (the 799,152-tet default does not, in the
+        # oracle either; see the design notes)
+        mesh = arm_assembly(bone_w=6, bone_len=24, r0=10.0, frames=120)
+        desc = (f"arm-like assembly: two box bones (E=1e10, 6x6x24 cells each, bone 1 pinned), hinge joint, "
+                f"fusiform muscle and tendon bars, {mesh.n_tets} tets, {mesh.n_verts} verts, "
+                f"120-frame activation sin^2 ramp, warm starts, rel residual 1e-6, final solve with affine bones")
+        return mesh, desc
     raise ValueError(name)
 
 
@@ -270,27 +279,41 @@ def threads_used(cpu_s, wall_s):
     return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
 
 
+def oracle_sample(workload_name):
+    """The CPU sample of a workload: (mesh, description, oracle, solve) with
+    solve(oracle, activation, previous F or None, tol, max_newton)."""
+    from oracle import EmuOracle, OracleParams
+
+    prm = OracleParams(alpha_rel=1.0, weight_mode=0)
+    if workload_name == "arm":
+        from oracle.bones import BoneOracle
+
+        mesh = arm_assembly(bone_w=3, bone_len=8, r0=3.0, frames=120)
+        sample = f"arm-like assembly 3x3x8-cell bones ({mesh.n_tets} tets, same construction), warm-started frames"
+        return mesh, sample, BoneOracle(mesh, prm), \
+            lambda o, a, F, tol, mx: o.solve(a, X0=F, tol=tol, max_newton=mx)
+    if workload_name in ("mtu", "mtu_small", "serve"):
+        mesh = muscle_tendon_unit(8, 8, 32, h=0.01, radius_cells=12.9 / 4, frames=60)
+        sample = f"muscle-tendon unit 8x8x32 grid ({mesh.n_tets} tets, same construction), warm-started ramp frames"
+    else:
+        mesh = box_beam(4, 4, 16, activation=np.linspace(0.0, 0.5, 12))
+        sample = "box beam 4x4x16, ramp frames"
+    return mesh, sample, EmuOracle(mesh, prm), lambda o, a, F, tol, mx: o.solve(a, F0=F, tol=tol, max_newton=mx)
+
+
 def cpu_baseline(workload_name, budget_s=15.0, ref_tol=1e-10):
     """FP64 oracle on a bounded sample of the workload (tet-iters/s).
 
     Returns the baseline entry and, for the parity figure of the line, the
     sample mesh, the frames it solved and the oracle's positions of the last
     of them re-converged (untimed) to ``ref_tol`` from its own state."""
-    from oracle import EmuOracle, OracleParams
-
-    if workload_name in ("mtu", "mtu_small"):
-        mesh = muscle_tendon_unit(8, 8, 32, h=0.01, radius_cells=12.9 / 4, frames=60)
-        sample = f"muscle-tendon unit 8x8x32 grid ({mesh.n_tets} tets, same construction), warm-started ramp frames"
-    else:
-        mesh = box_beam(4, 4, 16, activation=np.linspace(0.0, 0.5, 6))
-        sample = "box beam 4x4x16, ramp frames"
-    o = EmuOracle(mesh, OracleParams(alpha_rel=1.0, weight_mode=0))
+    mesh, sample, o, solve = oracle_sample(workload_name)
     F = None
     t0, c0 = time.perf_counter(), time.process_time()
     tets_iters = 0
     frames = 0
     for f in range(1, mesh.activations.shape[0]):
-        r = o.solve(mesh.activations[f], F0=F, tol=1e-6, max_newton=5000)
+        r = solve(o, mesh.activations[f], F, 1e-6, 5000)
         F = r.F
         tets_iters += mesh.n_tets * r.iterations
         frames += 1
@@ -298,11 +321,24 @@ def cpu_baseline(workload_name, budget_s=15.0, ref_tol=1e-10):
             break
     dt = time.perf_counter() - t0
     cores = threads_used(time.process_time() - c0, dt)
-    ref = o.solve(mesh.activations[frames], F0=F, tol=ref_tol, max_newton=20000)
-    cb = {"value": tets_iters / dt, "unit": "tet-iters/s", "cores": cores, "kind": "oracle",
-          "sample": f"{sample}; frames 1..{frames} ({tets_iters} tet-iters, {dt:.1f} s; "
-                    f"{os.cpu_count()} host cores, {cores} busy on average)"}
+    ref = None
+    for tol in (ref_tol, 3 * ref_tol, 10 * ref_tol):  # a stiff assembly's FP64 floor can lie above ref_tol
+        try:
+            ref = solve(o, mesh.activations[frames], F, tol, 20000)
+            ref_tol = tol
+            break
+        except RuntimeError:
+            continue
+    if ref is None:
+        return cb_entry(tets_iters, dt, cores, sample, frames), None
+    cb = cb_entry(tets_iters, dt, cores, sample, frames)
     return cb, {"mesh": mesh, "frames": frames, "q_ref": ref.q, "ref_tol": ref_tol, "sample": sample}
+
+
+def cb_entry(tets_iters, dt, cores, sample, frames):
+    return {"value": tets_iters / dt, "unit": "tet-iters/s", "cores": cores, "kind": "oracle",
+            "sample": f"{sample}; frames 1..{frames} ({tets_iters} tet-iters, {dt:.1f} s; "
+                      f"{os.cpu_count()} host cores, {cores} busy on average)"}
 
 
 def error_vs_oracle(emu, params, ref):
@@ -346,31 +382,23 @@ def run_reference(args, rank, world):
     6,080 tets for the muscle-tendon unit); W untimed frames, then K timed."""
     if rank != 0:
         return
-    from oracle import EmuOracle, OracleParams
-
     if args.workload == "batch":
         return run_reference_batch(args)
-    if args.workload in ("mtu", "mtu_small", "serve"):
-        mesh = muscle_tendon_unit(8, 8, 32, h=0.01, radius_cells=12.9 / 4, frames=60)
-        sample = f"muscle-tendon unit 8x8x32 ({mesh.n_tets} tets, same construction), warm-started ramp frames"
-    else:
-        mesh = box_beam(4, 4, 16, activation=np.linspace(0.0, 0.5, 12))
-        sample = "box beam 4x4x16, ramp frames"
+    mesh, sample, o, solve = oracle_sample(args.workload)
     if args.workload == "serve":
         desc = serve_desc(args, args.requests)
     else:
         _, desc = make_workload(args.workload)
-    o = EmuOracle(mesh, OracleParams(alpha_rel=1.0, weight_mode=0))
     nf = mesh.activations.shape[0]
     F = None
     f = 1
     for _ in range(args.warmup):
-        r = o.solve(mesh.activations[f], F0=F, tol=args.tol, max_newton=5000)
+        r = solve(o, mesh.activations[f], F, args.tol, 5000)
         F, f = r.F, f % (nf - 1) + 1
     t0, c0 = time.perf_counter(), time.process_time()
     tet_iters = 0
     for _ in range(args.steps):
-        r = o.solve(mesh.activations[f], F0=F, tol=args.tol, max_newton=5000)
+        r = solve(o, mesh.activations[f], F, args.tol, 5000)
         F, f = r.F, f % (nf - 1) + 1
         tet_iters += mesh.n_tets * r.iterations
     dt = time.perf_counter() - t0
@@ -591,7 +619,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mtu", choices=["mtu", "box", "mtu_small", "batch", "serve"])
+    ap.add_argument("--workload", default="mtu", choices=["mtu", "box", "mtu_small", "arm", "batch", "serve"])
     ap.add_argument("--meshes", type=int, default=256, help="batch: number of meshes")
     ap.add_argument("--requests", type=int, default=24, help="serve: requests taken from the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (1/s)")

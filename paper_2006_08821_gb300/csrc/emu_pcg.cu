@@ -421,8 +421,11 @@ int pcg_max_grid(int nrhs, int64_t n) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel<16, double, false>, 256, 0);
   if (occ < 1) return 1;  // cooperative launch needs co-residency; one block always fits
   // One block per SM at most: the barrier and the partial sums cost grow with
-  // the block count, and 256 threads per SM already cover ~500 rows each.
-  int64_t want = (n + 511) / 512;
+  // the block count. At least ~128 rows per block otherwise: FP64 issues at a
+  // small fraction of the FP32 rate on GB300, so a small system spread over
+  // few SMs is bound by their FP64 pipes (measured: 8,640 rows on 17 blocks,
+  // about 140 us per CG iteration).
+  int64_t want = (n + 127) / 128;
   int64_t cap = (int64_t)sms;
   int64_t g = want < cap ? want : cap;
   return (int)(g < 1 ? 1 : g);
