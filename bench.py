@@ -322,7 +322,8 @@ def cpu_baseline(workload_name, budget_s=15.0, ref_tol=1e-10):
     dt = time.perf_counter() - t0
     cores = threads_used(time.process_time() - c0, dt)
     ref = None
-    for tol in (ref_tol, 3 * ref_tol, 10 * ref_tol):  # a stiff assembly's FP64 floor can lie above ref_tol
+    # a stiff assembly's FP64 floor can lie above ref_tol (weak activations)
+    for tol in (ref_tol, 10 * ref_tol, 100 * ref_tol, 1000 * ref_tol):
         try:
             ref = solve(o, mesh.activations[frames], F, tol, 20000)
             ref_tol = tol
