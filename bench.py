@@ -465,10 +465,13 @@ def reduce_over_ranks(dist, maxes, sums, device="cuda"):
 
 def make_params(emu, args, mixed):
     """Solver parameters of a bench leg: tolerance, precision and, with
-    ``--ls-sigma0``, the first line-search trial step (else the library's)."""
+    ``--ls-sigma0`` / ``--cg-degree``, the first line-search trial step and
+    the local preconditioner degree of the dq solves (else the library's)."""
     p = emu.Params(tol_rel_residual=args.tol, precision=emu.PRECISION_MIXED if mixed else emu.PRECISION_FP64)
     if args.ls_sigma0 is not None:
         p.ls_sigma0 = args.ls_sigma0
+    if args.cg_degree is not None:
+        p.cg_local_degree = args.cg_degree
     return p
 
 
@@ -631,6 +634,8 @@ def main():
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--ls-sigma0", type=float, default=None,
                     help="first line-search trial step (default: the library's, 4)")
+    ap.add_argument("--cg-degree", type=int, default=None,
+                    help="degree of the block-local polynomial in the dq solves' preconditioner (default: the library's, 4)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

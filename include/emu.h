@@ -166,7 +166,15 @@ typedef struct {
  *   eps_joint       slack of the joint rows in the final coupling solve
  *                   (Sec. 3.3, < 0; default -1e-4): the joints become the
  *                   penalty Vbar^(1/3) / |eps_joint| |J q|^2 while every
- *                   bone's vertices follow its affine map exactly. */
+ *                   bone's vertices follow its affine map exactly.
+ *   cg_local_degree degree (1..8) of the block-local Chebyshev polynomial in
+ *                   the preconditioner of the mixed path's loose coupling
+ *                   solves (the dq solves): each CUDA block applies it to its
+ *                   own spatially compact part of the ACAP Laplacian of
+ *                   Eq. 4, next to the coarse space on the low-rank basis
+ *                   (a two-level additive Schwarz preconditioner). 1 is plain
+ *                   Jacobi; higher degrees cost more per CG iteration and
+ *                   take fewer iterations (default 4). */
 typedef struct {
   double alpha_rel;
   int32_t weight_mode;
@@ -187,6 +195,7 @@ typedef struct {
   int32_t q_refresh;
   double eps_bone;
   double eps_joint;
+  int32_t cg_local_degree;
 } emu_params;
 
 /* Per-solve statistics. */

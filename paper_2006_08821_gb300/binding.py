@@ -103,6 +103,7 @@ class emu_params(C.Structure):
         ("q_refresh", C.c_int32),
         ("eps_bone", C.c_double),
         ("eps_joint", C.c_double),
+        ("cg_local_degree", C.c_int32),
     ]
 
 
@@ -217,6 +218,7 @@ class Params:
     q_refresh: int = 32
     eps_bone: float = -1e-3
     eps_joint: float = -1e-4
+    cg_local_degree: int = 4
 
     def to_c(self) -> emu_params:
         p = emu_params()

@@ -85,6 +85,13 @@ struct emu_handle {
   float* aphi32 = nullptr;                // rows of L Phi for the pipelined FP32 CG
   bool aphi_ready = false;
   int grid32 = 0, rpt32 = 0;
+  // the partitioned system of the pipelined FP32 CG (emu_cgpart.h)
+  bool cg_part = false;  // built at creation (mixed path, pipelined shape)
+  int32_t *cg_perm = nullptr, *cg_off = nullptr, *cg_rowptr = nullptr, *cg_col = nullptr;
+  float *cg_val = nullptr, *cg_dinv = nullptr, *cg_phi = nullptr, *cg_aphi = nullptr;
+  uint32_t* cg_loc = nullptr;
+  int cg_lw = 0, cg_degree = 1;
+  float cg_c0 = 1.f, cg_c1[kChebMax] = {0}, cg_c2[kChebMax] = {0};
   double q_tol = 1e-8;
   double dq_tol_now = 5e-2;  // dq tolerance of the current solve call
   double dq_tol_base = 0.0;  // tighter dq tolerance a stalled solve settled on (0: params.dq_tol)

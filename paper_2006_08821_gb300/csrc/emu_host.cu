@@ -139,6 +139,8 @@ int validate_params(const emu_params* p) {
   if (p->q_refresh < 1) return fail(EMU_ERR_INVALID_ARG, "q_refresh must be >= 1");
   if (!(p->eps_bone < 0.0) || !(p->eps_joint < 0.0) || !std::isfinite(p->eps_bone) || !std::isfinite(p->eps_joint))
     return fail(EMU_ERR_INVALID_ARG, "eps_bone and eps_joint must be negative");
+  if (p->cg_local_degree < 1 || p->cg_local_degree > kChebMax)
+    return fail(EMU_ERR_INVALID_ARG, "cg_local_degree must be in [1, 8]");
   return EMU_OK;
 }
 
@@ -159,8 +161,24 @@ cudaError_t run_pcg32(emu_handle* h, const float* rhs, float* x, double tol) {
     w.ug = h->ug32;
     w.part = h->part32;
     w.sync = h->sync32;
-    if (tol >= kPipeMinTol && h->aphi_ready && a.phi && pcg32_pipe_ok(h->rpt32)) {
-      w.aphi = h->aphi32;
+    if (tol >= kPipeMinTol && h->aphi_ready && h->cg_part && a.phi && pcg32_pipe_ok(h->rpt32)) {
+      // the partitioned system (b and x stay in vertex order)
+      a.rowptr = h->cg_rowptr;
+      a.col = h->cg_col;
+      a.val = h->cg_val;
+      a.dinv = h->cg_dinv;
+      a.phi = h->cg_phi;
+      w.aphi = h->cg_aphi;
+      w.perm = h->cg_perm;
+      w.off = h->cg_off;
+      w.loc = h->cg_loc;
+      w.lw = h->cg_lw;
+      w.degree = h->cg_degree;
+      w.c0 = h->cg_c0;
+      for (int i = 0; i < kChebMax; ++i) {
+        w.c1[i] = h->cg_c1[i];
+        w.c2[i] = h->cg_c2[i];
+      }
       return launch_pcg32_pipe(a, w, h->grid32, h->rpt32, h->st);
     }
     return launch_pcg32(a, w, h->grid32, h->rpt32, h->st);
@@ -477,6 +495,10 @@ int build_modes(emu_handle* h) {
   EMU_CK(cudaMemcpyAsync(h->Einv, Ei.data(), 256 * 8, cudaMemcpyHostToDevice, h->st));
   if (h->mixed && h->rpt32 > 0)
     EMU_CK(launch_aphi32(n, h->rowptr, h->col, h->val32, h->phi32, h->aphi32, h->st));
+  if (h->cg_part) {  // the coarse rows in the partition order of the pipelined CG
+    EMU_CK(launch_gather_rows16(n, h->cg_perm, h->phi32, h->cg_phi, h->st));
+    EMU_CK(launch_gather_rows16(n, h->cg_perm, h->aphi32, h->cg_aphi, h->st));
+  }
   EMU_CK(cudaStreamSynchronize(h->st));
   h->coarse_ready = emax > 0.0;
   h->aphi_ready = h->mixed && h->rpt32 > 0;
@@ -524,6 +546,14 @@ bool alloc_device(emu_handle* h, int64_t nnz) {
     ok = ok && h->get(h->phi32, 16 * n) && h->get(h->ug32, 2 * n) && h->get(h->part32, 128 * (int64_t)h->sms) &&
          h->get(h->sync32, 96) && h->get(h->aphi32, 16 * n);
     if (!pcg32_shape(n, h->sms, &h->grid32, &h->rpt32)) h->rpt32 = 0;
+    // partitioned system of the pipelined CG (a dry run counts the widest table)
+    if (h->dry ? (h->rpt32 > 0 && pcg32_pipe_ok(h->rpt32)) : h->cg_part) {
+      const int lw = h->dry ? cg_local_width_max(h->rpt32) : h->cg_lw;
+      ok = ok && h->get(h->cg_perm, n) && h->get(h->cg_off, h->grid32 + 1) && h->get(h->cg_rowptr, n + 1) &&
+           h->get(h->cg_col, nnz) && h->get(h->cg_val, nnz) && h->get(h->cg_dinv, n) && h->get(h->cg_phi, 16 * n) &&
+           h->get(h->cg_aphi, 16 * n) &&
+           h->get(h->cg_loc, std::max<int64_t>(1, (int64_t)h->grid32 * h->rpt32 * lw * kPcg32Threads));
+    }
   }
   h->grid_tet = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 127) / 128), 8 * (int64_t)h->sms);
   h->grid_syrk = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 23) / 24), 2 * (int64_t)h->sms);
@@ -615,6 +645,7 @@ void emu_default_params(emu_params* p) {
   p->seed = 12345;
   p->eps_bone = -1e-3;
   p->eps_joint = -1e-4;
+  p->cg_local_degree = 4;
 }
 
 const char* emu_status_string(int status) {
@@ -852,6 +883,22 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
   h->device = dev;
   cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t nnz = (int64_t)colv.size();
+  // row partition and local preconditioner of the pipelined FP32 CG
+  CgPartHost cgp;
+  if (h->mixed) {
+    int g32 = 0, r32 = 0;
+    if (pcg32_shape(n, h->sms, &g32, &r32) && pcg32_pipe_ok(r32))
+      h->cg_part = build_cg_partition(n, Q, rowptr, colv, valv, g32, r32, kPcg32Threads, prm.cg_local_degree, &cgp);
+    if (h->cg_part) {
+      h->cg_lw = cgp.lw;
+      h->cg_degree = cgp.degree;
+      h->cg_c0 = cgp.c0;
+      for (int i = 0; i < kChebMax; ++i) {
+        h->cg_c1[i] = cgp.c1[i];
+        h->cg_c2[i] = cgp.c2[i];
+      }
+    }
+  }
   bool ok = alloc_device(h, nnz);
   if (!ok) {
     h->release();
@@ -917,6 +964,13 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
          up(h->w32, wf.data(), 4 * m) && up(h->mu32, muf.data(), 4 * m) && up(h->lam32, lf.data(), 4 * m) &&
          up(h->u32, uf.data(), 12 * m) && up(h->ka32, zf.data(), 4 * m) && up(h->val32, valf.data(), 4 * nnz) &&
          up(h->ldinv32, ldf.data(), 4 * n) && cudaStreamSynchronize(h->st) == cudaSuccess;
+    if (ok && h->cg_part) {
+      ok = up(h->cg_perm, cgp.perm.data(), 4 * n) && up(h->cg_off, cgp.off.data(), 4 * (h->grid32 + 1)) &&
+           up(h->cg_rowptr, cgp.rowptr.data(), 4 * (n + 1)) && up(h->cg_col, cgp.col.data(), 4 * cgp.col.size()) &&
+           up(h->cg_val, cgp.val.data(), 4 * cgp.val.size()) && up(h->cg_dinv, cgp.dinv.data(), 4 * n) &&
+           (cgp.loc.empty() || up(h->cg_loc, cgp.loc.data(), 4 * cgp.loc.size())) &&
+           cudaStreamSynchronize(h->st) == cudaSuccess;
+    }
   }
   if (!ok || cudaMemsetAsync(h->sc, 0, sizeof(DevScalars), h->st) != cudaSuccess) {
     h->release();

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "emu_cgpart.h"
 #include "emu_internal.h"
 
 namespace emu {
@@ -46,6 +47,8 @@ template <typename T> struct PcgArgsT {
 int pcg_max_grid(int nrhs, int64_t n);
 template <typename T> cudaError_t launch_pcg(int nrhs, const PcgArgsT<T>& args, int grid, cudaStream_t st);
 
+constexpr int kPcg32Threads = 256;  // threads per block of the FP32 CG kernels
+
 // Work space of the register-resident FP32 CG.
 struct Pcg32Work {
   float4* ug;      // 2 n exchange entries (x, then u, per vertex)
@@ -54,6 +57,15 @@ struct Pcg32Work {
   unsigned* sync;  // 96 words of barrier state, zero before the first launch
                    // (each launch leaves them zero)
   const float* aphi = nullptr;  // n x 16 rows of A Phi (pipelined kernel only)
+  // pipelined kernel only: the system in the row partition of emu_cgpart.h
+  // (args.rowptr/col/val/dinv/phi and aphi permuted; b and x in vertex order)
+  const int32_t* perm = nullptr;  // partition row -> vertex (n)
+  const int32_t* off = nullptr;   // grid + 1 row offsets of the blocks' parts
+  const uint32_t* loc = nullptr;  // local table: (grid x rpt x lw x 256) words
+  int lw = 0;                     // local entries per row slot
+  int degree = 1;                 // degree of the local polynomial (1: Jacobi)
+  float c0 = 1.f;                 // Chebyshev coefficients (emu_cgpart.h)
+  float c1[kChebMax] = {0}, c2[kChebMax] = {0};
 };
 
 // Register-resident FP32 CG (3 columns): shape for n rows on ``sms`` SMs
@@ -64,12 +76,17 @@ cudaError_t launch_pcg32(const PcgArgsT<float>& args, const Pcg32Work& work, int
 // Per-device kernel attributes of the FP32 CG (before its first launch).
 cudaError_t prepare_pcg32();
 // Pipelined form of the same iteration with one grid barrier per iteration
-// instead of two. It needs the coarse space (args.phi, args.Einv) and
-// work.aphi, and supports rpt <= 4; launch_pcg32_pipe returns
-// cudaErrorInvalidValue otherwise. Its recurrences drift from the true
-// residual near FP32 precision, so it serves the loose inner solves.
+// instead of two, on the partitioned system with the block-local polynomial
+// preconditioner. It needs the coarse space (args.phi, args.Einv),
+// work.aphi, work.perm and work.off, and supports rpt <= 4;
+// launch_pcg32_pipe returns cudaErrorInvalidValue otherwise. Its
+// recurrences drift from the true residual near FP32 precision, so it serves
+// the loose inner solves.
 bool pcg32_pipe_ok(int rpt);
 cudaError_t launch_pcg32_pipe(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, int rpt, cudaStream_t st);
+// dst[r][:] = src[perm[r]][:] for n rows of 16 floats (the coarse rows in
+// the partition order).
+cudaError_t launch_gather_rows16(int64_t n, const int32_t* perm, const float* src, float* dst, cudaStream_t st);
 // aphi = A phi for the n x 16 row-major coarse basis (FP32 CSR matrix).
 cudaError_t launch_aphi32(int64_t n, const int32_t* rowptr, const int32_t* col, const float* val, const float* phi,
                           float* aphi, cudaStream_t st);

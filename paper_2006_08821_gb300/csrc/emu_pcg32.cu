@@ -29,9 +29,11 @@ namespace emu {
 
 namespace {
 
-constexpr int NT = 256;  // threads per block
+constexpr int NT = kPcg32Threads;  // threads per block
 constexpr int NR = 3;    // right-hand sides (x, y, z)
 constexpr int kGather = 16;  // entries of a matrix row gathered at once
+constexpr int kGatherPart = 8;  // the same for the pruned, partitioned system
+constexpr int kLocUnroll = 8;   // local-table entries of a row read at once
 constexpr int kMaxGridStrides = 8;  // grid_sum_f handles up to 256 blocks
 // words of Pcg32Work::sync, one 128-byte line apart
 constexpr int kSyncCount = 0, kSyncDone = 32, kSyncErr = 64;
@@ -240,6 +242,47 @@ __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rowptr, co
   }
 }
 
+// The same product for the rows vr[k] of a partitioned system, GW entries
+// gathered at once (the pruned rows of a tetrahedral grid hold about 7).
+template <int RPT, int GW>
+__device__ __forceinline__ void spmv_rows_v(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                            const float* __restrict__ val, const bool (&own)[RPT],
+                                            const int64_t (&vr)[RPT], const float4* __restrict__ z,
+                                            float (&y)[RPT][NR]) {
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    y[k][0] = y[k][1] = y[k][2] = 0.f;
+    if (!own[k]) continue;
+    const int64_t v = vr[k];
+    const int32_t e0 = __ldg(rowptr + v), e1 = __ldg(rowptr + v + 1);
+    const int cnt = e1 - e0;
+    float4 z4[GW];
+    float a4[GW];
+#pragma unroll
+    for (int t = 0; t < GW; ++t) {
+      a4[t] = 0.f;
+      z4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (t < cnt) {
+        a4[t] = __ldg(val + e0 + t);
+        z4[t] = __ldcg(z + __ldg(col + e0 + t));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < GW; ++t) {
+      y[k][0] += a4[t] * z4[t].x;
+      y[k][1] += a4[t] * z4[t].y;
+      y[k][2] += a4[t] * z4[t].z;
+    }
+    for (int32_t e = e0 + GW; e < e1; ++e) {
+      const float av = __ldg(val + e);
+      const float4 zz = __ldcg(z + __ldg(col + e));
+      y[k][0] += av * zz.x;
+      y[k][1] += av * zz.y;
+      y[k][2] += av * zz.z;
+    }
+  }
+}
+
 // loc[m NR + j] += Phi[v][m] y[k][j] over the owned rows; the coarse rows of
 // a thread live in shared memory, float4 q of row k at sPhi[(q RPT + k) NT + tid]
 template <int RPT>
@@ -260,6 +303,19 @@ __device__ __forceinline__ void phi_t_rows(const float4* sPhi, const bool (&own)
       }
     }
   }
+}
+
+// The same, written as one float4 (3 columns and a zero) per mode.
+__device__ __forceinline__ void coarse_solve4(const float* s_Einv, const float* s_rho, float4* s_cc4) {
+  for (int e = threadIdx.x; e < kModes * NR; e += NT) {
+    const int m = e / NR, j = e % NR;
+    float acc = 0.f;
+#pragma unroll
+    for (int l = 0; l < kModes; ++l) acc += s_Einv[m * kModes + l] * s_rho[l * NR + j];
+    reinterpret_cast<float*>(s_cc4)[4 * m + j] = acc;
+  }
+  if (threadIdx.x < kModes) reinterpret_cast<float*>(s_cc4)[4 * threadIdx.x + 3] = 0.f;
+  __syncthreads();
 }
 
 // cc = E^-1 rho for the 16 x 3 coarse coefficients (block-wide, then a barrier)
@@ -548,12 +604,22 @@ timeout:
 // Vanroose), with one grid barrier per iteration instead of two. The
 // preconditioned residual u = M r and w = A u are carried by recurrences,
 // together with q = M s and z = A q, so that the only vector a block needs
-// from its neighbours, v = D^-1 w, is published with the partial sums of the
-// same iteration. The coarse part of M w, Phi E^-1 Phi^T w, needs Phi^T w,
-// a global sum; it is applied after the barrier through the precomputed
-// rows of A Phi: n = A M w = A v + (A Phi) c with c = E^-1 Phi^T w.
+// from its neighbours, v = P w (the local part of M w), is published with
+// the partial sums of the same iteration. The coarse part of M w,
+// Phi E^-1 Phi^T w, needs Phi^T w, a global sum; it is applied after the
+// barrier through the precomputed rows of A Phi:
+// n = A M w = A v + (A Phi) c with c = E^-1 Phi^T w.
 // Exchange vectors and partial sums alternate between two buffers: a block
 // may publish iteration i + 1 while a slower one still reads iteration i.
+//
+// The system is the partitioned one of emu_cgpart.h: block b owns the rows
+// off[b] .. off[b + 1] - 1 (a spatially compact part of the mesh), thread t
+// the rows off[b] + k NT + t. The local part of the preconditioner,
+// P = D^-1/2 p(A_b) D^-1/2 with A_b the block's diagonal block of
+// D^-1/2 A D^-1/2 and p the Chebyshev polynomial of the given degree, needs
+// no exchange: its products run on the block's rows in shared memory.
+// With the coarse space, M = P + Phi E^-1 Phi^T is a two-level additive
+// Schwarz preconditioner (degree 1: P = D^-1, plain Jacobi).
 template <int RPT>
 __global__ void __launch_bounds__(NT, 1) pcg32p_kernel(PcgArgsT<float> a, Pcg32Work wk) {
   constexpr int NC = kModes * NR;
@@ -564,82 +630,194 @@ __global__ void __launch_bounds__(NT, 1) pcg32p_kernel(PcgArgsT<float> a, Pcg32W
   __shared__ float ssum[NV0];
   __shared__ float s_al[NR], s_be[NR], s_ga[NR], s_thr[NR], s_bb[NR], s_rr[NR];
   __shared__ int s_act[NR];
-  __shared__ float s_rho[NC], s_cc[NC];
+  __shared__ float s_rho[NC];
+  __shared__ float4 s_cc4[kModes];  // E^-1 rho, one float4 (3 columns) per mode
   __shared__ float s_Einv[kModes * kModes];
   __shared__ int s_flag;
-  // rows of Phi, then rows of A Phi: float4 q of row k at [(q * RPT + k) * NT + tid]
+  __shared__ float s_c1[kChebMax], s_c2[kChebMax];  // Chebyshev coefficients
+  // rows of Phi, then rows of A Phi: float4 q of row k at [(q * RPT + k) * NT + tid];
+  // then two buffers of the local products and the local table
   extern __shared__ float4 sPhi[];
   float4* sAPhi = sPhi + (kModes / 4) * RPT * NT;
+  float4* sBuf = sAPhi + (kModes / 4) * RPT * NT;
+  uint32_t* sLoc = reinterpret_cast<uint32_t*>(sBuf + 2 * RPT * NT);
   unsigned epoch = 0;
-  const int64_t n = a.n;
   const int G = gridDim.x;
-  const int64_t stride = (int64_t)G * NT;
-  const int64_t g0 = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int lw = wk.degree > 1 ? wk.lw : 0;
+  const int64_t rbeg = wk.off[blockIdx.x], rend = wk.off[blockIdx.x + 1];
   const int32_t* __restrict__ rowptr = a.rowptr;
   const int32_t* __restrict__ col = a.col;
   const float* __restrict__ val = a.val;
+  const int32_t* __restrict__ perm = wk.perm;
   for (int k = threadIdx.x; k < kModes * kModes; k += NT) s_Einv[k] = (float)a.Einv[k];
+  if (threadIdx.x < kChebMax) {
+    s_c1[threadIdx.x] = wk.c1[threadIdx.x];
+    s_c2[threadIdx.x] = wk.c2[threadIdx.x];
+  }
+  {
+    const uint32_t* __restrict__ lsrc = wk.loc + (size_t)blockIdx.x * RPT * lw * NT;
+    for (int e = threadIdx.x; e < RPT * lw * NT; e += NT) sLoc[e] = __ldg(lsrc + e);
+  }
 
   float x[RPT][NR], r[RPT][NR], u[RPT][NR], w[RPT][NR], p[RPT][NR], s[RPT][NR], qv[RPT][NR], z[RPT][NR];
-  float di[RPT];
+  float di[RPT], sd[RPT];  // D^-1 and D^-1/2 of the rows
+  int64_t vr[RPT];
   bool own[RPT];
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
-    const int64_t v = g0 + k * stride;
-    own[k] = v < n;
+    const int64_t v = rbeg + k * NT + threadIdx.x;
+    vr[k] = v;
+    own[k] = v < rend;
     di[k] = own[k] ? __ldg(a.dinv + v) : 0.f;
-    const float4* ph = reinterpret_cast<const float4*>(a.phi + v * kModes);
-    const float4* aph = reinterpret_cast<const float4*>(wk.aphi + v * kModes);
+    sd[k] = sqrtf(di[k]);
+    const float4* ph = reinterpret_cast<const float4*>(a.phi + (own[k] ? v : 0) * kModes);
+    const float4* aph = reinterpret_cast<const float4*>(wk.aphi + (own[k] ? v : 0) * kModes);
 #pragma unroll
     for (int q = 0; q < kModes / 4; ++q) {
       sPhi[(q * RPT + k) * NT + threadIdx.x] = own[k] ? __ldg(ph + q) : make_float4(0.f, 0.f, 0.f, 0.f);
       sAPhi[(q * RPT + k) * NT + threadIdx.x] = own[k] ? __ldg(aph + q) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    const int64_t o = own[k] ? (int64_t)__ldg(perm + v) : 0;
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-      x[k][j] = own[k] ? a.x[v * NR + j] : 0.f;
+      x[k][j] = own[k] ? a.x[o * NR + j] : 0.f;
       p[k][j] = s[k][j] = qv[k][j] = z[k][j] = 0.f;
     }
   }
 
   auto spmv = [&](const float4* __restrict__ zsrc, float (&y)[RPT][NR]) {
-    spmv_rows<RPT>(rowptr, col, val, own, g0, stride, zsrc, y);
+    spmv_rows_v<RPT, kGatherPart>(rowptr, col, val, own, vr, zsrc, y);
   };
   auto phi_t = [&](const float (&y)[RPT][NR], float* loc) { phi_t_rows<RPT>(sPhi, own, y, loc); };
-  auto coarse_cc = [&]() { coarse_solve(s_Einv, s_rho, s_cc); };  // s_cc = E^-1 s_rho
-  // sum_m rows[v][m] s_cc[m NR + j] for row k (rows: sPhi or sAPhi)
-  auto coarse_row = [&](const float4* rows, int k, int j) {
-    float acc = 0.f;
+  auto coarse_cc = [&]() { coarse_solve4(s_Einv, s_rho, s_cc4); };  // s_cc4 = E^-1 s_rho
+  // o[j] = sum_m rows[v][m] cc[m][j] for row k (rows: sPhi or sAPhi)
+  auto coarse3 = [&](const float4* rows, int k, float (&o)[NR]) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < kModes / 4; ++q) {
       const float4 ph = rows[(q * RPT + k) * NT + threadIdx.x];
-      acc += ph.x * s_cc[(4 * q) * NR + j] + ph.y * s_cc[(4 * q + 1) * NR + j] + ph.z * s_cc[(4 * q + 2) * NR + j] +
-             ph.w * s_cc[(4 * q + 3) * NR + j];
+      const float4 c0 = s_cc4[4 * q], c1 = s_cc4[4 * q + 1], c2 = s_cc4[4 * q + 2], c3 = s_cc4[4 * q + 3];
+      acc.x += ph.x * c0.x + ph.y * c1.x + ph.z * c2.x + ph.w * c3.x;
+      acc.y += ph.x * c0.y + ph.y * c1.y + ph.z * c2.y + ph.w * c3.y;
+      acc.z += ph.x * c0.z + ph.y * c1.z + ph.z * c2.z + ph.w * c3.z;
     }
-    return acc;
+    o[0] = acc.x;
+    o[1] = acc.y;
+    o[2] = acc.z;
+  };
+  // t = O y on the block's rows, O the off-diagonal part of A_b (bfloat16
+  // weights, local column in the low half of a table word). Every thread of
+  // the block calls it (it holds a block barrier); the two buffers alternate,
+  // so one barrier per product suffices.
+  int pb = 0;
+  auto off_apply = [&](const float (&y)[RPT][NR], float (&t)[RPT][NR]) {
+    float4* buf = sBuf + pb * (RPT * NT);
+    pb ^= 1;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+      buf[k * NT + threadIdx.x] = own[k] ? make_float4(y[k][0], y[k][1], y[k][2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+      const uint32_t* le = sLoc + (size_t)k * lw * NT + threadIdx.x;
+      // the first kLocUnroll entries at once (all loads in flight), the rest in a loop
+      uint32_t wd[kLocUnroll];
+#pragma unroll
+      for (int e = 0; e < kLocUnroll; ++e) wd[e] = e < lw ? le[e * NT] : 0u;
+      float4 yv[kLocUnroll];
+#pragma unroll
+      for (int e = 0; e < kLocUnroll; ++e) yv[e] = buf[wd[e] & 0xFFFFu];
+#pragma unroll
+      for (int e = 0; e < kLocUnroll; ++e) {
+        const float av = __uint_as_float(wd[e] & 0xFFFF0000u);
+        t0 += av * yv[e].x;
+        t1 += av * yv[e].y;
+        t2 += av * yv[e].z;
+      }
+      for (int e = kLocUnroll; e < lw; ++e) {
+        const uint32_t word = le[e * NT];
+        const float av = __uint_as_float(word & 0xFFFF0000u);
+        const float4 y4 = buf[word & 0xFFFFu];
+        t0 += av * y4.x;
+        t1 += av * y4.y;
+        t2 += av * y4.z;
+      }
+      t[k][0] = t0;
+      t[k][1] = t1;
+      t[k][2] = t2;
+    }
+  };
+  // out = P y: Chebyshev acceleration for A_b x = D^-1/2 y from x = 0, then
+  // D^-1/2 x (degree 1: D^-1 y)
+  auto local_apply = [&](const float (&y)[RPT][NR], float (&out)[RPT][NR]) {
+    if (lw == 0) {
+#pragma unroll
+      for (int k = 0; k < RPT; ++k)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) out[k][j] = di[k] * y[k][j];
+      return;
+    }
+    float xk[RPT][NR], dk[RPT][NR], res[RPT][NR], t[RPT][NR];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        res[k][j] = sd[k] * y[k][j];
+        xk[k][j] = dk[k][j] = wk.c0 * res[k][j];
+      }
+    off_apply(xk, t);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) res[k][j] -= xk[k][j] + t[k][j];
+    // one copy of the step in the code (a short kernel body stays in the instruction cache)
+#pragma unroll 1
+    for (int i = 1; i < wk.degree; ++i) {
+      const float c1 = s_c1[i], c2 = s_c2[i];
+#pragma unroll
+      for (int k = 0; k < RPT; ++k)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          dk[k][j] = c1 * dk[k][j] + c2 * res[k][j];
+          xk[k][j] += dk[k][j];
+        }
+      if (i + 1 < wk.degree) {
+        off_apply(dk, t);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+#pragma unroll
+          for (int j = 0; j < NR; ++j) res[k][j] -= dk[k][j] + t[k][j];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) out[k][j] = sd[k] * xk[k][j];
+  };
+  auto rhs = [&](int k, int j) {  // b of row k (vertex order on input)
+    return a.b[(int64_t)__ldg(perm + vr[k]) * NR + j];
   };
 
   // ---- r = b - A x ------------------------------------------------------
 #pragma unroll
-  for (int k = 0; k < RPT; ++k) {
-    const int64_t v = g0 + k * stride;
-    if (own[k]) wk.ug[v] = make_float4(x[k][0], x[k][1], x[k][2], 0.f);
-  }
+  for (int k = 0; k < RPT; ++k)
+    if (own[k]) wk.ug[vr[k]] = make_float4(x[k][0], x[k][1], x[k][2], 0.f);
   if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
   spmv(wk.ug, w);
 #pragma unroll
-  for (int k = 0; k < RPT; ++k) {
-    const int64_t v = g0 + k * stride;
+  for (int k = 0; k < RPT; ++k)
 #pragma unroll
-    for (int j = 0; j < NR; ++j) r[k][j] = own[k] ? a.b[v * NR + j] - w[k][j] : 0.f;
-  }
-  {  // u = D^-1 r + Phi E^-1 Phi^T r, published in the second exchange buffer
+    for (int j = 0; j < NR; ++j) r[k][j] = own[k] ? rhs(k, j) - w[k][j] : 0.f;
+  {  // u = P r + Phi E^-1 Phi^T r, published in the second exchange buffer
     float loc[NV0];
 #pragma unroll
     for (int k = 0; k < NV0; ++k) loc[k] = 0.f;
     phi_t(r, loc);
     block_sum_f<NV0>(loc, ssum, sm);
     for (int k = threadIdx.x; k < NC; k += NT) wk.part[(size_t)k * G + blockIdx.x] = ssum[k];
+    float ul[RPT][NR];
+    local_apply(r, ul);
     if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
     grid_sum_f<NV0>(wk.part, NC, ssum);
     for (int k = threadIdx.x; k < NC; k += NT) s_rho[k] = ssum[k];
@@ -647,47 +825,49 @@ __global__ void __launch_bounds__(NT, 1) pcg32p_kernel(PcgArgsT<float> a, Pcg32W
     coarse_cc();
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
-      const int64_t v = g0 + k * stride;
+      float cm[NR];
+      coarse3(sPhi, k, cm);
 #pragma unroll
-      for (int j = 0; j < NR; ++j) u[k][j] = own[k] ? di[k] * r[k][j] + coarse_row(sPhi, k, j) : 0.f;
-      if (own[k]) wk.ug[n + v] = make_float4(u[k][0], u[k][1], u[k][2], 0.f);
+      for (int j = 0; j < NR; ++j) u[k][j] = own[k] ? ul[k][j] + cm[j] : 0.f;
+      if (own[k]) wk.ug[a.n + vr[k]] = make_float4(u[k][0], u[k][1], u[k][2], 0.f);
     }
   }
   if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
-  spmv(wk.ug + n, w);  // w = A u
+  spmv(wk.ug + a.n, w);  // w = A u
 
   {
     int it = 0, buf = 0;
     bool first = true, all_done = false;
     for (;;) {
-      float* __restrict__ pb = wk.part + (size_t)buf * PSTRIDE * G;
-      float4* __restrict__ ub = wk.ug + (size_t)buf * n;
-      {  // partial sums of this iteration and v = D^-1 w for the neighbours
+      float* __restrict__ pbuf = wk.part + (size_t)buf * PSTRIDE * G;
+      float4* __restrict__ ub = wk.ug + (size_t)buf * a.n;
+      float vl[RPT][NR];  // v = P w, published for the neighbours
+      local_apply(w, vl);
+      {  // partial sums of this iteration
         float loc[NV0];
 #pragma unroll
         for (int k = 0; k < NV0; ++k) loc[k] = 0.f;
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
           if (!own[k]) continue;
-          const int64_t v = g0 + k * stride;
 #pragma unroll
           for (int j = 0; j < NR; ++j) {
             loc[j] += r[k][j] * u[k][j];
             loc[NR + j] += w[k][j] * u[k][j];
             loc[2 * NR + j] += r[k][j] * r[k][j];
             if (first) {
-              const float bv = a.b[v * NR + j];
+              const float bv = rhs(k, j);
               loc[3 * NR + j] += bv * bv;
             }
           }
-          ub[v] = make_float4(di[k] * w[k][0], di[k] * w[k][1], di[k] * w[k][2], 0.f);
+          ub[vr[k]] = make_float4(vl[k][0], vl[k][1], vl[k][2], 0.f);
         }
         phi_t(w, loc + 4 * NR);
         block_sum_f<NV0>(loc, ssum, sm);
-        for (int k = threadIdx.x; k < NV0; k += NT) pb[(size_t)k * G + blockIdx.x] = ssum[k];
+        for (int k = threadIdx.x; k < NV0; k += NT) pbuf[(size_t)k * G + blockIdx.x] = ssum[k];
       }
       if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
-      grid_sum_f<NV0>(pb, NV0, ssum);
+      grid_sum_f<NV0>(pbuf, NV0, ssum);
       if (threadIdx.x < NR) {
         const int j = threadIdx.x;
         if (first) {
@@ -729,15 +909,18 @@ __global__ void __launch_bounds__(NT, 1) pcg32p_kernel(PcgArgsT<float> a, Pcg32W
       ++it;
       coarse_cc();  // c = E^-1 Phi^T w
       float nv[RPT][NR];
-      spmv(ub, nv);  // A D^-1 w
+      spmv(ub, nv);  // A P w
 #pragma unroll
-      for (int k = 0; k < RPT; ++k)
+      for (int k = 0; k < RPT; ++k) {
+        float cm[NR], cn[NR];
+        coarse3(sPhi, k, cm);
+        coarse3(sAPhi, k, cn);
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
           if (!s_act[j]) continue;
           const float be = s_be[j], al = s_al[j];
-          const float mv = di[k] * w[k][j] + coarse_row(sPhi, k, j);   // m = M w
-          const float nn = nv[k][j] + coarse_row(sAPhi, k, j);         // n = A M w
+          const float mv = vl[k][j] + cm[j];  // m = M w
+          const float nn = nv[k][j] + cn[j];  // n = A M w
           z[k][j] = nn + be * z[k][j];
           qv[k][j] = mv + be * qv[k][j];
           s[k][j] = w[k][j] + be * s[k][j];
@@ -747,15 +930,17 @@ __global__ void __launch_bounds__(NT, 1) pcg32p_kernel(PcgArgsT<float> a, Pcg32W
           u[k][j] -= al * qv[k][j];
           w[k][j] -= al * z[k][j];
         }
+      }
       first = false;
       buf ^= 1;
     }
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
-      const int64_t v = g0 + k * stride;
-      if (own[k])
+      if (own[k]) {
+        const int64_t o = __ldg(perm + vr[k]);
 #pragma unroll
-        for (int j = 0; j < NR; ++j) a.x[v * NR + j] = x[k][j];
+        for (int j = 0; j < NR; ++j) a.x[o * NR + j] = x[k][j];
+      }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       if (a.iters_out) atomicAdd(a.iters_out, it);
@@ -772,6 +957,16 @@ timeout:
   gbar_exit(wk);
 }
 
+// dst[r][:] = src[perm[r]][:], 16 floats per row (four float4)
+__global__ void k_gather_rows16(int64_t n, const int32_t* __restrict__ perm, const float4* __restrict__ src,
+                                float4* __restrict__ dst) {
+  const int64_t tot = n * (kModes / 4);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / (kModes / 4);
+    const int q = (int)(i % (kModes / 4));
+    dst[i] = src[(int64_t)perm[r] * (kModes / 4) + q];
+  }
+}
 // aphi = A phi, one thread per (row, four modes)
 __global__ void k_aphi32(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                          const float* __restrict__ val, const float4* __restrict__ phi, float4* __restrict__ aphi) {
@@ -838,9 +1033,11 @@ bool pcg32_shape(int64_t n, int sms, int* grid, int* rpt) {
 
 
 namespace {
+// rows of Phi and of A Phi, two buffers of the local products, the local table
 template <int RPT>
-constexpr size_t pipe_smem() {
-  return 2 * sizeof(float4) * (kModes / 4) * RPT * NT;  // rows of Phi and of A Phi
+constexpr size_t pipe_smem(int lw) {
+  return 2 * sizeof(float4) * (kModes / 4) * RPT * NT + 2 * sizeof(float4) * RPT * NT +
+         sizeof(uint32_t) * (size_t)RPT * lw * NT;
 }
 
 template <int RPT>
@@ -848,13 +1045,14 @@ cudaError_t prepare32p() {
   static bool set[64] = {false};
   static std::mutex mu;  // handles may be built from several threads
   std::lock_guard<std::mutex> lock(mu);
-  if (pipe_smem<RPT>() <= 48 * 1024) return cudaSuccess;
+  const size_t smem = pipe_smem<RPT>(cg_local_width_max(RPT));
+  if (smem <= 48 * 1024) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (set[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(pcg32p_kernel<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipe_smem<RPT>());
+  e = cudaFuncSetAttribute(pcg32p_kernel<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) set[dev] = true;
   return e;
 }
@@ -863,8 +1061,10 @@ template <int RPT>
 cudaError_t launch32p(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, cudaStream_t st) {
   PcgArgsT<float> a = args;
   Pcg32Work w = work;
+  const int lw = w.degree > 1 ? w.lw : 0;
+  if (lw > cg_local_width_max(RPT) || (w.degree > 1 && !w.loc)) return cudaErrorInvalidValue;
   void* params[] = {(void*)&a, (void*)&w};
-  return cudaLaunchCooperativeKernel((const void*)pcg32p_kernel<RPT>, dim3(grid), dim3(NT), params, pipe_smem<RPT>(),
+  return cudaLaunchCooperativeKernel((const void*)pcg32p_kernel<RPT>, dim3(grid), dim3(NT), params, pipe_smem<RPT>(lw),
                                      st);
 }
 }  // namespace
@@ -872,13 +1072,22 @@ cudaError_t launch32p(const PcgArgsT<float>& args, const Pcg32Work& work, int gr
 bool pcg32_pipe_ok(int rpt) { return rpt == 1 || rpt == 2 || rpt == 4; }
 
 cudaError_t launch_pcg32_pipe(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, int rpt, cudaStream_t st) {
-  if (grid > 32 * kMaxGridStrides || !args.phi || !args.Einv || !work.aphi) return cudaErrorInvalidValue;
+  if (grid > 32 * kMaxGridStrides || !args.phi || !args.Einv || !work.aphi || !work.perm || !work.off ||
+      work.degree < 1 || work.degree > kChebMax)
+    return cudaErrorInvalidValue;
   switch (rpt) {
     case 1: return launch32p<1>(args, work, grid, st);
     case 2: return launch32p<2>(args, work, grid, st);
     case 4: return launch32p<4>(args, work, grid, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_gather_rows16(int64_t n, const int32_t* perm, const float* src, float* dst, cudaStream_t st) {
+  const int64_t tot = n * (kModes / 4);
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(1, (tot + 255) / 256), 4096);
+  k_gather_rows16<<<grid, 256, 0, st>>>(n, perm, reinterpret_cast<const float4*>(src), reinterpret_cast<float4*>(dst));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_aphi32(int64_t n, const int32_t* rowptr, const int32_t* col, const float* val, const float* phi,
@@ -893,6 +1102,7 @@ cudaError_t launch_aphi32(int64_t n, const int32_t* rowptr, const int32_t* col, 
 cudaError_t prepare_pcg32() {
   cudaError_t e = prepare32<4, true>();
   if (e == cudaSuccess) e = prepare32<8, true>();
+  if (e == cudaSuccess) e = prepare32p<1>();
   if (e == cudaSuccess) e = prepare32p<2>();
   if (e == cudaSuccess) e = prepare32p<4>();
   return e;
