@@ -57,9 +57,10 @@ FALLBACK_HBM_GBS = 6800.0
 # kernel has changed since.
 NCU_TRAFFIC = {
     "pcg": (20.60e6, "profiles/pcg32p_kernel_mtu401920.md"),
-    "grad": (127.31e6, "profiles/k_grad_m_mtu401920.md"),
-    "dir": (229.04e6, "profiles/k_dir_m_mtu401920.md"),
-    "ls": None,  # k_ls_m's last-block selection changed after its capture
+    "grad": (124.19e6, "profiles/k_grad_m_mtu401920.md"),
+    "dir": (230.63e6, "profiles/k_dir_m_mtu401920.md"),
+    "ls": (82.91e6, "profiles/k_ls_m_mtu401920.md"),
+    "syrk": (183.33e6, "profiles/k_syrk_tc_mtu401920.md"),
 }
 
 
@@ -137,9 +138,10 @@ def algorithmic_bytes(phase, mixed, m, n, nnz, cg_iters):
 PER_TET_KERNELS = {"grad": 0.5, "syrk": 1.0, "dir": 1.0, "ls": 1.0, "update": 0.5}
 
 
-def per_tet_fractions(prof, mixed, m, n, nnz, peak):
+def per_tet_fractions(prof, mixed, m, n, nnz, peak, traffic_table=None):
     """Each per-tet kernel's algorithmic bytes per launch over its average
-    CUDA-event duration, against the HBM peak."""
+    CUDA-event duration, against the HBM peak; with the kernel's ncu DRAM
+    bytes per launch beside it where a capture of the unchanged kernel exists."""
     out = {}
     for name, per in PER_TET_KERNELS.items():
         ms, nl = prof.get(name, (0.0, 0))
@@ -151,6 +153,10 @@ def per_tet_fractions(prof, mixed, m, n, nnz, peak):
         gbs = b / (us * 1e-6) / 1e9
         out[name] = {"bytes_per_launch": b, "us_per_launch": round(us, 2), "achieved_gbs": round(gbs, 1),
                      "frac": round(gbs / peak, 3)}
+        tr = (traffic_table or {}).get(name)
+        if tr:
+            out[name]["ncu_dram_bytes"] = tr[0]
+            out[name]["ncu_dram_frac"] = round(tr[0] / (us * 1e-6) / 1e9 / peak, 3)
     return out
 
 
@@ -542,7 +548,7 @@ def run_batch(args, emu, torch, rank, world, dist):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": batch_desc(meshes, args.tol),
                    "precision": args.precision, "l2": "inputs larger than L2; flushed between steps",
-                   "tets": int(m_each.sum()), "meshes": len(meshes), "ls_sigma0": params.ls_sigma0},
+                   "tets": int(m_each.sum()), "meshes": len(meshes), "ls_sigma0": params.ls_sigma0, "cg_local_degree": params.cg_local_degree},
         "newton_iters_per_step": iters, "max_rel_residual_converged": float(np.max(resid)),
         "not_converged": failed[-1], "setup_s": setup_s,
         "roofline": None, "cpu_baseline": None,
@@ -739,7 +745,8 @@ def main():
     nnz = solver_nnz(mesh)
     cg_per_iter = prof_cg / max(prof_its, 1)
     dev_ms = sum(v[0] for v in prof.values())
-    per_tet = per_tet_fractions(prof, mixed, m, n, nnz, peak)
+    per_tet = per_tet_fractions(prof, mixed, m, n, nnz, peak,
+                                NCU_TRAFFIC if (mixed and args.workload == "mtu") else {})
     roof = dominant_roofline(prof, mixed, m, n, nnz, float(prof_cg), peak, peak_kind,
                              NCU_TRAFFIC if (mixed and args.workload == "mtu") else {})
     whole = whole_iteration(prof, mixed, m, n, nnz, float(prof_cg), prof_its, peak, value)
@@ -751,7 +758,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "l2": f"flushed ({args.flush_mb} MB write) between steps",
-                   "tets": m, "verts": n, "ls_sigma0": params.ls_sigma0},
+                   "tets": m, "verts": n, "ls_sigma0": params.ls_sigma0, "cg_local_degree": params.cg_local_degree},
         "ms_per_converged_frame_p50": float(np.median(frame_ms)),
         "frame_ms_p99": float(np.percentile(frame_ms, 99)),
         "newton_iters_per_frame": [int(x) for x in iters],
