@@ -60,7 +60,7 @@ NCU_TRAFFIC = {
     "grad": (124.19e6, "profiles/k_grad_m_mtu401920.md"),
     "dir": (230.63e6, "profiles/k_dir_m_mtu401920.md"),
     "ls": (82.91e6, "profiles/k_ls_m_mtu401920.md"),
-    "syrk": (183.33e6, "profiles/k_syrk_tc_mtu401920.md"),
+    "syrk": (183.30e6, "profiles/k_syrk05_mtu401920.md"),
 }
 
 

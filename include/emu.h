@@ -374,6 +374,23 @@ int emu_eval_stretch_terms(const double* s, const double* params, int64_t n, int
  * device memory for the duration of the call and synchronises ``stream``. */
 int emu_check_bounded_wait(int64_t wait_ns, void* stream);
 
+/* The capacitance of the Woodbury direction in its Gram form (Eq. 12) from
+ * per-tet factors, on the device kernels of the mixed path:
+ *   C  = sum_i Yh_i^T Yh_i,  Yh_i = sqrt(w_i) U_i (I3 (x) Gamma_i)   (48 x 48)
+ *   By = sum_i w_i (I3 (x) Gamma_i)^T y_i                           (48)
+ * with U_i the 6 x 9 chart factor (N_i = U_i^T U_i), Gamma_i the 3 x 16
+ * gradients of the 16 scalar modes on tet i (column j = 16 d + l of
+ * I3 (x) Gamma_i is e_d (x) Gamma_i[:, l]) and y_i a 9-vector (row-major
+ * 3 x 3). Host inputs, component-major over the m tets: U[(9 r + c) m + i]
+ * (U_i[r][c]), gamma[(3 l + b) m + i] (Gamma_i[b][l]), y[k m + i], w[i].
+ * kernel: 0 = the one a solve on these sizes uses, 1 = tcgen05 tensor
+ * cores (m a multiple of 4), 2 = mma.sync tensor cores. Yh is rounded to
+ * TF32 and the sums run in FP32 per block, FP64 across blocks. Outputs (host):
+ * C row-major, By. Allocates device memory for the call and synchronises
+ * ``stream``; EMU_ERR_INVALID_ARG for bad sizes or kernel 1 with m % 4 != 0. */
+int emu_eval_capacitance(int64_t m, const float* U, const float* gamma, const float* y, const float* w,
+                         int32_t kernel, double* C, double* By, void* stream);
+
 /* Polar decomposition F = R S (R proper rotation, S symmetric positive
  * definite) of n row-major 3x3 matrices with det F > 0, on the device.
  * Outputs R (n x 9) and s (n x 6, ordering as emu_get_element_state). */

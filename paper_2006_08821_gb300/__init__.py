@@ -17,6 +17,7 @@ from .binding import (  # noqa: F401
     required_bytes,
     TorchAllocator,
     default_params,
+    eval_capacitance,
     eval_polar,
     eval_stretch_terms,
     load_library,

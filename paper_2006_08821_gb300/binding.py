@@ -39,6 +39,7 @@ EXPORTED = [
     "emu_eval_stretch_terms", "emu_eval_polar", "emu_set_profiling", "emu_get_profile",
     "emu_acap_solve_noalloc", "emu_batch_solve", "emu_required_bytes", "emu_server_create",
     "emu_server_submit", "emu_server_poll", "emu_server_result", "emu_server_destroy", "emu_check_bounded_wait",
+    "emu_eval_capacitance",
 ]
 
 PHASES = ["rhs", "assemble", "pcg", "grad", "syrk", "small", "dir", "ls", "update"]
@@ -178,6 +179,8 @@ def load_library(path: str = LIB_PATH):
     lib.emu_server_result.argtypes = [C.c_void_p, C.c_uint64, P(C.c_double), P(emu_request_stats)]
     lib.emu_server_destroy.argtypes = [C.c_void_p]
     lib.emu_check_bounded_wait.argtypes = [C.c_int64, C.c_void_p]
+    lib.emu_eval_capacitance.argtypes = [C.c_int64, P(C.c_float), P(C.c_float), P(C.c_float), P(C.c_float),
+                                         C.c_int32, P(C.c_double), P(C.c_double), C.c_void_p]
     for name in EXPORTED:
         if name not in ("emu_default_params", "emu_status_string", "emu_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -483,6 +486,25 @@ def check_bounded_wait(wait_ns: int, stream=0) -> int:
     (EMU_ERR_TIMEOUT is the expected result)."""
     lib = load_library()
     return lib.emu_check_bounded_wait(int(wait_ns), C.c_void_p(int(stream)) if stream else None)
+
+
+def eval_capacitance(U, gamma, y, w, kernel=0, stream=0):
+    """emu_eval_capacitance: (C 48 x 48, By 48) from component-major float32
+    host arrays U (54, m), gamma (48, m), y (9, m), w (m,)."""
+    lib = load_library()
+    U = np.ascontiguousarray(U, dtype=np.float32)
+    gamma = np.ascontiguousarray(gamma, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    m = w.shape[0]
+    if U.shape != (54, m) or gamma.shape != (48, m) or y.shape != (9, m):
+        raise ValueError("U (54, m), gamma (48, m), y (9, m), w (m,) expected")
+    Cm = np.zeros((48, 48))
+    By = np.zeros(48)
+    _check(lib.emu_eval_capacitance(m, _dptr(U, C.c_float), _dptr(gamma, C.c_float), _dptr(y, C.c_float),
+                                    _dptr(w, C.c_float), int(kernel), _dptr(Cm, C.c_double), _dptr(By, C.c_double),
+                                    C.c_void_p(int(stream)) if stream else None), lib)
+    return Cm, By
 
 
 def eval_polar(F_dev, n, R_dev, s_dev, stream=0):

@@ -13,6 +13,7 @@
 #include "emu_kernels.cuh"
 #include "emu_mixed.cuh"
 #include "emu_pcg.h"
+#include "emu_syrk05.h"
 
 namespace emu {
 // Cyclic Jacobi eigen-decomposition of a symmetric N x N matrix (row-major):
@@ -84,6 +85,9 @@ struct emu_handle {
   float* part32 = nullptr;
   float* aphi32 = nullptr;                // rows of L Phi for the pipelined FP32 CG
   bool aphi_ready = false;
+  bool syrk05 = false;  // capacitance on the tcgen05 kernel (else mma.sync)
+  Syrk05Maps syrk05_maps;  // its tensor maps of Uw32, gam32, y32, sw32
+  float* sw32 = nullptr;    // sqrt of the ACAP weights (m)
   int grid32 = 0, rpt32 = 0;
   // the partitioned system of the pipelined FP32 CG (emu_cgpart.h)
   bool cg_part = false;  // built at creation (mixed path, pipelined shape)
@@ -320,6 +324,7 @@ struct emu_handle {
     a.V = V32;
     a.c = c32;
     a.w = w32;
+    a.sw = sw32;
     a.mu = mu32;
     a.lam = lam32;
     a.ka = ka32;

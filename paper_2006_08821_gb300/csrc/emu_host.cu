@@ -38,6 +38,7 @@ int fail(int code, const std::string& msg) {
 }  // namespace
 
 #include "emu_handle.h"
+#include "emu_syrk05.h"
 
 // Cyclic Jacobi eigen-decomposition of a symmetric N x N matrix (row-major):
 // A is overwritten (its diagonal holds the eigenvalues), V receives the
@@ -532,6 +533,7 @@ bool alloc_device(emu_handle* h, int64_t nnz) {
   if (h->mixed) {
     ok = ok && h->get(h->gam32, 48 * m) && h->get(h->y32, 9 * m) && h->get(h->d32, 9 * m) && h->get(h->Uw32, 54 * m);
     ok = ok && h->get(h->Dinv32, 9 * m) && h->get(h->V32, m) && h->get(h->c32, m) && h->get(h->w32, m) &&
+         h->get(h->sw32, m) &&
          h->get(h->mu32, m) && h->get(h->lam32, m) && h->get(h->u32, 3 * m) && h->get(h->ka32, m) &&
          h->get(h->E32, 6 * m) && h->get(h->g32, 9 * m) && h->get(h->quat, m) && h->get(h->dq32, 3 * n) &&
          h->get(h->b32, 3 * n) && h->get(h->r32, 3 * n) && h->get(h->e32, 3 * n) && h->get(h->fr, 3 * n) &&
@@ -564,7 +566,8 @@ bool alloc_device(emu_handle* h, int64_t nnz) {
   const int64_t gpart = std::max<int64_t>(h->grid_tet * (int64_t)kLsNV, 256 * (int64_t)(2 * h->sms + 1));
   ok = ok && h->get(h->part_grad, gpart) && h->get(h->part_dir, h->grid_tet + 1) && h->get(h->part_ls, (h->grid_tet + kBoneLsBlocks) * kLsNV) &&
        h->get(h->part_pcg, std::max<int64_t>(pcg_part, 256 * (int64_t)(2 * h->sms + 1))) &&
-       h->get(h->cpart, std::max<int64_t>(h->grid_syrk, kTcBlocksPerSM * (int64_t)h->sms) * (kCapEntries + kK)) && h->get(h->z, kK) && h->get(h->cfull, kCapEntries + kK) && h->get(h->small, 256) &&
+       h->get(h->cpart, std::max<int64_t>(h->grid_syrk, std::max(kTcBlocksPerSM, kSyrk05BlocksPerSM) * (int64_t)h->sms) *
+                            (kCapEntries + kK)) && h->get(h->z, kK) && h->get(h->cfull, kCapEntries + kK) && h->get(h->small, 256) &&
        h->get(h->sc, 1) && h->get(h->bar, 1);
   if (h->mixed) ok = ok && h->get(h->val32, nnz) && h->get(h->ldinv32, n);
   ok = ok && h->get(h->rowptr, n + 1) && h->get(h->col, nnz) && h->get(h->val, nnz) && h->get(h->ldinv, n) &&
@@ -922,6 +925,8 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     delete h;
     return fail(EMU_ERR_CUDA, "cudaFuncSetAttribute failed");
   }
+  // the tcgen05 capacitance kernel where its bulk copies can run (else mma.sync)
+  h->syrk05 = h->mixed && make_syrk05_maps(h->margs(), &h->syrk05_maps) && prepare_syrk05() == cudaSuccess;
   // barrier words of the FP32 CG start at zero (every launch leaves them so)
   if (h->sync32 && cudaMemsetAsync(h->sync32, 0, 96 * sizeof(unsigned), h->st) != cudaSuccess) {
     h->release();
@@ -948,7 +953,8 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     };
     std::vector<float> Df = f32(Dinv), Vf = f32(V), cf = f32(cv), wf = f32(wv), muf = f32(mu), lf = f32(lam),
                        uf = f32(uv), valf = f32(valv), ldf = f32(ldinv);
-    std::vector<float> zf(m, 0.f);
+    std::vector<float> zf(m, 0.f), swf(m);
+    for (int64_t i = 0; i < m; ++i) swf[i] = (float)std::sqrt(wv[i]);
     // E0_i = D_m D_m^-1 - I with the rounded D_m^-1 (FP64 arithmetic)
     std::vector<float> e0f(9 * m);
     for (int64_t i = 0; i < m; ++i) {
@@ -961,7 +967,8 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
         }
     }
     ok = up(h->E0, e0f.data(), 36 * m) && up(h->Qrest, Q, 24 * n) && up(h->Dinv32, Df.data(), 36 * m) && up(h->V32, Vf.data(), 4 * m) && up(h->c32, cf.data(), 4 * m) &&
-         up(h->w32, wf.data(), 4 * m) && up(h->mu32, muf.data(), 4 * m) && up(h->lam32, lf.data(), 4 * m) &&
+         up(h->w32, wf.data(), 4 * m) && up(h->sw32, swf.data(), 4 * m) && up(h->mu32, muf.data(), 4 * m) &&
+         up(h->lam32, lf.data(), 4 * m) &&
          up(h->u32, uf.data(), 12 * m) && up(h->ka32, zf.data(), 4 * m) && up(h->val32, valf.data(), 4 * nnz) &&
          up(h->ldinv32, ldf.data(), 4 * n) && cudaStreamSynchronize(h->st) == cudaSuccess;
     if (ok && h->cg_part) {
@@ -1119,7 +1126,10 @@ int enqueue_step(emu_handle* h) {
   // Woodbury direction (Eqs. 9-12)
   h->ph_begin();
   int syrk_blocks = h->grid_syrk;
-  if (h->mixed) {
+  if (h->mixed && h->syrk05) {
+    syrk_blocks = syrk05_grid(h->m, h->sms);
+    launch_syrk05(am, h->syrk05_maps, syrk_blocks, h->cpart, h->st);
+  } else if (h->mixed) {
     syrk_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (h->m + 31) / 32), kTcBlocksPerSM * (int64_t)h->sms);
     launch_syrk_tc(am, syrk_blocks, h->cpart, h->st);
   } else {
@@ -1743,6 +1753,67 @@ int emu_check_bounded_wait(int64_t wait_ns, void* stream) {
   cudaFree(buf);
   if (e != cudaSuccess) return fail(EMU_ERR_CUDA, std::string("emu_check_bounded_wait: ") + cudaGetErrorString(e));
   if (timed_out) return fail(EMU_ERR_TIMEOUT, "the check's grid-barrier wait ran out after its limit (as designed)");
+  return EMU_OK;
+}
+
+int emu_eval_capacitance(int64_t m, const float* U, const float* gamma, const float* y, const float* w,
+                         int32_t kernel, double* C, double* By, void* stream) {
+  if (m <= 0 || m > (int64_t)1 << 28 || !U || !gamma || !y || !w || !C || !By || kernel < 0 || kernel > 2)
+    return fail(EMU_ERR_INVALID_ARG, "bad arguments");
+  if (kernel == 1 && m % 4 != 0) return fail(EMU_ERR_INVALID_ARG, "the tcgen05 kernel needs m % 4 == 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  EMU_CK(cudaGetDevice(&dev));
+  EMU_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  EMU_CK(prepare_syrk_tc());
+  EMU_CK(prepare_syrk05());
+  const int64_t rows = 54 + 48 + 9 + 2;  // U, gamma, y, w, sqrt(w)
+  float* dbuf = nullptr;
+  double* cpart = nullptr;
+  const int grid_max = std::max(kTcBlocksPerSM, kSyrk05BlocksPerSM) * sms;
+  EMU_CK(cudaMalloc(&dbuf, sizeof(float) * rows * m));
+  cudaError_t e = cudaMalloc(&cpart, sizeof(double) * (size_t)grid_max * (kCapEntries + kK));
+  MixArgs a{};
+  a.m = m;
+  a.Uw = dbuf;
+  a.gam = dbuf + 54 * m;
+  a.y = dbuf + 102 * m;
+  a.w = dbuf + 111 * m;
+  a.sw = dbuf + 112 * m;
+  std::vector<float> swh(m);
+  for (int64_t i = 0; i < m; ++i) swh[i] = (float)std::sqrt((double)std::max(w[i], 0.f));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dbuf + 112 * m, swh.data(), sizeof(float) * m, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dbuf, U, sizeof(float) * 54 * m, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dbuf + 54 * m, gamma, sizeof(float) * 48 * m, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dbuf + 102 * m, y, sizeof(float) * 9 * m, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dbuf + 111 * m, w, sizeof(float) * m, cudaMemcpyHostToDevice, st);
+  Syrk05Maps maps;
+  const bool use05 = (kernel == 1 || kernel == 0) && make_syrk05_maps(a, &maps);
+  if (kernel == 1 && !use05 && e == cudaSuccess) e = cudaErrorNotSupported;
+  int grid = 0;
+  if (use05) {
+    grid = syrk05_grid(m, sms);
+    if (e == cudaSuccess) launch_syrk05(a, maps, grid, cpart, st);
+  } else {
+    grid = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 31) / 32), kTcBlocksPerSM * (int64_t)sms);
+    if (e == cudaSuccess) launch_syrk_tc(a, grid, cpart, st);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  std::vector<double> part((size_t)grid * (kCapEntries + kK));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(part.data(), cpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dbuf);
+  cudaFree(cpart);
+  if (e != cudaSuccess) return fail(EMU_ERR_CUDA, std::string("emu_eval_capacitance: ") + cudaGetErrorString(e));
+  for (int k = 0; k < kCapEntries + kK; ++k) {
+    double acc = 0.0;
+    for (int b = 0; b < grid; ++b) acc += part[(size_t)k * grid + b];
+    if (k < kCapEntries)
+      C[k] = acc;
+    else
+      By[k - kCapEntries] = acc;
+  }
   return EMU_OK;
 }
 

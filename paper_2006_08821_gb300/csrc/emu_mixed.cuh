@@ -19,6 +19,7 @@ struct MixArgs {
   const float* V;      // m
   const float* c;      // m  alpha w
   const float* w;      // m
+  const float* sw = nullptr;  // m: sqrt(w), for the tcgen05 capacitance kernel
   const float* mu;     // m
   const float* lam;    // m
   const float* ka;     // m  kappa a
