@@ -136,6 +136,11 @@ def algorithmic_bytes(phase, mixed, m, n, nnz, cg_iters):
 # also launches the per-vertex position update, the mixed gradient phase the
 # per-vertex split of the displacement)
 PER_TET_KERNELS = {"grad": 0.5, "syrk": 1.0, "dir": 1.0, "ls": 1.0, "update": 0.5}
+PER_TET_KERNELS_FP64 = {"grad": 1.0, "syrk": 1.0, "dir": 1.0, "ls": 1.0, "update": 0.5}
+
+
+def per_tet_kernels(mixed):
+    return PER_TET_KERNELS if mixed else PER_TET_KERNELS_FP64
 
 
 def per_tet_fractions(prof, mixed, m, n, nnz, peak, traffic_table=None):
@@ -143,7 +148,7 @@ def per_tet_fractions(prof, mixed, m, n, nnz, peak, traffic_table=None):
     CUDA-event duration, against the HBM peak; with the kernel's ncu DRAM
     bytes per launch beside it where a capture of the unchanged kernel exists."""
     out = {}
-    for name, per in PER_TET_KERNELS.items():
+    for name, per in per_tet_kernels(mixed).items():
         ms, nl = prof.get(name, (0.0, 0))
         if nl <= 0 or ms <= 0:
             continue
@@ -199,7 +204,7 @@ def whole_iteration(prof, mixed, m, n, nnz, cg_total, iters, peak, value):
     if iters <= 0:
         return None
     b = 0.0
-    for name, per in PER_TET_KERNELS.items():
+    for name, per in per_tet_kernels(mixed).items():
         ms, nl = prof.get(name, (0.0, 0))
         b += algorithmic_bytes(name, mixed, m, n, nnz, 0.0) * nl * per
     b += algorithmic_bytes("pcg", mixed, m, n, nnz, cg_total)
