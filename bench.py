@@ -56,7 +56,7 @@ FALLBACK_HBM_GBS = 6800.0
 # capture of the unchanged kernel (summaries under profiles/); None once the
 # kernel has changed since.
 NCU_TRAFFIC = {
-    "pcg": (20.60e6, "profiles/pcg32p_kernel_mtu401920.md"),
+    "pcg": (18.21e6, "profiles/pcg32p_kernel_mtu401920.md"),
     "grad": (124.19e6, "profiles/k_grad_m_mtu401920.md"),
     "dir": (230.63e6, "profiles/k_dir_m_mtu401920.md"),
     "ls": (82.91e6, "profiles/k_ls_m_mtu401920.md"),
