@@ -16,6 +16,7 @@ from .meshes import (  # noqa: F401
     request_stream,
     single_tet,
     arm_assembly,
+    gravity_forces,
     MUSCLE,
     TENDON,
     BONE,

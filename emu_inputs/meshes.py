@@ -59,6 +59,8 @@ class MeshSpec:
     # (b1, b2), "point" (3,) metres, and for a hinge "axis" (3,) unit and
     # "half_length" (metres; the hinge's two points are point +- half_length axis)
     joints: list | None = None
+    # constant external force per vertex (n, 3), newtons (e.g. gravity_forces)
+    f_ext: np.ndarray | None = None
     meta: dict = dataclasses.field(default_factory=dict)
 
     @property
@@ -375,3 +377,15 @@ def arm_assembly(bone_w=12, bone_len=58, r0=32.0, gap_x=1, h=2.5e-3, frames=120,
         joints=[hinge],
         meta=dict(nx=nx, ny=nyc, nz=nz, h=h, bone_w=bw, bone_len=L, r0=r0, gap_x=gap_x),
     )
+
+
+def gravity_forces(mesh: MeshSpec, density=1060.0, g=(0.0, 0.0, -9.81)) -> np.ndarray:
+    """Per-vertex gravity on a Kuhn-grid mesh: every tet of a grid of cubes
+    of edge h (``mesh.meta["h"]``) has the mass density * h^3 / 6, split
+    equally over its four corners, times the acceleration g. (n, 3).
+    Soft tissue density (1060 kg/m^3) by default."""
+    h = float(mesh.meta["h"])
+    T = np.asarray(mesh.tets, dtype=np.int64)
+    mass = np.zeros(mesh.n_verts)
+    np.add.at(mass, T.ravel(), density * h ** 3 / 24.0)
+    return mass[:, None] * np.asarray(g, dtype=np.float64)[None, :]

@@ -72,6 +72,8 @@ class BoneOracle:
                  modes: str = "eigsh"):
         if not (eps_bone < 0.0 and eps_joint_final < 0.0):
             raise ValueError("the Newton bone slack and the final joint slack must be negative")
+        if getattr(mesh, "f_ext", None) is not None:
+            raise ValueError("external forces (Sec. 3.4) are not combined with bones here")
         base = EmuOracle(mesh, params, modes="none", factor=False)
         self.base = base
         self.p = base.p

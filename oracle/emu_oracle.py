@@ -305,6 +305,19 @@ class EmuOracle:
         self.K = (self.G_f.T @ sp.diags(self.w9) @ self.G_f).tocsc()
         self._lu = spla.splu(self.K) if factor else None
         self.Gc_qc = self.G_c @ self.q_c
+
+        # Sec. 3.4, Eq. external-forces: a constant per-vertex force f does
+        # the work q*(F)^T f; since q* is affine in F, its F-gradient is the
+        # generalized force nu = W G_f K^-1 f_free (per tet 3 x 3), and the
+        # energy gains -<F, nu> (pinned vertices take their force).
+        self.nu = np.zeros((self.m, 3, 3))
+        f_ext = getattr(mesh, "f_ext", None)
+        if f_ext is not None:
+            if self._lu is None:
+                raise ValueError("external forces need the factorisation of Eq. 4")
+            f = np.asarray(f_ext, dtype=np.float64).reshape(-1)
+            x = self._lu.solve(f[self.free_dofs])
+            self.nu = (self.w9 * (self.G_f @ x)).reshape(self.m, 3, 3)
         if modes == "none":
             self.k = 0
             return
@@ -349,13 +362,14 @@ class EmuOracle:
         ka = self.kappa * a
         Psi = np.sum(self.V * psi(F, self.mu, self.lam, ka, self.u))
         D = self.deformation_gradients(q) - F
-        return Psi + 0.5 * self.alpha * np.sum(self.w * np.einsum("ijk,ijk->i", D, D))
+        return Psi + 0.5 * self.alpha * np.sum(self.w * np.einsum("ijk,ijk->i", D, D)) - float(np.sum(F * self.nu))
 
     def gradient(self, F, q, a):
-        """dE/dF = V Psi'(F) + alpha w (F - G q*(F)), (m,3,3)."""
+        """dE/dF = V Psi'(F) + alpha w (F - G q*(F)) - nu, (m,3,3)."""
         ka = self.kappa * a
         P = dpsi(F, self.mu, self.lam, ka, self.u)
-        return self.V[:, None, None] * P + (self.alpha * self.w)[:, None, None] * (F - self.deformation_gradients(q))
+        return (self.V[:, None, None] * P + (self.alpha * self.w)[:, None, None] * (F - self.deformation_gradients(q))
+                - self.nu)
 
     def residual_normaliser(self, a, F_start=None):
         """||dE/dF|| at F = I, q = q*(I) (the unloaded state), the scale of
@@ -398,7 +412,7 @@ class EmuOracle:
         dD = (self.deformation_gradients(dq) - d).reshape(self.m, 9)
         dC = 0.5 * self.alpha * np.sum(self.w * (2.0 * sigma * np.einsum("ij,ij->i", D, dD)
                                                  + sigma**2 * np.einsum("ij,ij->i", dD, dD)))
-        return dP + dC
+        return dP + dC - sigma * float(np.sum(d * self.nu))
 
     # --- Algorithm 1 (Newton part) ------------------------------------------
     def solve(self, a, F0=None, tol=None, max_newton=None, record=False):

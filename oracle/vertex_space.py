@@ -11,8 +11,9 @@
    different algorithm from Algorithm 1: no low-rank Hessian and no
    Woodbury step.
 
-2. ``fem_solve``: plain finite elements, min_q sum_i V_i Psi(G_i q). This is
-   the alpha -> infinity limit that Sec. 3.7 compares against.
+2. ``fem_solve``: plain finite elements, min_q sum_i V_i Psi(G_i q) - q^T f
+   (f the mesh's constant per-vertex force, if any). This is the
+   alpha -> infinity limit that Sec. 3.7 compares against.
 
 Both reuse only the per-tet energy functions (themselves pinned by finite
 differences) and the sparse G of Eq. 2.
@@ -97,14 +98,18 @@ def fem_solve(o: EmuOracle, a, tol=1e-12, max_iter=200):
     q = o.Q.reshape(-1).copy()
     q[o.fixed_dofs] = o.q_c
 
+    f_ext = getattr(o.mesh, "f_ext", None)
+    f_free = (np.zeros(o.free_dofs.size) if f_ext is None
+              else np.asarray(f_ext, dtype=np.float64).reshape(-1)[o.free_dofs])
+
     def energy(q):
-        return np.sum(o.V * psi(o.deformation_gradients(q), o.mu, o.lam, ka, o.u))
+        return np.sum(o.V * psi(o.deformation_gradients(q), o.mu, o.lam, ka, o.u)) - float(q[o.free_dofs] @ f_free)
 
     g_ref = None
     for _ in range(max_iter):
         F = o.deformation_gradients(q)
         P = o.V[:, None, None] * dpsi(F, o.mu, o.lam, ka, o.u)
-        grad = o.G_f.T @ P.reshape(-1)
+        grad = o.G_f.T @ P.reshape(-1) - f_free
         gn = np.linalg.norm(grad)
         if g_ref is None:
             g_ref = max(gn, 1e-300)
