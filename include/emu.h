@@ -232,6 +232,20 @@ int emu_set_activation(emu_handle* h, const double* a, int64_t count);
 /* Same as emu_set_activation with ``a`` a device pointer (n_tets float64). */
 int emu_set_activation_device(emu_handle* h, const double* a_device, int64_t count);
 
+/* Constant external forces (Sec. 3.4, Eq. external-forces), such as gravity:
+ * f is a host array of n_verts x 3 newtons (per vertex, row-major), or NULL
+ * to remove them. The force does the work q*(F)^T f through the coupling
+ * solve of Eq. 4, so on the deformation gradients it acts as the generalized
+ * force nu = W G K^-1 f (forces on pinned vertices are taken by the pins),
+ * computed here once on the device (an FP64 CG solve to 1e-13 and a per-tet
+ * kernel): every solve then minimises E(F) - <F, nu>. The handle keeps nu
+ * (9 n_tets doubles, plus as many floats on the mixed path, allocated on
+ * the first call, not counted by emu_required_bytes) until the next call.
+ * EMU_ERR_NOT_IMPLEMENTED on meshes with bones; EMU_ERR_INVALID_ARG for a
+ * count other than n_verts or a non-finite value; EMU_ERR_PCG if the solve
+ * does not converge. Synchronous. */
+int emu_set_external_forces(emu_handle* h, const double* f, int64_t n_verts);
+
 /* Runs Newton iterations from the resident state (warm start) until the
  * relative residual reaches tol_rel_residual (Algorithm 1, Newton part).
  * ``stats`` may be NULL. Returns EMU_ERR_NOT_CONVERGED when max_newton is

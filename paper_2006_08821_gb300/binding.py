@@ -39,7 +39,7 @@ EXPORTED = [
     "emu_eval_stretch_terms", "emu_eval_polar", "emu_set_profiling", "emu_get_profile",
     "emu_acap_solve_noalloc", "emu_batch_solve", "emu_required_bytes", "emu_server_create",
     "emu_server_submit", "emu_server_poll", "emu_server_result", "emu_server_destroy", "emu_check_bounded_wait",
-    "emu_eval_capacitance",
+    "emu_eval_capacitance", "emu_set_external_forces",
 ]
 
 PHASES = ["rhs", "assemble", "pcg", "grad", "syrk", "small", "dir", "ls", "update"]
@@ -158,6 +158,7 @@ def load_library(path: str = LIB_PATH):
     lib.emu_create.argtypes = [P(emu_mesh_desc), P(emu_params), P(emu_allocator), C.c_void_p, P(C.c_void_p)]
     lib.emu_destroy.argtypes = [C.c_void_p]
     lib.emu_set_activation.argtypes = [C.c_void_p, P(C.c_double), C.c_int64]
+    lib.emu_set_external_forces.argtypes = [C.c_void_p, P(C.c_double), C.c_int64]
     lib.emu_set_activation_device.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
     lib.emu_solve_quasistatic.argtypes = [C.c_void_p, P(emu_solve_stats)]
     lib.emu_get_positions.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
@@ -322,6 +323,8 @@ class Solver:
         cp = self.params.to_c()
         _check(self.lib.emu_create(C.byref(d), C.byref(cp), ap, st, C.byref(h)), self.lib)
         self.handle = h
+        if getattr(mesh, "f_ext", None) is not None:  # constant per-vertex forces of the mesh
+            self.set_external_forces(mesh.f_ext)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -337,6 +340,16 @@ class Solver:
     def set_activation(self, a):
         a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (self.n_tets,)))
         _check(self.lib.emu_set_activation(self.handle, _dptr(a, C.c_double), a.shape[0]), self.lib)
+
+    def set_external_forces(self, f):
+        """Constant per-vertex forces (n_verts, 3), e.g. gravity; None removes them."""
+        if f is None:
+            _check(self.lib.emu_set_external_forces(self.handle, None, 0), self.lib)
+            return
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64))
+        if f.shape != (self.n_verts, 3):
+            raise ValueError("forces must have shape (n_verts, 3)")
+        _check(self.lib.emu_set_external_forces(self.handle, _dptr(f, C.c_double), f.shape[0]), self.lib)
 
     def set_activation_device(self, a_dev_ptr: int):
         _check(self.lib.emu_set_activation_device(self.handle, C.c_void_p(a_dev_ptr), self.n_tets), self.lib)

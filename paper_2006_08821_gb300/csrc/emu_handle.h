@@ -86,6 +86,10 @@ struct emu_handle {
   float* aphi32 = nullptr;                // rows of L Phi for the pipelined FP32 CG
   bool aphi_ready = false;
   bool syrk05 = false;  // capacitance on the tcgen05 kernel (else mma.sync)
+  // constant external force (Sec. 3.4): generalized force nu = W G K^-1 f
+  bool has_force = false;
+  double* nu64 = nullptr;  // 9m (allocated on first use)
+  float* nu32 = nullptr;   // 9m, mixed path
   Syrk05Maps syrk05_maps;  // its tensor maps of Uw32, gam32, y32, sw32
   float* sw32 = nullptr;    // sqrt of the ACAP weights (m)
   int grid32 = 0, rpt32 = 0;
@@ -350,6 +354,7 @@ struct emu_handle {
     a.partials = part_grad;
     a.tkind = tkind;
     a.bone_st = bst;
+    a.nu = has_force ? nu32 : nullptr;
     return a;
   }
 };
@@ -382,6 +387,7 @@ template <> inline TetArgs<double> emu_handle::args<double>() {
   a.partials = part_grad;
   a.tkind = tkind;
   a.bone_st = bst;
+  a.nu = has_force ? nu64 : nullptr;
   return a;
 }
 template <> inline TetArgs<float> emu_handle::args<float>() {
@@ -412,6 +418,7 @@ template <> inline TetArgs<float> emu_handle::args<float>() {
   a.partials = part_grad;
   a.tkind = tkind;
   a.bone_st = bst;
+  a.nu = has_force ? nu64 : nullptr;
   return a;
 }
 

@@ -1039,6 +1039,49 @@ int emu_set_activation(emu_handle* h, const double* a, int64_t count) {
   return EMU_OK;
 }
 
+int emu_set_external_forces(emu_handle* h, const double* f, int64_t n_verts) {
+  if (!h) return fail(EMU_ERR_INVALID_ARG, "NULL handle");
+  if (!f) {
+    h->has_force = false;
+  } else {
+    if (n_verts != h->n) return fail(EMU_ERR_INVALID_ARG, "n_verts must equal the mesh's vertex count");
+    if (h->has_bones) return fail(EMU_ERR_NOT_IMPLEMENTED, "external forces are not combined with bones");
+    const int64_t n = h->n, m = h->m;
+    for (int64_t k = 0; k < 3 * n; ++k)
+      if (!std::isfinite(f[k])) return fail(EMU_ERR_INVALID_ARG, "forces must be finite");
+    if (!h->nu64 && !h->get(h->nu64, 9 * m)) return fail(EMU_ERR_OOM, "device allocation failed");
+    if (h->mixed && !h->nu32 && !h->get(h->nu32, 9 * m)) return fail(EMU_ERR_OOM, "device allocation failed");
+    // right-hand side: f on the free rows; the pinned rows are identity rows with 0
+    std::vector<uint8_t> fixed(n);
+    EMU_CK(cudaMemcpyAsync(fixed.data(), h->is_fixed, n, cudaMemcpyDeviceToHost, h->st));
+    EMU_CK(cudaStreamSynchronize(h->st));
+    std::vector<double> fb(f, f + 3 * n);
+    for (int64_t v = 0; v < n; ++v)
+      if (fixed[v]) fb[3 * v] = fb[3 * v + 1] = fb[3 * v + 2] = 0.0;
+    double* rhs = h->b;
+    double* x = h->b + 3 * n;
+    DevScalars init;
+    memset(&init, 0, sizeof(init));
+    EMU_CK(cudaMemcpyAsync(h->sc, &init, sizeof(init), cudaMemcpyHostToDevice, h->st));
+    EMU_CK(cudaMemcpyAsync(rhs, fb.data(), 24 * n, cudaMemcpyHostToDevice, h->st));
+    EMU_CK(cudaMemsetAsync(x, 0, 24 * n, h->st));
+    EMU_CK(launch_pcg<double>(3, h->pcg64(rhs, x, 1e-13), h->grid_pcg3, h->st));
+    launch_nu(m, h->tet, h->Dinv, h->w, x, h->nu64, h->mixed ? h->nu32 : nullptr, h->st);
+    EMU_CK(cudaGetLastError());
+    DevScalars out;
+    EMU_CK(cudaMemcpyAsync(&out, h->sc, sizeof(out), cudaMemcpyDeviceToHost, h->st));
+    EMU_CK(cudaStreamSynchronize(h->st));
+    if (out.barrier_timeout) return fail(EMU_ERR_TIMEOUT, "grid barrier timed out in the force solve");
+    if (out.pcg_fail) return fail(EMU_ERR_PCG, "the solve for the generalized force did not converge");
+    h->has_force = true;
+  }
+  // g(I) changes; the captured iteration graph holds the old kernel arguments
+  h->gref_valid = false;
+  if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
+  h->iter_exec = nullptr;
+  return EMU_OK;
+}
+
 int emu_set_activation_device(emu_handle* h, const double* a_device, int64_t count) {
   if (!h || !a_device) return fail(EMU_ERR_INVALID_ARG, "NULL argument");
   if (count != h->m) return fail(EMU_ERR_INVALID_ARG, "activation count must equal n_tets");

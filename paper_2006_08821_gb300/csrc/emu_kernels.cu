@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(128) k_grad(TetArgs<TW> a) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       g[k] = md.V * RP[k] + c * (F[k] - A[k]);
+      if (a.nu) g[k] -= a.nu[k * m + i];  // external force (Sec. 3.4)
       gg += g[k] * g[k];
       a.g[k * m + i] = g[k];
     }
@@ -552,6 +553,10 @@ __global__ void __launch_bounds__(128) k_ls(TetArgs<TW> a, double rho) {
     }
     const double Fudu = Fu[0] * du[0] + Fu[1] * du[1] + Fu[2] * du[2];
     const double dudu = du[0] * du[0] + du[1] * du[1] + du[2] * du[2];
+    double dnu = 0.0;  // <d, nu>: the external work's change is -sigma <d, nu>
+    if (a.nu)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) dnu += d[k] * a.nu[k * m + i];
     double sig = s0;
 #pragma unroll
     for (int j = 0; j < kLsTrials; ++j) {
@@ -562,7 +567,7 @@ __global__ void __launch_bounds__(128) k_ls(TetArgs<TW> a, double rho) {
         const double dl = log1p(x);
         const double nh = sig * FFd + 0.5 * sig * sig * dd - sig * sig * e2 - sig * sig * sig * detM + x_minus_log1p(x);
         dpsi = md.mu * nh + 0.5 * md.lam * dl * (2.0 * lnJ + dl) + md.ka * (2.0 * sig * Fudu + sig * sig * dudu);
-        dpsi *= md.V;
+        dpsi = dpsi * md.V - sig * dnu;
       } else {
         dpsi = 1e300;
       }
@@ -654,7 +659,8 @@ __global__ void __launch_bounds__(128) k_gref(TetArgs<double> a, const double* q
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) {
-        const double gv = V * 2.0 * ka * u[r] * u[cc] + c * ((r == cc ? 1.0 : 0.0) - A[3 * r + cc]);
+        double gv = V * 2.0 * ka * u[r] * u[cc] + c * ((r == cc ? 1.0 : 0.0) - A[3 * r + cc]);
+        if (a.nu) gv -= a.nu[(3 * r + cc) * m + i];
         gg += gv * gv;
       }
     acc[0] += gg;
@@ -801,6 +807,31 @@ void launch_gamma(int64_t m, const int4* tet, const double* Dinv, const double* 
   int grid = (int)((m + 255) / 256);
   if (grid < 1) grid = 1;
   k_gamma<TW><<<grid, 256, 0, st>>>(m, tet, Dinv, X, gam);
+}
+
+// ------------------------------------------------------- external force ---
+__global__ void __launch_bounds__(256) k_nu(int64_t m, const int4* __restrict__ tet, const double* __restrict__ Dinv,
+                                            const double* __restrict__ w, const double* __restrict__ x,
+                                            double* __restrict__ nu64, float* __restrict__ nu32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double D[9], A[9];
+    load_dinv(Dinv, m, i, D);
+    gather_defgrad(x, tet[i], D, A);
+    const double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double v = wi * A[k];
+      nu64[k * m + i] = v;
+      if (nu32) nu32[k * m + i] = (float)v;
+    }
+  }
+}
+
+void launch_nu(int64_t m, const int4* tet, const double* Dinv, const double* w, const double* x, double* nu64,
+               float* nu32, cudaStream_t st) {
+  int grid = (int)((m + 255) / 256);
+  if (grid < 1) grid = 1;
+  k_nu<<<grid, 256, 0, st>>>(m, tet, Dinv, w, x, nu64, nu32);
 }
 
 // ------------------------------------------------------------ element API --

@@ -37,6 +37,7 @@ template <typename TW> struct TetArgs {
   double* partials;     // per-block partial sums
   const int32_t* tkind = nullptr;    // bones: kind of each tet (null without bones)
   const double* bone_st = nullptr;   // bones: free bones' iteration state
+  const double* nu = nullptr;        // 9m generalized external force (Sec. 3.4), null without one
 };
 
 void launch_rhs_from_state(const TetArgs<double>& a, int grid, cudaStream_t st);
@@ -52,6 +53,10 @@ void launch_assemble(int64_t n, const int32_t* slot_ptr, const int32_t* slot_idx
                      const double* bfix, const uint8_t* is_fixed, const double* qfix, int mode, double* b,
                      cudaStream_t st);
 void launch_update_verts(int64_t n, const DevScalars* sc, const double* dq, double* q, cudaStream_t st);
+// Generalized external force of Sec. 3.4: nu_i = w_i G_i x (x = K^-1 f, 3n),
+// written component-major to nu64 (9m) and, when non-null, nu32.
+void launch_nu(int64_t m, const int4* tet, const double* Dinv, const double* w, const double* x, double* nu64,
+               float* nu32, cudaStream_t st);
 
 // Single-block reducers.
 void launch_reduce_grad(const double* partials, int nblk, DevScalars* sc, double* By, double* gsum,

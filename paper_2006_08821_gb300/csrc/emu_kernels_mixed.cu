@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(128, 4) k_grad_m(MixArgs a) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       g[k] = mat.V * RP[k] - c * Dk[k];
+      if (a.nu) g[k] -= a.nu[k * m + i];  // external force (Sec. 3.4)
       gg = fmaf(g[k], g[k], gg);
       a.g[k * m + i] = g[k];
     }
@@ -554,6 +555,10 @@ __global__ void __launch_bounds__(128) k_ls_m(MixArgs a, LsSelect sel) {
     }
     const float Fudu = Fu[0] * du[0] + Fu[1] * du[1] + Fu[2] * du[2];
     const float dudu = du[0] * du[0] + du[1] * du[1] + du[2] * du[2];
+    float dnu = 0.f;  // <d, nu>: the external work's change is -sigma <d, nu>
+    if (a.nu)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) dnu += d[k] * a.nu[k * m + i];
     float sig = s0;
 #pragma unroll
     for (int j = 0; j < kLsTrials; ++j) {
@@ -565,7 +570,7 @@ __global__ void __launch_bounds__(128) k_ls_m(MixArgs a, LsSelect sel) {
                                   x_minus_log1p(x));
         const float vol = 0.5f * md.lam * dl * (2.f * st.lnJ + dl);
         const float fib = md.ka * (2.f * sig * Fudu + sig * sig * dudu);
-        dpsi = md.V * (nh + vol + fib);
+        dpsi = md.V * (nh + vol + fib) - sig * dnu;
       } else {
         dpsi = INFINITY;  // an inverted trial: never accepted
       }

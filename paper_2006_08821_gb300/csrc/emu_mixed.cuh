@@ -51,6 +51,7 @@ struct MixArgs {
   // state (their directions at kBoneD)
   const int32_t* tkind = nullptr;
   const double* bone_st = nullptr;
+  const float* nu = nullptr;  // 9m generalized external force (Sec. 3.4), null without one
 };
 
 void launch_grad_mixed(const MixArgs& a, int grid, cudaStream_t st);
