@@ -388,6 +388,22 @@ int emu_eval_stretch_terms(const double* s, const double* params, int64_t n, int
  * device memory for the duration of the call and synchronises ``stream``. */
 int emu_check_bounded_wait(int64_t wait_ns, void* stream);
 
+/* Fiber directions from the heat equation (Sec. 3.6, "Modeling"): the P1
+ * harmonic field f (the discrete Laplace equation with the rest-volume
+ * weighted Laplacian L_ab = sum_i V_i gradN_a . gradN_b) with f = -1 on the
+ * origin vertices and +1 on the insertion vertices, then per tet the unit
+ * fiber u_i = grad f_i / |grad f_i| (the zero vector where the gradient
+ * vanishes). rest_pos: n_verts x 3; tets: n_tets x 4 (either orientation);
+ * origin, insertion: vertex indices (disjoint, at least one each); fibers:
+ * host output, n_tets x 3 (row-major). The solve runs on the device (FP64 CG
+ * to a relative residual of 1e-13). Allocates device memory for the call and
+ * synchronises ``stream``. EMU_ERR_INVALID_ARG for bad indices or a
+ * degenerate tet; EMU_ERR_PCG if the solve does not converge. Use the result
+ * as emu_mesh_desc.fiber_dir. */
+int emu_fiber_field(int64_t n_verts, const double* rest_pos, int64_t n_tets, const int32_t* tets,
+                    const int32_t* origin, int64_t n_origin, const int32_t* insertion, int64_t n_insertion,
+                    double* fibers, void* stream);
+
 /* The capacitance of the Woodbury direction in its Gram form (Eq. 12) from
  * per-tet factors, on the device kernels of the mixed path:
  *   C  = sum_i Yh_i^T Yh_i,  Yh_i = sqrt(w_i) U_i (I3 (x) Gamma_i)   (48 x 48)

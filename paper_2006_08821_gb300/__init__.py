@@ -18,6 +18,7 @@ from .binding import (  # noqa: F401
     TorchAllocator,
     default_params,
     eval_capacitance,
+    fiber_field,
     eval_polar,
     eval_stretch_terms,
     load_library,

@@ -39,7 +39,7 @@ EXPORTED = [
     "emu_eval_stretch_terms", "emu_eval_polar", "emu_set_profiling", "emu_get_profile",
     "emu_acap_solve_noalloc", "emu_batch_solve", "emu_required_bytes", "emu_server_create",
     "emu_server_submit", "emu_server_poll", "emu_server_result", "emu_server_destroy", "emu_check_bounded_wait",
-    "emu_eval_capacitance", "emu_set_external_forces",
+    "emu_eval_capacitance", "emu_set_external_forces", "emu_fiber_field",
 ]
 
 PHASES = ["rhs", "assemble", "pcg", "grad", "syrk", "small", "dir", "ls", "update"]
@@ -159,6 +159,8 @@ def load_library(path: str = LIB_PATH):
     lib.emu_destroy.argtypes = [C.c_void_p]
     lib.emu_set_activation.argtypes = [C.c_void_p, P(C.c_double), C.c_int64]
     lib.emu_set_external_forces.argtypes = [C.c_void_p, P(C.c_double), C.c_int64]
+    lib.emu_fiber_field.argtypes = [C.c_int64, P(C.c_double), C.c_int64, P(C.c_int32), P(C.c_int32), C.c_int64,
+                                    P(C.c_int32), C.c_int64, P(C.c_double), C.c_void_p]
     lib.emu_set_activation_device.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
     lib.emu_solve_quasistatic.argtypes = [C.c_void_p, P(emu_solve_stats)]
     lib.emu_get_positions.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
@@ -499,6 +501,21 @@ def check_bounded_wait(wait_ns: int, stream=0) -> int:
     (EMU_ERR_TIMEOUT is the expected result)."""
     lib = load_library()
     return lib.emu_check_bounded_wait(int(wait_ns), C.c_void_p(int(stream)) if stream else None)
+
+
+def fiber_field(rest_pos, tets, origin, insertion, stream=0):
+    """emu_fiber_field: unit fiber directions (n_tets, 3) from the heat
+    equation with -1 on ``origin`` and +1 on ``insertion`` vertices."""
+    lib = load_library()
+    Q = np.ascontiguousarray(rest_pos, dtype=np.float64)
+    T = np.ascontiguousarray(tets, dtype=np.int32)
+    o = np.ascontiguousarray(origin, dtype=np.int32)
+    ins = np.ascontiguousarray(insertion, dtype=np.int32)
+    out = np.zeros((T.shape[0], 3))
+    _check(lib.emu_fiber_field(Q.shape[0], _dptr(Q, C.c_double), T.shape[0], _dptr(T, C.c_int32), _dptr(o, C.c_int32),
+                               o.size, _dptr(ins, C.c_int32), ins.size, _dptr(out, C.c_double),
+                               C.c_void_p(int(stream)) if stream else None), lib)
+    return out
 
 
 def eval_capacitance(U, gamma, y, w, kernel=0, stream=0):
