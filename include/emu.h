@@ -388,6 +388,22 @@ int emu_eval_stretch_terms(const double* s, const double* params, int64_t n, int
  * device memory for the duration of the call and synchronises ``stream``. */
 int emu_check_bounded_wait(int64_t wait_ns, void* stream);
 
+/* The alpha heuristic of Sec. 3.7: for alpha_rel = alpha0 * factor^k
+ * (k = 0 .. max_steps - 1, at most 64; the paper starts at 1 and its table
+ * goes by decades) create a solver with *params (NULL: defaults) and that
+ * alpha_rel, solve once from the rest state at ``activation`` (n_tets
+ * values) and tally the Newton iterations; stop at the first count above
+ * jump times the previous one (a solve ending EMU_ERR_NOT_CONVERGED or
+ * EMU_ERR_LINESEARCH counts as such an increase) and return in *alpha_out
+ * the value before it, else the last value tried. newton_iters (may be
+ * NULL; max_steps entries) receives each count (-1: did not converge),
+ * *n_tried the number of solves. Each step builds and destroys a handle on
+ * ``stream`` (the set-up of Eq. 9 included). EMU_ERR_NOT_CONVERGED if the
+ * first value does not converge. */
+int emu_alpha_sweep(const emu_mesh_desc* desc, const emu_params* params, const double* activation, double alpha0,
+                    double factor, int32_t max_steps, double jump, double* alpha_out, int32_t* newton_iters,
+                    int32_t* n_tried, void* stream);
+
 /* Fiber directions from the heat equation (Sec. 3.6, "Modeling"): the P1
  * harmonic field f (the discrete Laplace equation with the rest-volume
  * weighted Laplacian L_ab = sum_i V_i gradN_a . gradN_b) with f = -1 on the

@@ -11,6 +11,7 @@ from .binding import (  # noqa: F401
     Params,
     Server,
     Solver,
+    alpha_sweep,
     batch_solve,
     check_bounded_wait,
     mesh_desc,

@@ -39,7 +39,7 @@ EXPORTED = [
     "emu_eval_stretch_terms", "emu_eval_polar", "emu_set_profiling", "emu_get_profile",
     "emu_acap_solve_noalloc", "emu_batch_solve", "emu_required_bytes", "emu_server_create",
     "emu_server_submit", "emu_server_poll", "emu_server_result", "emu_server_destroy", "emu_check_bounded_wait",
-    "emu_eval_capacitance", "emu_set_external_forces", "emu_fiber_field",
+    "emu_eval_capacitance", "emu_set_external_forces", "emu_fiber_field", "emu_alpha_sweep",
 ]
 
 PHASES = ["rhs", "assemble", "pcg", "grad", "syrk", "small", "dir", "ls", "update"]
@@ -159,6 +159,8 @@ def load_library(path: str = LIB_PATH):
     lib.emu_destroy.argtypes = [C.c_void_p]
     lib.emu_set_activation.argtypes = [C.c_void_p, P(C.c_double), C.c_int64]
     lib.emu_set_external_forces.argtypes = [C.c_void_p, P(C.c_double), C.c_int64]
+    lib.emu_alpha_sweep.argtypes = [P(emu_mesh_desc), P(emu_params), P(C.c_double), C.c_double, C.c_double,
+                                    C.c_int32, C.c_double, P(C.c_double), P(C.c_int32), P(C.c_int32), C.c_void_p]
     lib.emu_fiber_field.argtypes = [C.c_int64, P(C.c_double), C.c_int64, P(C.c_int32), P(C.c_int32), C.c_int64,
                                     P(C.c_int32), C.c_int64, P(C.c_double), C.c_void_p]
     lib.emu_set_activation_device.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
@@ -501,6 +503,24 @@ def check_bounded_wait(wait_ns: int, stream=0) -> int:
     (EMU_ERR_TIMEOUT is the expected result)."""
     lib = load_library()
     return lib.emu_check_bounded_wait(int(wait_ns), C.c_void_p(int(stream)) if stream else None)
+
+
+def alpha_sweep(mesh, activation, params: Params | None = None, alpha0=1.0, factor=10.0, max_steps=6, jump=3.0,
+                stream=0):
+    """emu_alpha_sweep: (chosen alpha_rel, the alpha_rel values tried, their
+    Newton counts, -1 where a solve did not converge)."""
+    lib = load_library()
+    d, keep = mesh_desc(mesh)
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(activation, dtype=np.float64), (mesh.n_tets,)))
+    cp = (params or Params()).to_c()
+    out = C.c_double(0.0)
+    iters = np.full(max_steps, -1, dtype=np.int32)
+    n = C.c_int32(0)
+    _check(lib.emu_alpha_sweep(C.byref(d), C.byref(cp), _dptr(a, C.c_double), alpha0, factor, max_steps, jump,
+                               C.byref(out), _dptr(iters, C.c_int32), C.byref(n),
+                               C.c_void_p(int(stream)) if stream else None), lib)
+    k = int(n.value)
+    return float(out.value), [alpha0 * factor ** i for i in range(k)], [int(x) for x in iters[:k]]
 
 
 def fiber_field(rest_pos, tets, origin, insertion, stream=0):
