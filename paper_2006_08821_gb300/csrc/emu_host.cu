@@ -162,14 +162,14 @@ cudaError_t run_pcg32(emu_handle* h, const float* rhs, float* x, double tol) {
     w.ug = h->ug32;
     w.part = h->part32;
     w.sync = h->sync32;
-    if (tol >= kPipeMinTol && h->aphi_ready && h->cg_part && a.phi && pcg32_pipe_ok(h->rpt32)) {
-      // the partitioned system (b and x stay in vertex order)
+    if (h->cg_part) {
+      // the partitioned system with the block-local preconditioner (b and x
+      // stay in vertex order)
       a.rowptr = h->cg_rowptr;
       a.col = h->cg_col;
       a.val = h->cg_val;
       a.dinv = h->cg_dinv;
-      a.phi = h->cg_phi;
-      w.aphi = h->cg_aphi;
+      a.phi = a.phi ? h->cg_phi : nullptr;
       w.perm = h->cg_perm;
       w.off = h->cg_off;
       w.loc = h->cg_loc;
@@ -180,7 +180,10 @@ cudaError_t run_pcg32(emu_handle* h, const float* rhs, float* x, double tol) {
         w.c1[i] = h->cg_c1[i];
         w.c2[i] = h->cg_c2[i];
       }
-      return launch_pcg32_pipe(a, w, h->grid32, h->rpt32, h->st);
+      if (tol >= kPipeMinTol && h->aphi_ready && a.phi && pcg32_pipe_ok(h->rpt32)) {
+        w.aphi = h->cg_aphi;
+        return launch_pcg32_pipe(a, w, h->grid32, h->rpt32, h->st);
+      }
     }
     return launch_pcg32(a, w, h->grid32, h->rpt32, h->st);
   }

@@ -57,8 +57,9 @@ struct Pcg32Work {
   unsigned* sync;  // 96 words of barrier state, zero before the first launch
                    // (each launch leaves them zero)
   const float* aphi = nullptr;  // n x 16 rows of A Phi (pipelined kernel only)
-  // pipelined kernel only: the system in the row partition of emu_cgpart.h
-  // (args.rowptr/col/val/dinv/phi and aphi permuted; b and x in vertex order)
+  // the system in the row partition of emu_cgpart.h (required by the
+  // pipelined kernel, optional for the plain one): args.rowptr/col/val/dinv/
+  // phi and aphi permuted; b and x in vertex order
   const int32_t* perm = nullptr;  // partition row -> vertex (n)
   const int32_t* off = nullptr;   // grid + 1 row offsets of the blocks' parts
   const uint32_t* loc = nullptr;  // local table: (grid x rpt x lw x 256) words
@@ -70,7 +71,10 @@ struct Pcg32Work {
 
 // Register-resident FP32 CG (3 columns): shape for n rows on ``sms`` SMs
 // (false when n needs more than 8 rows per thread), and its launch (at most
-// 256 blocks). args.bar, args.r .. args.s and args.partials are unused.
+// 256 blocks). args.bar, args.r .. args.s and args.partials are unused. With
+// work.off set (rpt <= 4) it runs on the partitioned system of emu_cgpart.h
+// with the block-local polynomial in its preconditioner, like the pipelined
+// kernel; otherwise thread t of block b owns the rows (b + k grid) 256 + t.
 bool pcg32_shape(int64_t n, int sms, int* grid, int* rpt);
 cudaError_t launch_pcg32(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, int rpt, cudaStream_t st);
 // Per-device kernel attributes of the FP32 CG (before its first launch).

@@ -14,7 +14,9 @@
 //     result is deterministic;
 //   * the matrix, D^-1 and Phi are read-only for the whole launch (__ldg).
 // Two grid-wide barriers per iteration (after u, after the partial sums);
-// pcg32p_kernel below is the pipelined variant with one.
+// pcg32p_kernel below is the pipelined variant with one. Both run on the
+// partitioned system of emu_cgpart.h when the handle has one, with the
+// block-local Chebyshev polynomial (LocalPrec) in place of D^-1.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -318,6 +320,113 @@ __device__ __forceinline__ void coarse_solve4(const float* s_Einv, const float* 
   __syncthreads();
 }
 
+// Block-local part P of the two-level preconditioner (emu_cgpart.h) on a
+// partitioned system: P y = D^-1/2 x_k, x_k the Chebyshev iterate of degree
+// k for A_b x = D^-1/2 y from x = 0, A_b the block's diagonal block of
+// D^-1/2 A D^-1/2 held in shared memory as words of a 16-bit local column
+// and a bfloat16 weight (D^-1 y when the degree is 1). Every thread of the
+// block calls apply (it holds block barriers); the two product buffers
+// alternate, so one barrier per product suffices.
+template <int RPT>
+struct LocalPrec {
+  float4* buf;            // 2 RPT NT float4 of shared memory
+  const uint32_t* table;  // RPT lw NT words of shared memory
+  const float* c1;        // Chebyshev coefficients (shared)
+  const float* c2;
+  float c0;
+  int lw;                 // 0: Jacobi only
+  int degree;
+  int pb;
+
+  // t = O y on the block's rows, O the off-diagonal part of A_b
+  __device__ __forceinline__ void off(const bool (&own)[RPT], const float (&y)[RPT][NR], float (&t)[RPT][NR]) {
+    float4* b = buf + pb * (RPT * NT);
+    pb ^= 1;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+      b[k * NT + threadIdx.x] = own[k] ? make_float4(y[k][0], y[k][1], y[k][2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+      const uint32_t* le = table + (size_t)k * lw * NT + threadIdx.x;
+      // the first kLocUnroll entries at once (all loads in flight), the rest in a loop
+      uint32_t wd[kLocUnroll];
+#pragma unroll
+      for (int e = 0; e < kLocUnroll; ++e) wd[e] = e < lw ? le[e * NT] : 0u;
+      float4 yv[kLocUnroll];
+#pragma unroll
+      for (int e = 0; e < kLocUnroll; ++e) yv[e] = b[wd[e] & 0xFFFFu];
+#pragma unroll
+      for (int e = 0; e < kLocUnroll; ++e) {
+        const float av = __uint_as_float(wd[e] & 0xFFFF0000u);
+        t0 += av * yv[e].x;
+        t1 += av * yv[e].y;
+        t2 += av * yv[e].z;
+      }
+      for (int e = kLocUnroll; e < lw; ++e) {
+        const uint32_t word = le[e * NT];
+        const float av = __uint_as_float(word & 0xFFFF0000u);
+        const float4 y4 = b[word & 0xFFFFu];
+        t0 += av * y4.x;
+        t1 += av * y4.y;
+        t2 += av * y4.z;
+      }
+      t[k][0] = t0;
+      t[k][1] = t1;
+      t[k][2] = t2;
+    }
+  }
+
+  // out = P y
+  __device__ __forceinline__ void apply(const bool (&own)[RPT], const float (&di)[RPT], const float (&sd)[RPT],
+                                        const float (&y)[RPT][NR], float (&out)[RPT][NR]) {
+    if (lw == 0) {
+#pragma unroll
+      for (int k = 0; k < RPT; ++k)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) out[k][j] = di[k] * y[k][j];
+      return;
+    }
+    float xk[RPT][NR], dk[RPT][NR], res[RPT][NR], t[RPT][NR];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        res[k][j] = sd[k] * y[k][j];
+        xk[k][j] = dk[k][j] = c0 * res[k][j];
+      }
+    off(own, xk, t);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) res[k][j] -= xk[k][j] + t[k][j];
+    // one copy of the step in the code (a short kernel body stays in the instruction cache)
+#pragma unroll 1
+    for (int i = 1; i < degree; ++i) {
+      const float a1 = c1[i], a2 = c2[i];
+#pragma unroll
+      for (int k = 0; k < RPT; ++k)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          dk[k][j] = a1 * dk[k][j] + a2 * res[k][j];
+          xk[k][j] += dk[k][j];
+        }
+      if (i + 1 < degree) {
+        off(own, dk, t);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+#pragma unroll
+          for (int j = 0; j < NR; ++j) res[k][j] -= dk[k][j] + t[k][j];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) out[k][j] = sd[k] * xk[k][j];
+  }
+};
+
 // cc = E^-1 rho for the 16 x 3 coarse coefficients (block-wide, then a barrier)
 __device__ __forceinline__ void coarse_solve(const float* s_Einv, const float* s_rho, float* s_cc) {
   for (int e = threadIdx.x; e < kModes * NR; e += NT) {
@@ -343,9 +452,16 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
   __shared__ float s_rho[NC > 0 ? NC : 1], s_sig[NC > 0 ? NC : 1], s_cc[NC > 0 ? NC : 1];
   __shared__ float s_Einv[COARSE ? kModes * kModes : 1];
   __shared__ int s_flag;
+  __shared__ float s_c1[kChebMax], s_c2[kChebMax];  // Chebyshev coefficients
   // the coarse basis rows of this thread, float4 q of row k at
-  // sPhi[(q * RPT + k) * NT + tid] (consecutive threads, consecutive 16 bytes)
+  // sPhi[(q * RPT + k) * NT + tid] (consecutive threads, consecutive 16 bytes);
+  // then, on a partitioned system, two buffers of the local products and the local table
   extern __shared__ float4 sPhi[];
+  float4* sBuf = sPhi + (COARSE ? (kModes / 4) * RPT * NT : 0);
+  uint32_t* sLoc = reinterpret_cast<uint32_t*>(sBuf + 2 * RPT * NT);
+  const bool parted = wk.off != nullptr;  // rows in the partition of emu_cgpart.h
+  const int lw = (parted && wk.degree > 1) ? wk.lw : 0;
+  const int32_t* __restrict__ perm = wk.perm;
   unsigned epoch = 0;
   const int64_t n = a.n;
   float4* __restrict__ ugx = wk.ug;      // x of the first residual
@@ -359,19 +475,34 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
   if constexpr (COARSE) {
     for (int k = threadIdx.x; k < kModes * kModes; k += NT) s_Einv[k] = (float)a.Einv[k];
   }
+  if (threadIdx.x < kChebMax) {
+    s_c1[threadIdx.x] = wk.c1[threadIdx.x];
+    s_c2[threadIdx.x] = wk.c2[threadIdx.x];
+  }
+  if (lw > 0) {
+    const uint32_t* __restrict__ lsrc = wk.loc + (size_t)blockIdx.x * RPT * lw * NT;
+    for (int e = threadIdx.x; e < RPT * lw * NT; e += NT) sLoc[e] = __ldg(lsrc + e);
+  }
 
   float x[RPT][NR], r[RPT][NR], p[RPT][NR], s[RPT][NR], u[RPT][NR], w[RPT][NR];
-  float di[RPT];
+  float di[RPT], sd[RPT];
+  int64_t vr[RPT];
   bool own[RPT];
+  const int64_t rbeg = parted ? wk.off[blockIdx.x] : 0, rend = parted ? wk.off[blockIdx.x + 1] : n;
+  // row k of this thread and the vertex it stands for (b and x are in vertex order)
+  auto vert = [&](int k) -> int64_t { return parted ? (int64_t)__ldg(perm + vr[k]) : vr[k]; };
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
-    const int64_t v = g0 + k * stride;
-    own[k] = v < n;
+    const int64_t v = parted ? rbeg + k * NT + threadIdx.x : g0 + k * stride;
+    vr[k] = v;
+    own[k] = v < rend;
     di[k] = own[k] ? __ldg(a.dinv + v) : 0.f;
+    sd[k] = sqrtf(di[k]);
+    const int64_t o = own[k] ? vert(k) : 0;
 #pragma unroll
-    for (int j = 0; j < NR; ++j) x[k][j] = own[k] ? a.x[v * NR + j] : 0.f;
+    for (int j = 0; j < NR; ++j) x[k][j] = own[k] ? a.x[o * NR + j] : 0.f;
     if constexpr (COARSE) {
-      const float4* ph = reinterpret_cast<const float4*>(a.phi + v * kModes);
+      const float4* ph = reinterpret_cast<const float4*>(a.phi + (own[k] ? v : 0) * kModes);
 #pragma unroll
       for (int q = 0; q < kModes / 4; ++q)
         sPhi[(q * RPT + k) * NT + threadIdx.x] = own[k] ? __ldg(ph + q) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -379,16 +510,27 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
   }
 
   auto spmv = [&](const float4* __restrict__ z, float (&y)[RPT][NR]) {
-    spmv_rows<RPT>(rowptr, col, val, own, g0, stride, z, y);
+    spmv_rows_v<RPT, kGather>(rowptr, col, val, own, vr, z, y);
   };
-  // u = D^-1 r + Phi cc, stored for the neighbours
+  LocalPrec<RPT> lp{sBuf, sLoc, s_c1, s_c2, wk.c0, lw, wk.degree, 0};
+  // u = P r + Phi cc (P: the block-local polynomial, D^-1 without one), stored
+  // for the neighbours; every thread of the block calls it
   auto precond = [&]() {
+    float ul[RPT][NR];
+    if constexpr (RPT <= 4) {  // partitioned systems have at most 4 rows per thread
+      lp.apply(own, di, sd, r, ul);
+    } else {
+#pragma unroll
+      for (int k = 0; k < RPT; ++k)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) ul[k][j] = di[k] * r[k][j];
+    }
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
       if (!own[k]) continue;
-      const int64_t v = g0 + k * stride;
+      const int64_t v = vr[k];
 #pragma unroll
-      for (int j = 0; j < NR; ++j) u[k][j] = di[k] * r[k][j];
+      for (int j = 0; j < NR; ++j) u[k][j] = ul[k][j];
       if constexpr (COARSE) {
 #pragma unroll
         for (int q = 0; q < kModes / 4; ++q) {
@@ -415,17 +557,15 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
 
   // ---- r = b - A x ------------------------------------------------------
 #pragma unroll
-  for (int k = 0; k < RPT; ++k) {
-    const int64_t v = g0 + k * stride;
-    if (own[k]) ugx[v] = make_float4(x[k][0], x[k][1], x[k][2], 0.f);
-  }
+  for (int k = 0; k < RPT; ++k)
+    if (own[k]) ugx[vr[k]] = make_float4(x[k][0], x[k][1], x[k][2], 0.f);
   if (!gbar(wk, epoch, &s_flag, a.wait_ns)) goto timeout;
   spmv(ugx, w);
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
-    const int64_t v = g0 + k * stride;
+    const int64_t o = own[k] ? vert(k) : 0;
 #pragma unroll
-    for (int j = 0; j < NR; ++j) r[k][j] = own[k] ? a.b[v * NR + j] - w[k][j] : 0.f;
+    for (int j = 0; j < NR; ++j) r[k][j] = own[k] ? a.b[o * NR + j] - w[k][j] : 0.f;
   }
   if constexpr (COARSE) {  // rho = Phi^T r
     float loc[NV0];
@@ -451,10 +591,10 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
       if (!own[k]) continue;
-      const int64_t v = g0 + k * stride;
+      const int64_t o = vert(k);
 #pragma unroll
       for (int j = 0; j < NR; ++j) {
-        const float bv = a.b[v * NR + j];
+        const float bv = a.b[o * NR + j];
         loc[j] += r[k][j] * u[k][j];
         loc[NR + j] += w[k][j] * u[k][j];
         loc[2 * NR + j] += r[k][j] * r[k][j];
@@ -579,10 +719,11 @@ __global__ void __launch_bounds__(NT, 1) pcg32_kernel(PcgArgsT<float> a, Pcg32Wo
     }
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
-      const int64_t v = g0 + k * stride;
-      if (own[k])
+      if (own[k]) {
+        const int64_t o = vert(k);
 #pragma unroll
-        for (int j = 0; j < NR; ++j) a.x[v * NR + j] = x[k][j];
+        for (int j = 0; j < NR; ++j) a.x[o * NR + j] = x[k][j];
+      }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       if (a.iters_out) atomicAdd(a.iters_out, it);
@@ -705,96 +846,9 @@ __global__ void __launch_bounds__(NT, 1) pcg32p_kernel(PcgArgsT<float> a, Pcg32W
     o[1] = acc.y;
     o[2] = acc.z;
   };
-  // t = O y on the block's rows, O the off-diagonal part of A_b (bfloat16
-  // weights, local column in the low half of a table word). Every thread of
-  // the block calls it (it holds a block barrier); the two buffers alternate,
-  // so one barrier per product suffices.
-  int pb = 0;
-  auto off_apply = [&](const float (&y)[RPT][NR], float (&t)[RPT][NR]) {
-    float4* buf = sBuf + pb * (RPT * NT);
-    pb ^= 1;
-#pragma unroll
-    for (int k = 0; k < RPT; ++k)
-      buf[k * NT + threadIdx.x] = own[k] ? make_float4(y[k][0], y[k][1], y[k][2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-      float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-      const uint32_t* le = sLoc + (size_t)k * lw * NT + threadIdx.x;
-      // the first kLocUnroll entries at once (all loads in flight), the rest in a loop
-      uint32_t wd[kLocUnroll];
-#pragma unroll
-      for (int e = 0; e < kLocUnroll; ++e) wd[e] = e < lw ? le[e * NT] : 0u;
-      float4 yv[kLocUnroll];
-#pragma unroll
-      for (int e = 0; e < kLocUnroll; ++e) yv[e] = buf[wd[e] & 0xFFFFu];
-#pragma unroll
-      for (int e = 0; e < kLocUnroll; ++e) {
-        const float av = __uint_as_float(wd[e] & 0xFFFF0000u);
-        t0 += av * yv[e].x;
-        t1 += av * yv[e].y;
-        t2 += av * yv[e].z;
-      }
-      for (int e = kLocUnroll; e < lw; ++e) {
-        const uint32_t word = le[e * NT];
-        const float av = __uint_as_float(word & 0xFFFF0000u);
-        const float4 y4 = buf[word & 0xFFFFu];
-        t0 += av * y4.x;
-        t1 += av * y4.y;
-        t2 += av * y4.z;
-      }
-      t[k][0] = t0;
-      t[k][1] = t1;
-      t[k][2] = t2;
-    }
-  };
-  // out = P y: Chebyshev acceleration for A_b x = D^-1/2 y from x = 0, then
-  // D^-1/2 x (degree 1: D^-1 y)
-  auto local_apply = [&](const float (&y)[RPT][NR], float (&out)[RPT][NR]) {
-    if (lw == 0) {
-#pragma unroll
-      for (int k = 0; k < RPT; ++k)
-#pragma unroll
-        for (int j = 0; j < NR; ++j) out[k][j] = di[k] * y[k][j];
-      return;
-    }
-    float xk[RPT][NR], dk[RPT][NR], res[RPT][NR], t[RPT][NR];
-#pragma unroll
-    for (int k = 0; k < RPT; ++k)
-#pragma unroll
-      for (int j = 0; j < NR; ++j) {
-        res[k][j] = sd[k] * y[k][j];
-        xk[k][j] = dk[k][j] = wk.c0 * res[k][j];
-      }
-    off_apply(xk, t);
-#pragma unroll
-    for (int k = 0; k < RPT; ++k)
-#pragma unroll
-      for (int j = 0; j < NR; ++j) res[k][j] -= xk[k][j] + t[k][j];
-    // one copy of the step in the code (a short kernel body stays in the instruction cache)
-#pragma unroll 1
-    for (int i = 1; i < wk.degree; ++i) {
-      const float c1 = s_c1[i], c2 = s_c2[i];
-#pragma unroll
-      for (int k = 0; k < RPT; ++k)
-#pragma unroll
-        for (int j = 0; j < NR; ++j) {
-          dk[k][j] = c1 * dk[k][j] + c2 * res[k][j];
-          xk[k][j] += dk[k][j];
-        }
-      if (i + 1 < wk.degree) {
-        off_apply(dk, t);
-#pragma unroll
-        for (int k = 0; k < RPT; ++k)
-#pragma unroll
-          for (int j = 0; j < NR; ++j) res[k][j] -= dk[k][j] + t[k][j];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < RPT; ++k)
-#pragma unroll
-      for (int j = 0; j < NR; ++j) out[k][j] = sd[k] * xk[k][j];
-  };
+  // out = P y, the block-local part of M (a Chebyshev polynomial of the block's diagonal block)
+  LocalPrec<RPT> lp{sBuf, sLoc, s_c1, s_c2, wk.c0, lw, wk.degree, 0};
+  auto local_apply = [&](const float (&y)[RPT][NR], float (&out)[RPT][NR]) { lp.apply(own, di, sd, y, out); };
   auto rhs = [&](int k, int j) {  // b of row k (vertex order on input)
     return a.b[(int64_t)__ldg(perm + vr[k]) * NR + j];
   };
@@ -988,11 +1042,18 @@ __global__ void k_aphi32(int64_t n, const int32_t* __restrict__ rowptr, const in
 }
 
 namespace {
+// dynamic shared memory: the coarse rows (C), then on a partitioned system
+// two buffers of the local products and a local table of lw words per row slot
+template <int RPT, bool C>
+constexpr size_t plain_smem(bool parted, int lw) {
+  return (C ? sizeof(float4) * (kModes / 4) * RPT * NT : 0) +
+         (parted ? 2 * sizeof(float4) * RPT * NT + sizeof(uint32_t) * (size_t)RPT * lw * NT : 0);
+}
+
 template <int RPT, bool C>
 cudaError_t prepare32() {
-  // the coarse rows live in dynamic shared memory (RPT x 16 KB); above the
-  // default 48 KB the kernel needs the opt-in, a per-device attribute
-  const size_t smem = C ? sizeof(float4) * (kModes / 4) * RPT * NT : 0;
+  // above the default 48 KB the kernel needs the opt-in, a per-device attribute
+  const size_t smem = plain_smem<RPT, C>(RPT <= 4, RPT <= 4 ? cg_local_width_max(RPT) : 0);
   if (smem <= 48 * 1024) return cudaSuccess;
   static bool set[64] = {false};
   static std::mutex mu;  // handles may be built from several threads
@@ -1009,7 +1070,12 @@ cudaError_t prepare32() {
 
 template <int RPT, bool C>
 cudaError_t launch32(const PcgArgsT<float>& args, const Pcg32Work& work, int grid, cudaStream_t st) {
-  const size_t smem = C ? sizeof(float4) * (kModes / 4) * RPT * NT : 0;
+  const bool parted = work.off != nullptr;
+  const int lw = (parted && work.degree > 1) ? work.lw : 0;
+  if (parted && (RPT > 4 || !work.perm || lw > cg_local_width_max(RPT) || (lw > 0 && !work.loc) ||
+                 work.degree < 1 || work.degree > kChebMax))
+    return cudaErrorInvalidValue;
+  const size_t smem = plain_smem<RPT, C>(parted, lw);
   PcgArgsT<float> a = args;
   Pcg32Work w = work;
   void* params[] = {(void*)&a, (void*)&w};
@@ -1100,7 +1166,12 @@ cudaError_t launch_aphi32(int64_t n, const int32_t* rowptr, const int32_t* col, 
 }
 
 cudaError_t prepare_pcg32() {
-  cudaError_t e = prepare32<4, true>();
+  cudaError_t e = prepare32<1, true>();
+  if (e == cudaSuccess) e = prepare32<1, false>();
+  if (e == cudaSuccess) e = prepare32<2, true>();
+  if (e == cudaSuccess) e = prepare32<2, false>();
+  if (e == cudaSuccess) e = prepare32<4, true>();
+  if (e == cudaSuccess) e = prepare32<4, false>();
   if (e == cudaSuccess) e = prepare32<8, true>();
   if (e == cudaSuccess) e = prepare32p<1>();
   if (e == cudaSuccess) e = prepare32p<2>();
