@@ -51,6 +51,7 @@ from emu_inputs import arm_assembly, batch_set, box_beam, mtu_for_tet_count, mus
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 129e6  # GB300 L2
 
 # DRAM bytes (read + write) per launch of a phase's kernel from one ncu
 # capture of the unchanged kernel (summaries under profiles/); None once the
@@ -182,6 +183,14 @@ def dominant_roofline(prof, mixed, m, n, nnz, cg_total, peak, peak_kind, traffic
     bound = "hbm"
     if traffic is not None and traffic < 0.25 * per_launch:
         bound = "latency"
+    # without a capture of this workload: the coupling solve's system (CSR,
+    # D^-1, coarse rows, six 3-vectors) well inside the 129 MB L2 is
+    # latency-bound by construction (grid barriers and L2 round trips)
+    f = 4 if mixed else 8
+    system_bytes = nnz * (f + 4) + n * (f + 16 * f + 6 * 3 * f)
+    l2_resident = name == "pcg" and traffic is None and system_bytes < 0.5 * L2_BYTES
+    if l2_resident:
+        bound = "latency"
     roof = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_source": tr[1] if tr else None,
             "peak_source": peak_kind, "bytes_per_launch": per_launch, "avg_launch_ms": 1e3 * avg_s,
@@ -193,6 +202,10 @@ def dominant_roofline(prof, mixed, m, n, nnz, cg_total, peak, peak_kind, traffic
         roof["note"] = ("L2-resident: DRAM traffic per launch is far below the algorithmic bytes, so frac "
                         "measures how fast the solve streams its operands from L2; the limit is grid-barrier "
                         "and L2 latency")
+        if l2_resident:
+            roof["note"] = (f"L2-resident by size (system {system_bytes / 1e6:.1f} MB against the 129 MB L2; no "
+                            "ncu capture of this workload): frac measures how fast the solve streams its operands "
+                            "from L2; the limit is grid-barrier and L2 latency")
     return roof
 
 

@@ -19,8 +19,11 @@ def test_dominant_phase_with_little_dram_traffic_is_latency_bound():
     assert math.isclose(roof["bytes_per_launch"], per_launch)
     assert math.isclose(roof["frac"], per_launch / (3.4e-3 / 11) / 1e9 / 6800.0)
     assert math.isclose(roof["dram_frac"], 20e6 / (3.4e-3 / 11) / 1e9 / 6800.0)
-    # without a DRAM figure the phase is labelled by its algorithmic bytes
+    # without a DRAM figure a system well inside L2 is latency-bound by size ...
     roof = bench.dominant_roofline(_prof(), True, m, n, nnz, 300.0, 6800.0, "measured", {})
+    assert roof["bound"] == "latency" and roof["traffic"] is None and "by size" in roof["note"]
+    # ... and one too large for L2 is labelled by its algorithmic bytes
+    roof = bench.dominant_roofline(_prof(), True, 40 * m, 40 * n, 40 * nnz, 300.0, 6800.0, "measured", {})
     assert roof["bound"] == "hbm" and roof["traffic"] is None
 
 
