@@ -105,24 +105,26 @@ def make_workload(name):
     raise ValueError(name)
 
 
-def algorithmic_bytes(phase, mixed, m, n, nnz, cg_iters):
+def algorithmic_bytes(phase, mixed, m, n, nnz, cg_iters, fform=False):
     """Minimum bytes one launch of a phase must move (each array read or
     written once; vertex arrays once per vertex), for the roofline.
 
     Per-tet phases count per-tet records of the mixed (FP32) or FP64 layout;
     the ACAP solve counts, per CG iteration, the CSR matrix (value + column
     index), D^-1, the 16 coarse-basis values and six 3-vectors read and
-    written once, times the CG iterations of the launch."""
+    written once, times the CG iterations of the launch. The F-form (FP64)
+    keeps F (9 values) as its state and a 45-entry factor per tet."""
     f = 4 if mixed else 8
     rec = 16 + 9 * f + 6 * f + 3 * f          # tet, D^-1, V c w mu lam ka, u
-    state = (16 + 6 * 4) if mixed else (72 + 48)
+    state = (16 + 6 * 4) if mixed else (72 if fform else 72 + 48)
+    fac = 45 if fform else 54
     vert = 24 * n / m                          # q gathered, each vertex once
     per_tet = {
-        "grad": rec + state + vert + 9 * f + 9 * f + 9 * f + 54 * f,   # + E0 (mixed), write g, y, Uw
-        "dir": 48 * f + 54 * f + 9 * f + 9 * f + 9 * f + f + 9 * f + 96,  # gam, Uw, y, g, D^-1, w -> d, corner terms
+        "grad": rec + state + vert + 9 * f + 9 * f + 9 * f + fac * f,   # + E0 (mixed), write g, y, Uw
+        "dir": 48 * f + fac * f + 9 * f + 9 * f + 9 * f + f + 9 * f + 96,  # gam, Uw, y, g, D^-1, w -> d, corner terms
         "ls": rec + state + 9 * f + 2 * vert + (9 * 4 if mixed else 0),
         "update": 2 * state + 9 * f,
-        "syrk": 54 * f + 48 * f + 9 * f + f,
+        "syrk": fac * f + 48 * f + 9 * f + f,
         "rhs": 16 + 9 * f + state + f + 96,
     }
     if phase in per_tet:
@@ -144,7 +146,7 @@ def per_tet_kernels(mixed):
     return PER_TET_KERNELS if mixed else PER_TET_KERNELS_FP64
 
 
-def per_tet_fractions(prof, mixed, m, n, nnz, peak, traffic_table=None):
+def per_tet_fractions(prof, mixed, m, n, nnz, peak, traffic_table=None, fform=False):
     """Each per-tet kernel's algorithmic bytes per launch over its average
     CUDA-event duration, against the HBM peak; with the kernel's ncu DRAM
     bytes per launch beside it where a capture of the unchanged kernel exists."""
@@ -154,7 +156,7 @@ def per_tet_fractions(prof, mixed, m, n, nnz, peak, traffic_table=None):
         if nl <= 0 or ms <= 0:
             continue
         launches = nl * per
-        b = algorithmic_bytes(name, mixed, m, n, nnz, 0.0)
+        b = algorithmic_bytes(name, mixed, m, n, nnz, 0.0, fform)
         us = 1e3 * ms / launches
         gbs = b / (us * 1e-6) / 1e9
         out[name] = {"bytes_per_launch": b, "us_per_launch": round(us, 2), "achieved_gbs": round(gbs, 1),
@@ -166,13 +168,13 @@ def per_tet_fractions(prof, mixed, m, n, nnz, peak, traffic_table=None):
     return out
 
 
-def dominant_roofline(prof, mixed, m, n, nnz, cg_total, peak, peak_kind, traffic_table):
+def dominant_roofline(prof, mixed, m, n, nnz, cg_total, peak, peak_kind, traffic_table, fform=False):
     """Roofline entry of the phase with the most device time. The coupling
     solve's system (CSR, vectors, coarse rows) is L2-resident on the
     benchmark meshes: when its measured DRAM traffic is far below the
     algorithmic bytes it is reported as latency-bound, with both fractions."""
     name, (ms_tot, nl) = max(prof.items(), key=lambda kv: kv[1][0])
-    total = algorithmic_bytes(name, mixed, m, n, nnz, cg_total)
+    total = algorithmic_bytes(name, mixed, m, n, nnz, cg_total, fform)
     if total is None or nl <= 0 or ms_tot <= 0:
         return None
     per_launch = total / nl if name == "pcg" else total
@@ -209,7 +211,7 @@ def dominant_roofline(prof, mixed, m, n, nnz, cg_total, peak, peak_kind, traffic
     return roof
 
 
-def whole_iteration(prof, mixed, m, n, nnz, cg_total, iters, peak, value):
+def whole_iteration(prof, mixed, m, n, nnz, cg_total, iters, peak, value, fform=False):
     """One Newton iteration against the HBM roofline: the algorithmic bytes
     of every per-tet kernel and of the coupling solve over the device time
     per iteration, and the measured tet-iters/s against the scope's ceiling
@@ -219,7 +221,7 @@ def whole_iteration(prof, mixed, m, n, nnz, cg_total, iters, peak, value):
     b = 0.0
     for name, per in per_tet_kernels(mixed).items():
         ms, nl = prof.get(name, (0.0, 0))
-        b += algorithmic_bytes(name, mixed, m, n, nnz, 0.0) * nl * per
+        b += algorithmic_bytes(name, mixed, m, n, nnz, 0.0, fform) * nl * per
     b += algorithmic_bytes("pcg", mixed, m, n, nnz, cg_total)
     b /= iters
     t = sum(v[0] for v in prof.values()) / 1e3 / iters
@@ -496,6 +498,8 @@ def make_params(emu, args, mixed):
         p.ls_sigma0 = args.ls_sigma0
     if args.cg_degree is not None:
         p.cg_local_degree = args.cg_degree
+    if getattr(args, "form", "rs") == "f":
+        p.form = emu.FORM_F
     return p
 
 
@@ -653,6 +657,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (1/s)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: device-memory budget")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--form", default="rs", choices=["rs", "f"],
+                    help="Newton variables: rotation-stretch chart (rs) or the F-form of Sec. 3.2.1 (f, FP64 only)")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
@@ -661,6 +667,8 @@ def main():
     ap.add_argument("--cg-degree", type=int, default=None,
                     help="degree of the block-local polynomial in the dq solves' preconditioner (default: the library's, 4)")
     args = ap.parse_args()
+    if args.form == "f" and args.precision != "fp64":
+        ap.error("--form f runs in FP64: add --precision fp64")
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -763,11 +771,12 @@ def main():
     nnz = solver_nnz(mesh)
     cg_per_iter = prof_cg / max(prof_its, 1)
     dev_ms = sum(v[0] for v in prof.values())
+    fform = args.form == "f"
     per_tet = per_tet_fractions(prof, mixed, m, n, nnz, peak,
-                                NCU_TRAFFIC if (mixed and args.workload == "mtu") else {})
+                                NCU_TRAFFIC if (mixed and args.workload == "mtu") else {}, fform)
     roof = dominant_roofline(prof, mixed, m, n, nnz, float(prof_cg), peak, peak_kind,
-                             NCU_TRAFFIC if (mixed and args.workload == "mtu") else {})
-    whole = whole_iteration(prof, mixed, m, n, nnz, float(prof_cg), prof_its, peak, value)
+                             NCU_TRAFFIC if (mixed and args.workload == "mtu") else {}, fform)
+    whole = whole_iteration(prof, mixed, m, n, nnz, float(prof_cg), prof_its, peak, value, fform)
     err = None
     if cb_ref is not None:
         err = error_vs_oracle(emu, params, cb_ref)
@@ -776,7 +785,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "l2": f"flushed ({args.flush_mb} MB write) between steps",
-                   "tets": m, "verts": n, "ls_sigma0": params.ls_sigma0, "cg_local_degree": params.cg_local_degree},
+                   "tets": m, "verts": n, "ls_sigma0": params.ls_sigma0, "cg_local_degree": params.cg_local_degree,
+                   "form": args.form},
         "ms_per_converged_frame_p50": float(np.median(frame_ms)),
         "frame_ms_p99": float(np.percentile(frame_ms, 99)),
         "newton_iters_per_frame": [int(x) for x in iters],

@@ -58,6 +58,11 @@ typedef enum {
 } emu_status;
 
 typedef enum { EMU_PRECISION_FP64 = 0, EMU_PRECISION_MIXED = 1 } emu_precision;
+/* Variables of the Newton iteration (emu_params.form): the rotation-stretch
+ * chart F_i = R_i S(s_i) with its 6 x 6 stretch Hessian, or the paper's own
+ * F-form (Sec. 3.2.1, Eqs. 10-12) with one free F_i and a 9 x 9 block per
+ * tet. Both reach the same equilibrium. */
+typedef enum { EMU_FORM_RS = 0, EMU_FORM_F = 1 } emu_form;
 
 /* Opaque solver handle (library-owned). */
 typedef struct emu_handle emu_handle;
@@ -174,7 +179,18 @@ typedef struct {
  *                   Eq. 4, next to the coarse space on the low-rank basis
  *                   (a two-level additive Schwarz preconditioner). 1 is plain
  *                   Jacobi; higher degrees cost more per CG iteration and
- *                   take fewer iterations (default 4). */
+ *                   take fewer iterations (default 4).
+ *   form            EMU_FORM_RS (default) or EMU_FORM_F. The F-form keeps one
+ *                   deformation gradient F_i per tet, builds the 9 x 9 block
+ *                   H_i = PSD(V Psi_iso''(F_i)) + V Psi_fiber''(F_i)
+ *                   + alpha w_i I (the definiteness fix on the isotropic
+ *                   term, through its analytic eigen-system) and updates
+ *                   F <- F + sigma d directly (no polar re-extraction). It
+ *                   runs in FP64 (precision must be EMU_PRECISION_FP64) on
+ *                   meshes without bones or joints; otherwise emu_create
+ *                   returns EMU_ERR_NOT_IMPLEMENTED. emu_get_element_state
+ *                   then returns F and its polar factors R, s;
+ *                   emu_set_element_state sets F = R S. */
 typedef struct {
   double alpha_rel;
   int32_t weight_mode;
@@ -196,6 +212,7 @@ typedef struct {
   double eps_bone;
   double eps_joint;
   int32_t cg_local_degree;
+  int32_t form;
 } emu_params;
 
 /* Per-solve statistics. */
@@ -375,6 +392,21 @@ int emu_get_sizes(emu_handle* h, int64_t* n_verts, int64_t* n_tets, int32_t* k_m
  * inputs and outputs. */
 int emu_eval_stretch_terms(const double* s, const double* params, int64_t n, int32_t mixed,
                            double* psi, double* grad, double* hess, void* stream);
+
+/* Evaluates, on the device, the F-form's element terms (Sec. 3.1 energy,
+ * Sec. 3.2.1 Hessian):
+ *   psi[i]  = V_i Psi(F_i)  (1e40 V_i when det F_i <= 0),
+ *   grad[i] = V_i P(F_i), the first Piola stress (9, row-major F index),
+ *   hess[i] = V_i [PSD(Psi_iso''(F_i)) + Psi_fiber''(F_i)] (9 x 9
+ *             row-major over the row-major F index): the neo-Hookean
+ *             Hessian with its negative eigenvalues clamped at zero, from
+ *             its analytic eigen-system in the singular-value frame of F,
+ *             plus 2 kappa a I (x) u u^T. NaN where det F_i <= 0.
+ * Device pointers: F (n x 9), params (n x 8: V, mu, lambda, kappa*a, u_x,
+ * u_y, u_z, unused), outputs psi (n), grad (n x 9), hess (n x 81); any
+ * output may be NULL. Synchronises ``stream``. */
+int emu_eval_fform_terms(const double* F, const double* params, int64_t n, double* psi, double* grad, double* hess,
+                         void* stream);
 
 /* Self-check of the bounded device waits (no counterpart in the paper).
  * Every spin-wait in this library's kernels (the grid barriers of the

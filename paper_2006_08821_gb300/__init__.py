@@ -22,7 +22,10 @@ from .binding import (  # noqa: F401
     fiber_field,
     eval_polar,
     eval_stretch_terms,
+    eval_fform_terms,
     load_library,
     PRECISION_FP64,
     PRECISION_MIXED,
+    FORM_RS,
+    FORM_F,
 )

@@ -30,6 +30,8 @@ EMU_ERR_NOT_IMPLEMENTED = -10
 
 PRECISION_FP64 = 0
 PRECISION_MIXED = 1
+FORM_RS = 0  # rotation-stretch chart (emu_form)
+FORM_F = 1   # the F-form of Sec. 3.2.1
 
 # Entry points declared in include/emu.h (checked by the export test).
 EXPORTED = [
@@ -40,6 +42,7 @@ EXPORTED = [
     "emu_acap_solve_noalloc", "emu_batch_solve", "emu_required_bytes", "emu_server_create",
     "emu_server_submit", "emu_server_poll", "emu_server_result", "emu_server_destroy", "emu_check_bounded_wait",
     "emu_eval_capacitance", "emu_set_external_forces", "emu_fiber_field", "emu_alpha_sweep",
+    "emu_eval_fform_terms",
 ]
 
 PHASES = ["rhs", "assemble", "pcg", "grad", "syrk", "small", "dir", "ls", "update"]
@@ -105,6 +108,7 @@ class emu_params(C.Structure):
         ("eps_bone", C.c_double),
         ("eps_joint", C.c_double),
         ("cg_local_degree", C.c_int32),
+        ("form", C.c_int32),
     ]
 
 
@@ -227,6 +231,7 @@ class Params:
     eps_bone: float = -1e-3
     eps_joint: float = -1e-4
     cg_local_degree: int = 4
+    form: int = FORM_RS
 
     def to_c(self) -> emu_params:
         p = emu_params()
@@ -496,6 +501,14 @@ def eval_stretch_terms(s_dev, params_dev, n, mixed, psi_dev, grad_dev, hess_dev,
     cv = lambda x: None if x is None else C.c_void_p(int(x))  # noqa: E731
     _check(lib.emu_eval_stretch_terms(cv(s_dev), cv(params_dev), n, mixed, cv(psi_dev), cv(grad_dev),
                                       cv(hess_dev), cv(stream)), lib)
+
+
+def eval_fform_terms(F_dev, params_dev, n, psi_dev, grad_dev, hess_dev, stream=0):
+    """emu_eval_fform_terms on device pointers (ints)."""
+    lib = load_library()
+    cv = lambda x: None if x is None else C.c_void_p(int(x))  # noqa: E731
+    _check(lib.emu_eval_fform_terms(cv(F_dev), cv(params_dev), n, cv(psi_dev), cv(grad_dev), cv(hess_dev),
+                                    cv(stream)), lib)
 
 
 def check_bounded_wait(wait_ns: int, stream=0) -> int:

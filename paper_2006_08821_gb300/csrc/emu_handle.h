@@ -42,6 +42,7 @@ struct emu_handle {
   int kmodes = 16;
   bool mixed = false;
   bool escalated = false;  // a mixed handle running the FP64 kernels for the rest of a solve
+  bool fform = false;      // the F-form of Sec. 3.2.1 (FP64): R holds F, Uw the 9 x 9 factors
   std::vector<emu::DevBuf> bufs;
 
   double mu_ref = 0, alpha = 0, kappa = 0;
@@ -78,6 +79,7 @@ struct emu_handle {
   double* phi64 = nullptr;
   float* phi32 = nullptr;
   double* Einv = nullptr;
+  double* lam_add = nullptr;  // F-form: Phi^T K Phi (48 x 48) and 48 zeros, the capacitance's addend
   bool coarse_ready = false;
   // register-resident FP32 CG: exchange buffer, partial sums, launch shape
   float4* ug32 = nullptr;                // 2 n exchange entries of the FP32 CG

@@ -14,6 +14,7 @@
 
 #include "emu_internal.h"
 #include "emu_kernels.cuh"
+#include "emu_fform.h"
 #include "emu_mixed.cuh"
 #include "emu_pcg.h"
 
@@ -142,6 +143,7 @@ int validate_params(const emu_params* p) {
     return fail(EMU_ERR_INVALID_ARG, "eps_bone and eps_joint must be negative");
   if (p->cg_local_degree < 1 || p->cg_local_degree > kChebMax)
     return fail(EMU_ERR_INVALID_ARG, "cg_local_degree must be in [1, 8]");
+  if (p->form != EMU_FORM_RS && p->form != EMU_FORM_F) return fail(EMU_ERR_INVALID_ARG, "form must be RS or F");
   return EMU_OK;
 }
 
@@ -225,6 +227,8 @@ int refresh_begin(emu_handle* h, double /*tol*/) {
   h->ph_begin();
   if (h->mixed)
     launch_rhs_state_mixed(h->margs(), h->grid_tet, h->st);
+  else if (h->fform)
+    launch_rhs_fform(h->args<double>(), h->grid_tet, h->st);
   else
     launch_rhs_from_state(h->args<double>(), h->grid_tet, h->st);
   h->ph_end(EMU_PHASE_RHS, 1);
@@ -485,6 +489,16 @@ int build_modes(emu_handle* h) {
   EMU_CK(cudaStreamSynchronize(h->st));
   for (int i = 0; i < 16; ++i)
     for (int j = 0; j < 16; ++j) Eg[16 * i + j] = 0.5 * (Eg[16 * i + j] + Eg[16 * j + i]);
+  if (h->fform) {
+    // Lambda = Phi^T K Phi of Eqs. 9-12 for the 48 columns (coordinate r,
+    // scalar mode j) at 16 r + j: K = L (x) I_3, so three copies of E
+    std::vector<double> lam(kCapEntries + kK, 0.0);
+    for (int r = 0; r < 3; ++r)
+      for (int i = 0; i < 16; ++i)
+        for (int j = 0; j < 16; ++j) lam[(16 * r + i) * kK + 16 * r + j] = Eg[16 * i + j];
+    EMU_CK(cudaMemcpyAsync(h->lam_add, lam.data(), lam.size() * 8, cudaMemcpyHostToDevice, h->st));
+    EMU_CK(cudaStreamSynchronize(h->st));
+  }
   std::vector<double> Ev;
   host_jacobi_eig(Eg, Ev, 16);
   double emax = 0.0;
@@ -576,6 +590,7 @@ bool alloc_device(emu_handle* h, int64_t nnz) {
   ok = ok && h->get(h->rowptr, n + 1) && h->get(h->col, nnz) && h->get(h->val, nnz) && h->get(h->ldinv, n) &&
        h->get(h->bfix, 3 * n) && h->get(h->qfix, 3 * n) && h->get(h->is_fixed, n) && h->get(h->slot_ptr, n + 1) &&
        h->get(h->slot_idx, 4 * m);
+  if (h->fform) ok = ok && h->get(h->lam_add, kCapEntries + kK);
   ok = ok && bones_alloc(h);
   return ok;
 }
@@ -652,6 +667,7 @@ void emu_default_params(emu_params* p) {
   p->eps_bone = -1e-3;
   p->eps_joint = -1e-4;
   p->cg_local_degree = 4;
+  p->form = EMU_FORM_RS;
 }
 
 const char* emu_status_string(int status) {
@@ -693,6 +709,14 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     emu_default_params(&prm);
   rc = validate_params(&prm);
   if (rc) return rc;
+  if (prm.form == EMU_FORM_F) {
+    // the F-form runs the FP64 kernels on meshes without bones or joints
+    if (prm.precision != EMU_PRECISION_FP64)
+      return fail(EMU_ERR_NOT_IMPLEMENTED, "the F-form runs in FP64 only");
+    bool bones = desc->n_joints > 0;
+    for (int64_t i = 0; i < desc->n_tets && !bones && desc->bone_id; ++i) bones = desc->bone_id[i] >= 0;
+    if (bones) return fail(EMU_ERR_NOT_IMPLEMENTED, "the F-form is not combined with bones");
+  }
 
   emu_handle* h = new (std::nothrow) emu_handle();
   if (!h) return fail(EMU_ERR_OOM, "host allocation failed");
@@ -704,6 +728,7 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     h->has_alloc = true;
   }
   h->mixed = prm.precision == EMU_PRECISION_MIXED;
+  h->fform = prm.form == EMU_FORM_F;
   h->kmodes = prm.k_modes / 3;
   const int64_t n = desc->n_verts, m = desc->n_tets;
   h->n = n;
@@ -1146,6 +1171,8 @@ int enqueue_grad(emu_handle* h) {
     // the displacement's float pair for this iteration's per-tet kernels
     launch_split_disp(h->n, h->q, h->Qrest, h->uh32, h->ul32, h->st);
     launch_grad_mixed(h->margs(), h->grid_tet4, h->st);
+  } else if (h->fform) {
+    launch_grad_fform(h->args<double>(), h->grid_tet, h->st);
   } else {
     launch_grad<double>(h->args<double>(), h->grid_tet, h->st);
   }
@@ -1178,6 +1205,8 @@ int enqueue_step(emu_handle* h) {
   } else if (h->mixed) {
     syrk_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (h->m + 31) / 32), kTcBlocksPerSM * (int64_t)h->sms);
     launch_syrk_tc(am, syrk_blocks, h->cpart, h->st);
+  } else if (h->fform) {
+    launch_syrk_fform(a64, h->grid_syrk, h->cpart, h->st);
   } else {
     launch_syrk<double>(a64, h->grid_syrk, h->cpart, h->st);
   }
@@ -1186,7 +1215,7 @@ int enqueue_step(emu_handle* h) {
   // the 48 x 48 factor in FP32 on the mixed path, in FP64 with bones (their
   // 1/|eps_bone|-weighted terms widen the capacitance's spectrum)
   launch_cap_solve(h->cpart, syrk_blocks, h->cfull, h->z, h->sc, h->mixed && !h->has_bones, h->st,
-                   bones_cap_addend(h));
+                   h->fform ? h->lam_add : bones_cap_addend(h));
   bones_before_dir(h);
   h->ph_end(EMU_PHASE_SMALL, 2);
   h->ph_begin();
@@ -1197,7 +1226,10 @@ int enqueue_step(emu_handle* h) {
   } else {
     TetArgs<double> ad = a64;
     ad.partials = h->part_dir;
-    launch_dir<double>(ad, h->grid_tet, h->st);
+    if (h->fform)
+      launch_dir_fform(ad, h->grid_tet, h->st);
+    else
+      launch_dir<double>(ad, h->grid_tet, h->st);
   }
   h->ph_end(EMU_PHASE_DIR, 1);
   EMU_CK(cudaGetLastError());
@@ -1228,7 +1260,10 @@ int enqueue_step(emu_handle* h) {
       launch_bone_ls(h->bargs(), h->dq, h->prm.ls_rho, h->part_ls + (size_t)h->grid_tet * kLsNV, h->st);
       nls += kBoneLsBlocks;
     }
-    launch_ls<double>(al, h->grid_tet, h->prm.ls_rho, h->st);
+    if (h->fform)
+      launch_ls_fform(al, h->grid_tet, h->prm.ls_rho, h->st);
+    else
+      launch_ls<double>(al, h->grid_tet, h->prm.ls_rho, h->st);
     h->ph_end(EMU_PHASE_LS, 1);
     h->ph_begin();
     launch_ls_select(h->part_dir, dir_partial_count(h), h->part_ls, nls, h->sc, h->sigma0_now, h->prm.ls_rho,
@@ -1244,7 +1279,10 @@ int enqueue_step(emu_handle* h) {
     else
       launch_update_verts_f(h->n, h->sc, h->dq32, h->q, h->st);
   } else {
-    launch_update_tets<double>(a64, h->grid_tet, h->st);
+    if (h->fform)
+      launch_update_fform(a64, h->grid_tet, h->st);
+    else
+      launch_update_tets<double>(a64, h->grid_tet, h->st);
     launch_update_verts(h->n, h->sc, h->dq, h->q, h->st);
   }
   h->ph_end(EMU_PHASE_UPDATE, 2);
@@ -1610,6 +1648,7 @@ int emu_required_bytes(const emu_mesh_desc* desc, const emu_params* params, size
   h.n = desc->n_verts;
   h.m = desc->n_tets;
   h.mixed = prm.precision == EMU_PRECISION_MIXED;
+  h.fform = prm.form == EMU_FORM_F;
   if (desc->bone_id)
     for (int64_t i = 0; i < h.m && !h.has_bones; ++i) h.has_bones = desc->bone_id[i] >= 0;
   int dev = 0;
@@ -1680,6 +1719,18 @@ int emu_get_element_state(emu_handle* h, double* R, double* s, double* F) {
     bones_state_to_element_arrays(h);  // the bones' FP64 states
     EMU_CK(cudaGetLastError());
   }
+  if (h->fform) {
+    // the state is F itself; R and s from its polar decomposition (in the
+    // corner and direction buffers, which each iteration rewrites)
+    if (R || s) {
+      launch_fform_to_Rs(m, h->R, h->contrib, h->d64, h->st);
+      EMU_CK(cudaGetLastError());
+    }
+    if (R && (rc = soa_to_aos(h->contrib, 9, R))) return rc;
+    if (s && (rc = soa_to_aos(h->d64, 6, s))) return rc;
+    if (F && (rc = soa_to_aos(h->R, 9, F))) return rc;
+    return EMU_OK;
+  }
   if (R && (rc = soa_to_aos(h->R, 9, R))) return rc;
   if (s && (rc = soa_to_aos(h->s, 6, s))) return rc;
   if (F) {
@@ -1693,6 +1744,13 @@ int emu_get_element_state(emu_handle* h, double* R, double* s, double* F) {
 int emu_set_element_state(emu_handle* h, const double* R, const double* s, const double* q) {
   if (!h) return fail(EMU_ERR_INVALID_ARG, "NULL handle");
   const int64_t m = h->m;
+  if (h->fform && (R || s) && (!R || !s)) {
+    // F-form: the untouched factor comes from the current F = R S
+    std::vector<double> Rc(9 * m), sc_(6 * m);
+    int rc = emu_get_element_state(h, R ? nullptr : Rc.data(), s ? nullptr : sc_.data(), nullptr);
+    if (rc) return rc;
+    return emu_set_element_state(h, R ? R : Rc.data(), s ? s : sc_.data(), q);
+  }
   std::vector<double> tmp(9 * m);
   if (R) {
     for (int64_t i = 0; i < m; ++i)
@@ -1717,6 +1775,11 @@ int emu_set_element_state(emu_handle* h, const double* R, const double* s, const
     // a free bone's tets share one state: every copy takes its first tet's
     bones_state_from_element_arrays(h);
     EMU_CK(cudaGetLastError());
+  }
+  if (h->fform && (R || s)) {  // F = R S in place of R
+    launch_compose_F(m, h->R, h->s, h->R, h->st);
+    EMU_CK(cudaGetLastError());
+    EMU_CK(cudaStreamSynchronize(h->st));
   }
   if (h->mixed && (R || s)) {
     launch_Rs_to_mixed(m, h->R, h->s, h->quat, h->E32, h->st);
@@ -1780,6 +1843,16 @@ int emu_eval_stretch_terms(const double* s, const double* params, int64_t n, int
   if (!s || !params || n < 0) return fail(EMU_ERR_INVALID_ARG, "bad arguments");
   if (n == 0) return EMU_OK;
   launch_eval_stretch(s, params, n, mixed, psi, grad, hess, (cudaStream_t)stream);
+  EMU_CK(cudaGetLastError());
+  EMU_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return EMU_OK;
+}
+
+int emu_eval_fform_terms(const double* F, const double* params, int64_t n, double* psi, double* grad, double* hess,
+                         void* stream) {
+  if (!F || !params || n < 0) return fail(EMU_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return EMU_OK;
+  launch_eval_fform(F, params, n, psi, grad, hess, (cudaStream_t)stream);
   EMU_CK(cudaGetLastError());
   EMU_CK(cudaStreamSynchronize((cudaStream_t)stream));
   return EMU_OK;
