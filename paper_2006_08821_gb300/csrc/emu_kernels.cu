@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(256) k_syrk(TetArgs<TW> a, double* __restrict_
   __shared__ TW sy[CH][9];
   __shared__ double sw[CH];
   const int tid = threadIdx.x;
-  const int tr = tid >> 4, tc = tid & 15;
+  int tr = 0, tc = 0;
+  const bool tile = lower_tile(tid, tr, tc);  // 5 of the 8 warps issue the product
   TW acc[3][3];  // per-block partial sums in TW; across blocks in FP64
 #pragma unroll
   for (int p = 0; p < 3; ++p)
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(256) k_syrk(TetArgs<TW> a, double* __restrict_
     }
     __syncthreads();
 #pragma unroll 4
-    for (int kr = 0; kr < KR; ++kr) {
+    for (int kr = 0; kr < (tile ? KR : 0); ++kr) {
       const TW a0 = sY[kr][3 * tr], a1 = sY[kr][3 * tr + 1], a2 = sY[kr][3 * tr + 2];
       const TW b0 = sY[kr][3 * tc], b1 = sY[kr][3 * tc + 1], b2 = sY[kr][3 * tc + 2];
       acc[0][0] += a0 * b0;
@@ -240,10 +241,15 @@ __global__ void __launch_bounds__(256) k_syrk(TetArgs<TW> a, double* __restrict_
   }
   // entry-major partials: cpart[e * gridDim.x + block]
   const size_t nb = gridDim.x;
+  if (tile)
 #pragma unroll
-  for (int p = 0; p < 3; ++p)
+    for (int p = 0; p < 3; ++p)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) cpart[(size_t)((3 * tr + p) * kK + 3 * tc + q) * nb + blockIdx.x] = (double)acc[p][q];
+      for (int q = 0; q < 3; ++q) {
+        const double v = (double)acc[p][q];
+        cpart[(size_t)((3 * tr + p) * kK + 3 * tc + q) * nb + blockIdx.x] = v;
+        if (tr != tc) cpart[(size_t)((3 * tc + q) * kK + 3 * tr + p) * nb + blockIdx.x] = v;
+      }
   if (tid < kK) cpart[(size_t)(kCapEntries + tid) * nb + blockIdx.x] = by;
 }
 

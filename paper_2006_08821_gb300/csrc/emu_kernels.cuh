@@ -145,4 +145,19 @@ __device__ __forceinline__ void ls_select_block(const double* dir_partials, int 
 
 constexpr int kCapEntries = kK * kK;   // 48 x 48 partial capacitance
 
+// The 3 x 3 tiles of the lower triangle of the 48 x 48 symmetric product
+// (tile row >= tile column), 136 of them: thread t < 136 of a block takes
+// tile t in row order; the others have none. The upper triangle is the
+// mirror image (a_p b_q and b_q a_p are the same product, so each entry's
+// sum is the one a full tiling would form).
+constexpr int kLowerTiles = (kK / 3) * (kK / 3 + 1) / 2;
+__device__ __forceinline__ bool lower_tile(int t, int& tr, int& tc) {
+  if (t >= kLowerTiles) return false;
+  int r = 0;
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  tr = r;
+  tc = t - r * (r + 1) / 2;
+  return true;
+}
+
 }  // namespace emu
