@@ -57,40 +57,78 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned& epoch, int
   return *s_flag == 0;
 }
 
+// Values carried per reduction, padded to a power of two (the butterfly below).
+__host__ __device__ constexpr int red_pad(int nv) { return nv <= 1 ? 1 : 2 * red_pad((nv + 1) / 2); }
+
+// Block sum of v[0..NV) in a fixed order, written to out[0..NV) (shared or
+// global; sm holds 8 * red_pad(NV) doubles). Within a warp a halving
+// butterfly: at each of the five steps a lane keeps half of the values it
+// carries and adds its partner's copy of that half, so a lane does about
+// P adds (P = red_pad(NV)) instead of 5 NV shuffle-adds of a plain tree per
+// value. That matters in FP64, whose warp instructions occupy GB300's FP64
+// pipe for many cycles each. Lane l ends with the sums of indices
+// l * (P / 32) .. when P >= 32, else of index l / (32 / P).
 template <int NV>
 __device__ __forceinline__ void block_partials(double (&v)[NV], double* out, double* sm) {
+  constexpr int P = red_pad(NV);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double x[P];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double x = v[k];
+  for (int k = 0; k < P; ++k) x[k] = k < NV ? v[k] : 0.0;
+  int base = 0;  // index of x[0] after the halving steps
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) sm[warp * NV + k] = x;
+  for (int t = 0; t < 5; ++t) {
+    const int o = 16 >> t;
+    constexpr int P0 = P;
+    const int h = (P0 >> t) / 2;  // values kept at this step (0: one value left)
+    if (h >= 1) {
+      const bool hi = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < P0 / 2; ++i) {
+        if (i < h) {
+          const double keep = hi ? x[h + i] : x[i];
+          const double send = hi ? x[i] : x[h + i];
+          x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+      if (hi) base += h;
+    } else {
+      x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+    }
+  }
+  constexpr int C = P >= 32 ? P / 32 : 1;
+  if (P >= 32 || (lane % (32 / P)) == 0) {
+#pragma unroll
+    for (int i = 0; i < C; ++i) sm[warp * P + base + i] = x[i];
   }
   __syncthreads();
   for (int k = threadIdx.x; k < NV; k += blockDim.x) {
-    double x = 0.0;
-    for (int w = 0; w < nw; ++w) x += sm[w * NV + k];
-    out[k] = x;
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sm[w * P + k];
+    out[k] = t;
   }
   __syncthreads();
 }
 
-// Every block sums the per-block partials with the same fixed tree, so all
-// blocks hold bit-identical scalars. Loads bypass L1 (__ldcg): the partials
-// were written by other SMs.
+// Every block sums the per-block partials in the same fixed order (thread k
+// adds value k over the blocks 0, 1, ...), so all blocks hold bit-identical
+// scalars. Loads bypass L1 (__ldcg): the partials were written by other SMs.
 template <int NV>
-__device__ __forceinline__ void sum_partials(const double* partials, double* s_out, double* sm) {
-  // thread t sums blocks t, t + blockDim, ... for every value, then a
-  // shared-memory tree over the 256 threads
-  double loc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) loc[k] = 0.0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) loc[k] += __ldcg(partials + (size_t)b * NV + k);
+__device__ __forceinline__ void sum_partials(const double* partials, double* s_out, double*) {
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    const unsigned nb = gridDim.x;
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    unsigned b = 0;
+    for (; b + 4 <= nb; b += 4) {
+      t0 += __ldcg(partials + (size_t)b * NV + k);
+      t1 += __ldcg(partials + (size_t)(b + 1) * NV + k);
+      t2 += __ldcg(partials + (size_t)(b + 2) * NV + k);
+      t3 += __ldcg(partials + (size_t)(b + 3) * NV + k);
+    }
+    for (; b < nb; ++b) t0 += __ldcg(partials + (size_t)b * NV + k);
+    s_out[k] = (t0 + t1) + (t2 + t3);
   }
-  block_partials<NV>(loc, s_out, sm);
+  __syncthreads();
 }
 
 template <int NR, typename T>
@@ -133,7 +171,7 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgsT<T> a) {
   constexpr int NC = COARSE ? kModes * NR : 0;  // coarse values (mode j, column c) at j * NR + c
   constexpr int NV0 = 4 * NR + NC;              // gamma, delta, rr, bb, Phi^T w
   constexpr int NV = 3 * NR + NC;               // gamma, delta, rr, Phi^T w
-  __shared__ double sm[8 * NV0];
+  __shared__ double sm[8 * red_pad(NV0)];
   __shared__ double sc[NV0];
   __shared__ int s_flag;
   __shared__ double s_alpha[NR], s_beta[NR], s_gamma[NR], s_thr[NR], s_bb[NR], s_rr[NR];
@@ -453,7 +491,7 @@ __global__ void __launch_bounds__(256) k_residual64(int64_t n, const int32_t* __
                                                     const double* __restrict__ b, const double* __restrict__ x,
                                                     float* __restrict__ r32, double* __restrict__ r64,
                                                     double* __restrict__ partials, const uint8_t* __restrict__ skip) {
-  __shared__ double sm[8 * 6];
+  __shared__ double sm[8 * red_pad(6)];
   double loc[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     double acc[3];
