@@ -500,6 +500,8 @@ def make_params(emu, args, mixed):
         p.cg_local_degree = args.cg_degree
     if getattr(args, "form", "rs") == "f":
         p.form = emu.FORM_F
+    if getattr(args, "autotune", False):
+        p.autotune = 1
     return p
 
 
@@ -657,6 +659,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (1/s)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: device-memory budget")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--autotune", action="store_true",
+                    help="let the library time and pick the coupling solves' launch settings at set-up")
     ap.add_argument("--form", default="rs", choices=["rs", "f"],
                     help="Newton variables: rotation-stretch chart (rs) or the F-form of Sec. 3.2.1 (f, FP64 only)")
     ap.add_argument("--tol", type=float, default=1e-6)
@@ -709,6 +713,7 @@ def main():
     t_setup = time.perf_counter()
     solver = emu.Solver(mesh, params, stream=stream.cuda_stream, allocator=emu.TorchAllocator(local))
     setup_s = time.perf_counter() - t_setup
+    tuning = solver.tuning()
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
     m, n = mesh.n_tets, mesh.n_verts
 
@@ -786,7 +791,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "l2": f"flushed ({args.flush_mb} MB write) between steps",
                    "tets": m, "verts": n, "ls_sigma0": params.ls_sigma0, "cg_local_degree": params.cg_local_degree,
-                   "form": args.form},
+                   "form": args.form, "tuning": tuning},
         "ms_per_converged_frame_p50": float(np.median(frame_ms)),
         "frame_ms_p99": float(np.percentile(frame_ms, 99)),
         "newton_iters_per_frame": [int(x) for x in iters],

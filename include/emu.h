@@ -190,7 +190,17 @@ typedef struct {
  *                   meshes without bones or joints; otherwise emu_create
  *                   returns EMU_ERR_NOT_IMPLEMENTED. emu_get_element_state
  *                   then returns F and its polar factors R, s;
- *                   emu_set_element_state sets F = R S. */
+ *                   emu_set_element_state sets F = R S.
+ *   autotune        0 (default) or 1: emu_create times candidate settings of
+ *                   the coupling solves on the mesh's own matrix and keeps
+ *                   the fastest: the local polynomial's degree (2, 3, 4, 6,
+ *                   8; overrides cg_local_degree) for the mixed path's dq
+ *                   solves, and the rows per block (64, 128, 256) of the
+ *                   FP64 CG. Each choice is kept for the process per device
+ *                   and mesh size, so handles of one mesh run the same
+ *                   settings; another process may choose differently, and
+ *                   its results then differ in rounding. emu_get_tuning
+ *                   reports the settings in use. */
 typedef struct {
   double alpha_rel;
   int32_t weight_mode;
@@ -213,6 +223,7 @@ typedef struct {
   double eps_joint;
   int32_t cg_local_degree;
   int32_t form;
+  int32_t autotune;
 } emu_params;
 
 /* Per-solve statistics. */
@@ -392,6 +403,12 @@ int emu_get_sizes(emu_handle* h, int64_t* n_verts, int64_t* n_tets, int32_t* k_m
  * inputs and outputs. */
 int emu_eval_stretch_terms(const double* s, const double* params, int64_t n, int32_t mixed,
                            double* psi, double* grad, double* hess, void* stream);
+
+/* Launch settings of the coupling solves in use: the local polynomial's
+ * degree of the mixed path's pipelined CG (0 where that CG is not used),
+ * the rows per block of the FP64 CG, and whether emu_create ran the
+ * autotuner. Any pointer may be NULL. */
+int emu_get_tuning(emu_handle* h, int32_t* cg_local_degree, int32_t* cg64_rows_per_block, int32_t* tuned);
 
 /* Evaluates, on the device, the F-form's element terms (Sec. 3.1 energy,
  * Sec. 3.2.1 Hessian):

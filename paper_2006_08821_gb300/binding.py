@@ -42,7 +42,7 @@ EXPORTED = [
     "emu_acap_solve_noalloc", "emu_batch_solve", "emu_required_bytes", "emu_server_create",
     "emu_server_submit", "emu_server_poll", "emu_server_result", "emu_server_destroy", "emu_check_bounded_wait",
     "emu_eval_capacitance", "emu_set_external_forces", "emu_fiber_field", "emu_alpha_sweep",
-    "emu_eval_fform_terms",
+    "emu_eval_fform_terms", "emu_get_tuning",
 ]
 
 PHASES = ["rhs", "assemble", "pcg", "grad", "syrk", "small", "dir", "ls", "update"]
@@ -109,6 +109,7 @@ class emu_params(C.Structure):
         ("eps_joint", C.c_double),
         ("cg_local_degree", C.c_int32),
         ("form", C.c_int32),
+        ("autotune", C.c_int32),
     ]
 
 
@@ -232,6 +233,7 @@ class Params:
     eps_joint: float = -1e-4
     cg_local_degree: int = 4
     form: int = FORM_RS
+    autotune: int = 0
 
     def to_c(self) -> emu_params:
         p = emu_params()
@@ -394,6 +396,12 @@ class Solver:
 
     def reset(self):
         _check(self.lib.emu_reset(self.handle), self.lib)
+
+    def tuning(self) -> dict:
+        """emu_get_tuning: the coupling solves' launch settings in use."""
+        d, r, t = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+        _check(self.lib.emu_get_tuning(self.handle, C.byref(d), C.byref(r), C.byref(t)), self.lib)
+        return {"cg_local_degree": int(d.value), "cg64_rows_per_block": int(r.value), "tuned": bool(t.value)}
 
     def acap_solve_noalloc(self, F_dev_ptr: int, q_dev_ptr: int, stream=None):
         """emu_acap_solve_noalloc: q = q*(F) with no device allocation (device pointers)."""

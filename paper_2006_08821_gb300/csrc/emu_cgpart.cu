@@ -205,20 +205,25 @@ bool build_cg_partition(int64_t n, const double* Q, const std::vector<int32_t>& 
       lmax = std::max(lmax, rs);
     }
   P.lmax = lmax;
-  // Chebyshev acceleration on [lmin, lmax] from a zero start (Saad,
-  // Iterative Methods for Sparse Linear Systems, Alg. 12.1): d_0 = r / theta,
-  // then d_i = rho_i rho_{i-1} d_{i-1} + (2 rho_i / delta) res_i
+  cg_cheb_coeffs(lmax, degree, &P.c0, P.c1, P.c2);
+  return true;
+}
+
+// Chebyshev acceleration on [lmin, lmax] from a zero start (Saad,
+// Iterative Methods for Sparse Linear Systems, Alg. 12.1): d_0 = r / theta,
+// then d_i = rho_i rho_{i-1} d_{i-1} + (2 rho_i / delta) res_i
+void cg_cheb_coeffs(double lmax, int degree, float* c0, float* c1, float* c2) {
   const double lmin = lmax / kChebRatio;
   const double th = 0.5 * (lmax + lmin), de = 0.5 * (lmax - lmin), sg = th / de;
   double rho = 1.0 / sg;
-  P.c0 = (float)(1.0 / th);
+  *c0 = (float)(1.0 / th);
+  for (int i = 0; i < kChebMax; ++i) c1[i] = c2[i] = 0.f;
   for (int i = 1; i < degree; ++i) {
     const double rn = 1.0 / (2.0 * sg - rho);
-    P.c1[i] = (float)(rn * rho);
-    P.c2[i] = (float)(2.0 * rn / de);
+    c1[i] = (float)(rn * rho);
+    c2[i] = (float)(2.0 * rn / de);
     rho = rn;
   }
-  return true;
 }
 
 }  // namespace emu

@@ -44,6 +44,10 @@ int cg_local_width_max(int rpt);
 // and the local table for a polynomial of ``degree`` (1: no local table).
 // Rows with more local entries than cg_local_width_max(rpt) keep their
 // largest ones, symmetrically. Returns false if the sizes do not fit.
+// Coefficients of the local Chebyshev polynomial of ``degree`` (>= 2) on
+// [lmax / kChebRatio, lmax] (c0 and the steps c1[i], c2[i] for i < degree).
+void cg_cheb_coeffs(double lmax, int degree, float* c0, float* c1, float* c2);
+
 bool build_cg_partition(int64_t n, const double* Q, const std::vector<int32_t>& rowptr,
                         const std::vector<int32_t>& col, const std::vector<double>& val, int G, int rpt, int nt,
                         int degree, CgPartHost* out);

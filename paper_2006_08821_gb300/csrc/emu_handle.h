@@ -102,6 +102,9 @@ struct emu_handle {
   uint32_t* cg_loc = nullptr;
   int cg_lw = 0, cg_degree = 1;
   float cg_c0 = 1.f, cg_c1[kChebMax] = {0}, cg_c2[kChebMax] = {0};
+  double cg_lmax = 0.0;            // Gershgorin bound of the local blocks (the polynomial's interval)
+  int cg64_rows = 128;             // rows per block of the FP64 CG (grid_pcg3 = ceil(n / cg64_rows), capped)
+  bool tuned = false;              // set-up ran the autotuner (emu_params.autotune)
   double q_tol = 1e-8;
   double dq_tol_now = 5e-2;  // dq tolerance of the current solve call
   double dq_tol_base = 0.0;  // tighter dq tolerance a stalled solve settled on (0: params.dq_tol)

@@ -7,7 +7,10 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <thread>
 #include <vector>
@@ -17,6 +20,13 @@
 #include "emu_fform.h"
 #include "emu_mixed.cuh"
 #include "emu_pcg.h"
+
+namespace emu {
+namespace {
+int enqueue_grad(emu_handle* h);
+int enqueue_direction(emu_handle* h);
+}  // namespace
+}  // namespace emu
 
 using namespace emu;
 
@@ -144,6 +154,7 @@ int validate_params(const emu_params* p) {
   if (p->cg_local_degree < 1 || p->cg_local_degree > kChebMax)
     return fail(EMU_ERR_INVALID_ARG, "cg_local_degree must be in [1, 8]");
   if (p->form != EMU_FORM_RS && p->form != EMU_FORM_F) return fail(EMU_ERR_INVALID_ARG, "form must be RS or F");
+  if (p->autotune != 0 && p->autotune != 1) return fail(EMU_ERR_INVALID_ARG, "autotune must be 0 or 1");
   return EMU_OK;
 }
 
@@ -365,6 +376,164 @@ int solve_dq(emu_handle* h) {
   return EMU_OK;
 }
 
+// ---- autotuner (emu_params.autotune) ----
+// Candidate launch settings of the coupling solves are timed at set-up on
+// the handle's own matrix, and the fastest is kept:
+//  * the degree of the block-local Chebyshev polynomial in the mixed path's
+//    pipelined FP32 CG (its dq solves): one solve to dq_tol from zero per
+//    degree on the right-hand side of a real first Newton direction, the
+//    better of two runs each;
+//  * the rows per block of the FP64 CG (the FP64 path, meshes with bones):
+//    a fixed count of iterations per candidate on a seeded right-hand side
+//    (the count to a tolerance does not depend on the launch shape).
+// Each candidate runs the same method; only rounding differs between them.
+// A choice is kept for the process per (device, mesh size, kind), so every
+// handle of one mesh in a process runs the same settings (a batch stays
+// bit-identical to its meshes solved alone).
+constexpr int kTuneDegrees[] = {2, 3, 4, 6, 8};
+constexpr int kTuneRows[] = {64, 128, 256};
+constexpr int kTuneIters64 = 40;
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int64_t, int64_t, int, double>, int> g_tune;
+
+// Right-hand side of a real dq solve: the first Newton direction from rest
+// at activation 0.5 on every tet (the handle's activation is zero again
+// afterwards). The coupling solves see the spectrum of real directions;
+// a random right-hand side would favour low local degrees.
+int tune_dq_rhs(emu_handle* h) {
+  std::vector<double> act(h->m, 0.5);
+  int rc = emu_set_activation(h, act.data(), h->m);
+  if (rc) return rc;
+  DevScalars init;
+  memset(&init, 0, sizeof(init));
+  init.sigma_start = h->sigma0_now;
+  EMU_CK(cudaMemcpyAsync(h->sc, &init, sizeof(init), cudaMemcpyHostToDevice, h->st));
+  rc = enqueue_grad(h);
+  if (!rc) rc = enqueue_direction(h);
+  if (rc) return rc;
+  launch_assemble_f(h->n, h->slot_ptr, h->slot_idx, h->contrib32, h->is_fixed, h->b32, h->st);
+  EMU_CK(cudaGetLastError());
+  EMU_CK(cudaStreamSynchronize(h->st));
+  std::fill(act.begin(), act.end(), 0.0);
+  return emu_set_activation(h, act.data(), h->m);
+}
+
+int tune_rhs(emu_handle* h) {
+  const int64_t n = h->n;
+  std::vector<uint8_t> fixed(n);
+  EMU_CK(cudaMemcpyAsync(fixed.data(), h->is_fixed, n, cudaMemcpyDeviceToHost, h->st));
+  EMU_CK(cudaStreamSynchronize(h->st));
+  uint64_t seed = h->prm.seed ^ 0x7E57AB1Eull;
+  std::vector<double> b(3 * n, 0.0);
+  for (int64_t k = 0; k < 3 * n; ++k) {
+    const double r = (double)(splitmix64(seed) >> 11) * (1.0 / 9007199254740992.0);
+    b[k] = fixed[k / 3] ? 0.0 : 2.0 * r - 1.0;
+  }
+  EMU_CK(cudaMemcpyAsync(h->b, b.data(), 24 * n, cudaMemcpyHostToDevice, h->st));
+  EMU_CK(cudaStreamSynchronize(h->st));
+  return EMU_OK;
+}
+
+// device time of ``run`` on the handle's stream (ms); -1 on a CUDA error
+template <typename F> float tune_time(emu_handle* h, F&& run) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = -1.f;
+  if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+      cudaEventRecord(e0, h->st) == cudaSuccess && run() == cudaSuccess && cudaEventRecord(e1, h->st) == cudaSuccess &&
+      cudaEventSynchronize(e1) == cudaSuccess)
+    cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return ms;
+}
+
+void set_cg_degree(emu_handle* h, int d) {
+  h->cg_degree = d;
+  cg_cheb_coeffs(h->cg_lmax, d, &h->cg_c0, h->cg_c1, h->cg_c2);
+}
+
+void set_cg64_rows(emu_handle* h, int rows) {
+  h->cg64_rows = rows;
+  h->grid_pcg3 = (int)std::max<int64_t>(1, std::min<int64_t>((h->n + rows - 1) / rows, h->sms));
+}
+
+int autotune(emu_handle* h) {
+  h->tuned = true;
+  const auto key = [&](int kind, double tol) { return std::make_tuple(h->device, h->n, h->m, kind, tol); };
+  // the local polynomial's degree (pipelined FP32 CG of the dq solves)
+  if (h->mixed && !cg64(h) && h->cg_part && h->cg_lw > 0 && h->aphi_ready && pcg32_pipe_ok(h->rpt32)) {
+    const double tol = h->prm.dq_tol;
+    int best = -1;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune.find(key(0, tol));
+      if (it != g_tune.end()) best = it->second;
+    }
+    if (best < 0) {
+      int rc = tune_dq_rhs(h);
+      if (rc) return rc;
+      float tbest = 0.f;
+      for (int d : kTuneDegrees) {
+        set_cg_degree(h, d);
+        float t = -1.f;
+        for (int rep = 0; rep < 2; ++rep) {
+          const float ms = tune_time(h, [&]() {
+            cudaError_t e = cudaMemsetAsync(h->dq32, 0, 12 * h->n, h->st);
+            return e == cudaSuccess ? run_pcg32(h, h->b32, h->dq32, tol) : e;
+          });
+          if (ms < 0.f) return fail(EMU_ERR_CUDA, "autotune: CG launch failed");
+          t = (t < 0.f || ms < t) ? ms : t;
+        }
+        if (best < 0 || t < tbest) {
+          best = d;
+          tbest = t;
+        }
+      }
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      best = g_tune.emplace(key(0, tol), best).first->second;  // a concurrent set-up may have stored one first
+    }
+    set_cg_degree(h, best);
+  }
+  // rows per block of the FP64 CG
+  if (cg64(h)) {
+    int best = -1;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune.find(key(1, 0.0));
+      if (it != g_tune.end()) best = it->second;
+    }
+    if (best < 0) {
+      int rc = tune_rhs(h);
+      if (rc) return rc;
+      float tbest = 0.f;
+      for (int rows : kTuneRows) {
+        set_cg64_rows(h, rows);
+        const float ms = tune_time(h, [&]() {
+          cudaError_t e = cudaMemsetAsync(h->dq, 0, 24 * h->n, h->st);
+          if (e != cudaSuccess) return e;
+          PcgArgsT<double> a = h->pcg64(h->b, h->dq, 0.0);
+          a.max_iter = kTuneIters64;
+          a.iters_out = nullptr;
+          a.fail_out = nullptr;
+          return launch_pcg<double>(3, a, h->grid_pcg3, h->st);
+        });
+        if (ms < 0.f) return fail(EMU_ERR_CUDA, "autotune: CG launch failed");
+        if (best < 0 || ms < tbest) {
+          best = rows;
+          tbest = ms;
+        }
+      }
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      best = g_tune.emplace(key(1, 0.0), best).first->second;
+    }
+    set_cg64_rows(h, best);
+  }
+  EMU_CK(cudaMemsetAsync(h->dq, 0, 24 * h->n, h->st));
+  if (h->dq32) EMU_CK(cudaMemsetAsync(h->dq32, 0, 12 * h->n, h->st));
+  EMU_CK(cudaStreamSynchronize(h->st));
+  return EMU_OK;
+}
+
 int set_rest_state(emu_handle* h) {
   std::vector<double> Rh(9 * h->m, 0.0), sh(6 * h->m, 0.0);
   for (int64_t i = 0; i < h->m; ++i) {
@@ -579,7 +748,10 @@ bool alloc_device(emu_handle* h, int64_t nnz) {
   h->grid_tet4 = (int)std::min<int64_t>(std::max<int64_t>(1, (m + 127) / 128), 4 * (int64_t)h->sms);
   h->grid_pcg3 = pcg_max_grid(3, n);
   h->grid_pcg16 = pcg_max_grid(16, n);
-  const int pcg_part = std::max(h->grid_pcg3 * (4 * 3 + 3 * kModes), h->grid_pcg16 * 64);  // per-block partials
+  // the autotuner may take up to one block per 64 rows for the FP64 CG
+  const int g3max = h->prm.autotune ? std::max<int>(h->grid_pcg3, (int)std::min<int64_t>((n + 63) / 64, h->sms))
+                                    : h->grid_pcg3;
+  const int pcg_part = std::max(g3max * (4 * 3 + 3 * kModes), h->grid_pcg16 * 64);  // per-block partials
   const int64_t gpart = std::max<int64_t>(h->grid_tet * (int64_t)kLsNV, 256 * (int64_t)(2 * h->sms + 1));
   ok = ok && h->get(h->part_grad, gpart) && h->get(h->part_dir, h->grid_tet + 1) && h->get(h->part_ls, (h->grid_tet + kBoneLsBlocks) * kLsNV) &&
        h->get(h->part_pcg, std::max<int64_t>(pcg_part, 256 * (int64_t)(2 * h->sms + 1))) &&
@@ -668,6 +840,7 @@ void emu_default_params(emu_params* p) {
   p->eps_joint = -1e-4;
   p->cg_local_degree = 4;
   p->form = EMU_FORM_RS;
+  p->autotune = 0;
 }
 
 const char* emu_status_string(int status) {
@@ -923,6 +1096,7 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     if (h->cg_part) {
       h->cg_lw = cgp.lw;
       h->cg_degree = cgp.degree;
+      h->cg_lmax = cgp.lmax;
       h->cg_c0 = cgp.c0;
       for (int i = 0; i < kChebMax; ++i) {
         h->cg_c1[i] = cgp.c1[i];
@@ -1034,6 +1208,7 @@ int emu_create(const emu_mesh_desc* desc, const emu_params* params, const emu_al
     rc = fail(EMU_ERR_CUDA, "copy q0");
   if (!rc) rc = build_modes(h);
   if (!rc) rc = final_setup_device(h);
+  if (!rc && h->prm.autotune) rc = autotune(h);
   if (!rc) rc = read_scalars(h);
   if (!rc && h->sc_host->barrier_timeout) rc = fail(EMU_ERR_TIMEOUT, "grid barrier timed out during setup");
   if (rc) {
@@ -1192,11 +1367,10 @@ int enqueue_grad(emu_handle* h) {
   return EMU_OK;
 }
 
-// enqueue the rest of one Newton iteration: direction, dq, line search, update
-int enqueue_step(emu_handle* h) {
+// the Woodbury direction (Eqs. 9-12) and its corner terms
+int enqueue_direction(emu_handle* h) {
   TetArgs<double> a64 = h->args<double>();
   MixArgs am = h->margs();
-  // Woodbury direction (Eqs. 9-12)
   h->ph_begin();
   int syrk_blocks = h->grid_syrk;
   if (h->mixed && h->syrk05) {
@@ -1233,7 +1407,16 @@ int enqueue_step(emu_handle* h) {
   }
   h->ph_end(EMU_PHASE_DIR, 1);
   EMU_CK(cudaGetLastError());
-  int rc = solve_dq(h);
+  return EMU_OK;
+}
+
+// enqueue the rest of one Newton iteration: direction, dq, line search, update
+int enqueue_step(emu_handle* h) {
+  TetArgs<double> a64 = h->args<double>();
+  MixArgs am = h->margs();
+  int rc = enqueue_direction(h);
+  if (rc) return rc;
+  rc = solve_dq(h);
   if (rc) return rc;
   // Armijo line search (Algorithm 1)
   h->ph_begin();
@@ -1645,6 +1828,7 @@ int emu_required_bytes(const emu_mesh_desc* desc, const emu_params* params, size
   if (rc) return rc;
   emu_handle h;
   h.dry = true;
+  h.prm = prm;
   h.n = desc->n_verts;
   h.m = desc->n_tets;
   h.mixed = prm.precision == EMU_PRECISION_MIXED;
@@ -1855,6 +2039,14 @@ int emu_eval_fform_terms(const double* F, const double* params, int64_t n, doubl
   launch_eval_fform(F, params, n, psi, grad, hess, (cudaStream_t)stream);
   EMU_CK(cudaGetLastError());
   EMU_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return EMU_OK;
+}
+
+int emu_get_tuning(emu_handle* h, int32_t* cg_local_degree, int32_t* cg64_rows_per_block, int32_t* tuned) {
+  if (!h) return fail(EMU_ERR_INVALID_ARG, "NULL handle");
+  if (cg_local_degree) *cg_local_degree = h->cg_part ? h->cg_degree : 0;
+  if (cg64_rows_per_block) *cg64_rows_per_block = h->cg64_rows;
+  if (tuned) *tuned = h->tuned ? 1 : 0;
   return EMU_OK;
 }
 

@@ -67,11 +67,15 @@ __host__ __device__ constexpr int red_pad(int nv) { return nv <= 1 ? 1 : 2 * red
 // P adds (P = red_pad(NV)) instead of 5 NV shuffle-adds of a plain tree per
 // value. That matters in FP64, whose warp instructions occupy GB300's FP64
 // pipe for many cycles each. Lane l ends with the sums of indices
-// l * (P / 32) .. when P >= 32, else of index l / (32 / P).
+// l * (P / 32) .. when P >= 32, else of index l / (32 / P). Warps from
+// ``nw_data`` on hold only zeros (their threads own no rows) and are left
+// out of the sum.
 template <int NV>
-__device__ __forceinline__ void block_partials(double (&v)[NV], double* out, double* sm) {
+__device__ __forceinline__ void block_partials(double (&v)[NV], double* out, double* sm, int nw_data = 32) {
   constexpr int P = red_pad(NV);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = min(nw_data, (int)(blockDim.x >> 5));
+  if (warp < nw) {
   double x[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) x[k] = k < NV ? v[k] : 0.0;
@@ -101,6 +105,7 @@ __device__ __forceinline__ void block_partials(double (&v)[NV], double* out, dou
 #pragma unroll
     for (int i = 0; i < C; ++i) sm[warp * P + base + i] = x[i];
   }
+  }
   __syncthreads();
   for (int k = threadIdx.x; k < NV; k += blockDim.x) {
     double t = 0.0;
@@ -110,23 +115,37 @@ __device__ __forceinline__ void block_partials(double (&v)[NV], double* out, dou
   __syncthreads();
 }
 
-// Every block sums the per-block partials in the same fixed order (thread k
-// adds value k over the blocks 0, 1, ...), so all blocks hold bit-identical
-// scalars. Loads bypass L1 (__ldcg): the partials were written by other SMs.
+// Every block sums the per-block partials in the same fixed order, so all
+// blocks hold bit-identical scalars: the block's 256 threads form G groups
+// of P = red_pad(NV) (thread g P + k takes value k of the blocks g, g + G,
+// ..., eight loads in flight), then thread k adds the G group sums in
+// order. Loads bypass L1 (__ldcg): the partials were written by other SMs.
+// Needs blockDim.x == 256.
 template <int NV>
 __device__ __forceinline__ void sum_partials(const double* partials, double* s_out, double*) {
-  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+  constexpr int P = red_pad(NV);
+  constexpr int G = P <= 256 ? 256 / P : 1;
+  __shared__ double sg[256];
+  const int g = threadIdx.x / P, k = threadIdx.x % P;
+  if (g < G && k < NV) {
     const unsigned nb = gridDim.x;
-    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-    unsigned b = 0;
-    for (; b + 4 <= nb; b += 4) {
-      t0 += __ldcg(partials + (size_t)b * NV + k);
-      t1 += __ldcg(partials + (size_t)(b + 1) * NV + k);
-      t2 += __ldcg(partials + (size_t)(b + 2) * NV + k);
-      t3 += __ldcg(partials + (size_t)(b + 3) * NV + k);
+    double t = 0.0;
+    unsigned b = g;
+    for (; b + 7 * G < nb; b += 8 * G) {
+      double l[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) l[u] = __ldcg(partials + (size_t)(b + u * G) * NV + k);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t += l[u];
     }
-    for (; b < nb; ++b) t0 += __ldcg(partials + (size_t)b * NV + k);
-    s_out[k] = (t0 + t1) + (t2 + t3);
+    for (; b < nb; b += G) t += __ldcg(partials + (size_t)b * NV + k);
+    sg[g * P + k] = t;
+  }
+  __syncthreads();
+  for (int kk = threadIdx.x; kk < NV; kk += blockDim.x) {
+    double t = 0.0;
+    for (int gg = 0; gg < G; ++gg) t += sg[gg * P + kk];
+    s_out[kk] = t;
   }
   __syncthreads();
 }
@@ -189,6 +208,8 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgsT<T> a) {
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * per;
   const int64_t r1 = r0 + per < n ? r0 + per : n;
+  // warps whose threads own rows (the others' partial sums are zero)
+  const int nwr = r1 > r0 ? (int)((r1 - r0 + 31) / 32 < 8 ? (r1 - r0 + 31) / 32 : 8) : 0;
   const T* __restrict__ b = a.b;
   T* __restrict__ x = a.x;
   T* __restrict__ r = a.r;
@@ -248,7 +269,7 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgsT<T> a) {
         for (int j = 0; j < NR; ++j) loc[k * NR + j] += ph * (double)r[v * NR + j];
       }
     }
-    block_partials<NC>(loc, a.partials + (size_t)blockIdx.x * NV0, sm);
+    block_partials<NC>(loc, a.partials + (size_t)blockIdx.x * NV0, sm, nwr);
     if (!grid_sync(a.bar, epoch, &s_flag, a.wait_ns)) goto timeout;
     {
       double tmp[NC > 0 ? NC : 1];
@@ -290,7 +311,7 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgsT<T> a) {
         }
       }
     }
-    block_partials<NV0>(loc, a.partials + (size_t)blockIdx.x * NV0, sm);
+    block_partials<NV0>(loc, a.partials + (size_t)blockIdx.x * NV0, sm, nwr);
   }
   if (!grid_sync(a.bar, epoch, &s_flag, a.wait_ns)) goto timeout;
   sum_partials<NV0>(a.partials, sc, sm);
@@ -368,7 +389,7 @@ __global__ void __launch_bounds__(256) pcg_kernel(PcgArgsT<T> a) {
             }
           }
         }
-        block_partials<NV>(loc, a.partials + (size_t)blockIdx.x * NV, sm);
+        block_partials<NV>(loc, a.partials + (size_t)blockIdx.x * NV, sm, nwr);
       }
       if (!grid_sync(a.bar, epoch, &s_flag, a.wait_ns)) goto timeout;
       sum_partials<NV>(a.partials, sc, sm);
