@@ -533,10 +533,29 @@ __global__ void __launch_bounds__(256) k_residual64(int64_t n, const int32_t* __
   block_partials<6>(loc, partials + (size_t)blockIdx.x * 6, sm);
 }
 
-__global__ void k_sum_partials6(const double* partials, int nblk, double* out) {
+// out[k] = sum over the blocks of partials[b * 6 + k]: 32 groups of 8 threads
+// (thread 8 g + k takes blocks g, g + 32, ..., eight loads in flight), then
+// the group sums in a fixed order.
+__global__ void __launch_bounds__(256) k_sum_partials6(const double* partials, int nblk, double* out) {
+  __shared__ double sg[32][8];
+  const int g = threadIdx.x >> 3, k = threadIdx.x & 7;
+  double t = 0.0;
+  if (k < 6) {
+    int b = g;
+    for (; b + 7 * 32 < nblk; b += 8 * 32) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = partials[(size_t)(b + 32 * u) * 6 + k];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t += v[u];
+    }
+    for (; b < nblk; b += 32) t += partials[(size_t)b * 6 + k];
+  }
+  sg[g][k] = t;
+  __syncthreads();
   if (threadIdx.x < 6) {
     double x = 0.0;
-    for (int b = 0; b < nblk; ++b) x += partials[(size_t)b * 6 + threadIdx.x];
+    for (int gg = 0; gg < 32; ++gg) x += sg[gg][threadIdx.x];
     out[threadIdx.x] = x;
   }
 }
@@ -550,7 +569,7 @@ cudaError_t launch_residual64(int64_t n, const int32_t* rowptr, const int32_t* c
                               const double* x, float* r32, double* r64, double* partials, int grid, double* out6,
                               cudaStream_t st, const uint8_t* skip) {
   k_residual64<<<grid, 256, 0, st>>>(n, rowptr, col, val, b, x, r32, r64, partials, skip);
-  k_sum_partials6<<<1, 32, 0, st>>>(partials, grid, out6);
+  k_sum_partials6<<<1, 256, 0, st>>>(partials, grid, out6);
   return cudaGetLastError();
 }
 
