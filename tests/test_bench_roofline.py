@@ -39,3 +39,17 @@ def test_per_tet_fractions_and_whole_iteration():
     assert math.isclose(w["scope_ceiling_tet_iters_s"], 6800e9 / (560 + 140 * 30.0))
     assert math.isclose(w["frac_of_scope_ceiling"], 5e8 / w["scope_ceiling_tet_iters_s"])
     assert math.isclose(w["us_per_iter"], 1e3 * sum(v[0] for v in _prof().values()) / 10)
+
+
+def test_fform_byte_accounting():
+    # the F-form (FP64) keeps F (72 B) as its state instead of R and s
+    # (120 B) and a 45-entry factor instead of the 54-entry chart factor
+    m, n, nnz = 1000, 300, 4000
+    for phase, dstate, dfac in [("grad", 48, 9 * 8), ("dir", 0, 9 * 8), ("syrk", 0, 9 * 8), ("ls", 48, 0),
+                                ("update", 96, 0), ("rhs", 48, 0)]:
+        rs = bench.algorithmic_bytes(phase, False, m, n, nnz, 0.0)
+        ff = bench.algorithmic_bytes(phase, False, m, n, nnz, 0.0, fform=True)
+        assert math.isclose(rs - ff, (dstate + dfac) * m), phase
+    # the coupling solve does not depend on the form
+    assert bench.algorithmic_bytes("pcg", False, m, n, nnz, 10.0) == bench.algorithmic_bytes(
+        "pcg", False, m, n, nnz, 10.0, fform=True)
